@@ -1,0 +1,186 @@
+/*
+ * pm.h — C ABI of the B300 pattern-morphing library (exact subgraph-pattern
+ * counting and MNI support on a CSR data graph, with pattern morphing).
+ *
+ * Problem statement followed (Jamshidi & Vora, "Pattern Morphing for
+ * Efficient Graph Mining", Section 2): a data graph G, a set of query
+ * patterns (simple connected graphs, optionally vertex-labeled) each either
+ * edge-induced (p^E: no anti-edges) or vertex-induced (p^V: an anti-edge on
+ * every non-adjacent pair), and an operation: counting (Motif Counting, sum
+ * aggregation) or minimum-node-image support (Frequent Subgraph Mining).
+ * The library morphs the query set into an alternative pattern set
+ * (Section 3), matches that set on the GPU, and transforms the aggregated
+ * results back (Theorems 3.1 / 3.2, Corollary 3.1).
+ *
+ * Conventions for every entry point:
+ *  - Status codes are returned; the library never aborts the process.
+ *  - The plan handle type is pm_query_plan (the C name pm_plan is the
+ *    function that makes one).
+ *  - Host input arrays are read during the call only and never retained;
+ *    the caller keeps ownership.  Handles (pm_graph, pm_query_plan) are owned by
+ *    the library and released with pm_free_graph / pm_free_plan.
+ *  - A graph is read-only after loading; several plans (on several streams)
+ *    may share it.  A plan is used by one stream at a time.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *  - Vertex ids in inputs and outputs are the caller's; internally vertices
+ *    are renumbered by (degree, caller id) ascending.
+ *  - Counts are exact 128-bit unsigned integers stored as two uint64 words
+ *    (low word first); the morph transform runs modulo 2^128, which is exact
+ *    whenever every true result fits in 128 bits.
+ */
+#ifndef PM_H
+#define PM_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pm_graph pm_graph;
+typedef struct pm_query_plan pm_query_plan;   /* made by pm_plan() */
+
+typedef enum {
+    PM_OK = 0,
+    PM_EINVAL = -1,        /* bad argument: null pointer, id out of range, pattern not connected, ... */
+    PM_ENOMEM = -2,        /* host or device allocation failed */
+    PM_ECUDA = -3,         /* a CUDA runtime call failed (pm_last_error() has the text) */
+    PM_ETIMEOUT = -4,      /* the device deadline expired; partial results are not returned */
+    PM_EOVERFLOW = -5,     /* a result does not fit the requested output width */
+    PM_EUNSUPPORTED = -6,  /* valid request the library does not handle (e.g. MNI vertex-from-edge morph) */
+    PM_ECANCELLED = -7     /* cancelled by the caller */
+} pm_status;
+
+/* Section 2: edge-induced patterns have no anti-edges; vertex-induced ones
+ * have anti-edges on all non-adjacent pairs.  Cliques are both. */
+typedef enum { PM_EDGE_INDUCED = 0, PM_VERTEX_INDUCED = 1 } pm_induced;
+
+/* Section 2 applications: counting (Motif Counting) or MNI support (FSM). */
+typedef enum { PM_OP_COUNT = 0, PM_OP_SUPPORT = 1 } pm_op;
+
+/* Section 4.2 variants: no morphing (query patterns matched as given),
+ * naive morphing (edge-induced queries -> vertex-induced superpatterns,
+ * vertex-induced queries -> edge-induced superpatterns), and cost-based
+ * selection among the alternative sets (Section 4.1). */
+typedef enum { PM_MORPH_NONE = 0, PM_MORPH_NAIVE = 1, PM_MORPH_COST = 2 } pm_morph_mode;
+
+#define PM_MAX_K 8
+
+/* A query pattern on vertices 0..k-1 (2 <= k <= PM_MAX_K, at most 6 for
+ * PM_OP_SUPPORT).  edge_mask bit i is the i-th pair (a, b), a < b, in
+ * lexicographic order (0,1), (0,2), ..., (0,k-1), (1,2), ...  label[u] is the
+ * vertex label required at u, or -1 for any label.  The pattern must be
+ * connected (Section 2), otherwise PM_EINVAL. */
+typedef struct {
+    int32_t k;
+    uint32_t edge_mask;
+    int8_t label[PM_MAX_K];
+    int32_t induced;        /* pm_induced */
+} pm_pattern;
+
+typedef struct {
+    int64_t n;               /* vertices */
+    int64_t m;               /* undirected edges after cleaning */
+    int64_t self_loops;      /* input edges dropped as self-loops */
+    int64_t duplicates;      /* input edges dropped as duplicates (either direction) */
+    int64_t max_degree;
+    int64_t device_bytes;    /* device memory held by the graph */
+    int32_t labeled;
+    int32_t device;
+} pm_graph_info;
+
+typedef struct {
+    int32_t n_queries;       /* requested patterns */
+    int32_t n_matched;       /* distinct patterns the GPU matches (alternative set) */
+    int32_t n_kernels_plans; /* matching plans (one per automorphism orbit of each matched pattern) */
+    int32_t op;
+} pm_plan_info;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  Both
+ * callbacks must be set together; NULL restores cudaMalloc/cudaFree.  They
+ * are called with the target device current and must return device memory
+ * aligned to at least 256 bytes, or NULL on failure. */
+typedef void *(*pm_alloc_fn)(size_t bytes, int device, void *ctx);
+typedef void (*pm_free_fn)(void *ptr, size_t bytes, int device, void *ctx);
+pm_status pm_set_allocator(pm_alloc_fn alloc, pm_free_fn release, void *ctx);
+
+/* Load an undirected data graph (Section 2: G with vertices V, edges E and
+ * optional labels L).  n vertices with ids 0..n-1; m_raw edges (src[i], dst[i])
+ * in either direction; self-loops and duplicates are dropped and reported.
+ * labels: n bytes or NULL (unlabeled).  The graph is renumbered by
+ * (degree, id) ascending, stored as CSR with sorted rows (int64 row offsets,
+ * int32 column ids, uint8 labels) on `device`, uploaded on `stream`, and the
+ * call returns after the upload completes.  Errors: PM_EINVAL (null pointer,
+ * n < 1 or n > 2^31-1, an id outside [0, n)), PM_ENOMEM, PM_ECUDA. */
+pm_status pm_load_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_t *dst,
+                        const uint8_t *labels, int device, void *stream, pm_graph **out);
+pm_status pm_graph_get_info(const pm_graph *g, pm_graph_info *out);
+/* new_id[v] = internal (degree-ordered) id of caller vertex v; n entries. */
+pm_status pm_graph_vertex_order(const pm_graph *g, int32_t *new_id);
+void pm_free_graph(pm_graph *g);
+
+/* Plan a query set (Section 4.1 "external module", step a): canonicalise and
+ * deduplicate the nq query patterns, choose each one's alternative pattern
+ * set by `mode` (Theorem 3.1 for edge-induced queries, Corollary 3.1 applied
+ * recursively for vertex-induced ones; MNI support morphs only edge-induced
+ * queries, Section 3.2.3), deduplicate the matched patterns across queries,
+ * and compile one matching plan per automorphism orbit of each matched
+ * pattern.  Host-only (device tables are made on the first pm_count or
+ * pm_support); the plan keeps a reference to g (free plans first).  g may
+ * be NULL: the plan then serves pm_morph, pm_plan_matched and
+ * pm_plan_export only, and running it returns PM_EINVAL.
+ * Errors: PM_EINVAL (bad pattern, labels on an unlabeled graph),
+ * PM_EUNSUPPORTED, PM_ENOMEM. */
+pm_status pm_plan(const pm_graph *g, const pm_pattern *queries, int32_t nq, pm_op op,
+                  pm_morph_mode mode, pm_query_plan **out);
+pm_status pm_plan_get_info(const pm_query_plan *p, pm_plan_info *out);
+/* The matched (alternative) patterns, n_matched entries. */
+pm_status pm_plan_matched(const pm_query_plan *p, pm_pattern *out);
+void pm_free_plan(pm_query_plan *p);
+/* Copy the compiled matching plans (the device plan table, n_kernels_plans
+ * records of 96 bytes: int32 k, n_enum, tail, closed, counter, dom_base,
+ * n_columns, pad; then 8 levels of uint8 isect, diff, lt, gt, neq, int8
+ * label, uint8 column, pad) into out (cap bytes).  For inspection and tests;
+ * returns PM_EINVAL if cap is too small. */
+pm_status pm_plan_export(const pm_query_plan *p, void *out, int64_t cap);
+
+/* Section 4.1 step b for counting: requested[2*i..] = sum_j T[i][j] *
+ * matched[2*j..] modulo 2^128, where T holds the morph coefficients
+ * (c(p, q) = number of distinct copies of p spanning q, signed for
+ * vertex-from-edge).  matched: 2*n_matched words, requested: 2*n_queries.
+ * Pure host arithmetic, usable on its own. */
+pm_status pm_morph(const pm_query_plan *p, const uint64_t *matched, uint64_t *requested);
+
+/* Count every query pattern (distinct occurrences = matches / |Aut(p)|).
+ * Runs the matching kernels on `stream`, waits for them, applies pm_morph.
+ * counts: 2*n_queries words (128-bit, low word first).  matched (nullable):
+ * 2*n_matched words receiving the alternative set's raw counts.
+ * timeout_s <= 0 means no deadline; otherwise the kernels stop at the
+ * deadline and the call returns PM_ETIMEOUT. */
+pm_status pm_count(pm_query_plan *p, void *stream, double timeout_s, uint64_t *counts,
+                   uint64_t *matched);
+
+/* As pm_count, restricted to occurrences whose highest-ranked vertex —
+ * rank ordering vertices by (degree, caller id) — is one of the nroots
+ * caller vertex ids in roots[].  Summing over a partition of V gives
+ * pm_count's result, so sampled roots give exactly checkable partial counts. */
+pm_status pm_count_roots(pm_query_plan *p, void *stream, double timeout_s, const int32_t *roots,
+                         int64_t nroots, uint64_t *counts, uint64_t *matched);
+
+/* MNI support (Section 2, FSM) of every query of a PM_OP_SUPPORT plan:
+ * one column per orbit of the query's label-preserving automorphism group,
+ * holding the images of the orbit's vertices over all matches; support = the
+ * smallest column.  support: n_queries words; frequent (nullable): n_queries
+ * bytes, 1 when support >= threshold. */
+pm_status pm_support(pm_query_plan *p, void *stream, double timeout_s, uint64_t threshold,
+                     uint64_t *support, uint8_t *frequent);
+
+const char *pm_strerror(pm_status s);
+/* Text of the last error raised on the calling thread ("" if none). */
+const char *pm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PM_H */

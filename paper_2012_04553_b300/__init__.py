@@ -1,0 +1,286 @@
+"""Python binding of the B300 pattern-morphing library (libpm_b300.so).
+
+Argument marshalling only: every step (graph preparation, morph selection,
+plan compilation, matching, morph transform) runs inside the library, whose
+C ABI is include/pm.h.  The library must be built (python
+paper_2012_04553_b300/build.py); importing this package without it raises.
+PyTorch supplies device memory (through pm_set_allocator) and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpm_b300.so")
+
+PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_ETIMEOUT, PM_EOVERFLOW, PM_EUNSUPPORTED, PM_ECANCELLED = \
+    0, -1, -2, -3, -4, -5, -6, -7
+EDGE_INDUCED, VERTEX_INDUCED = 0, 1
+OP_COUNT, OP_SUPPORT = 0, 1
+MORPH_NONE, MORPH_NAIVE, MORPH_COST = 0, 1, 2
+MAX_K = 8
+
+
+class PMError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.pm_strerror(status).decode()
+        detail = _lib.pm_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status}){': ' + detail if detail else ''}")
+
+
+class PMTimeout(PMError):
+    pass
+
+
+class c_pattern(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("edge_mask", ctypes.c_uint32),
+                ("label", ctypes.c_int8 * MAX_K), ("induced", ctypes.c_int32)]
+
+
+class c_graph_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("self_loops", ctypes.c_int64),
+                ("duplicates", ctypes.c_int64), ("max_degree", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("labeled", ctypes.c_int32),
+                ("device", ctypes.c_int32)]
+
+
+class c_plan_info(ctypes.Structure):
+    _fields_ = [("n_queries", ctypes.c_int32), ("n_matched", ctypes.c_int32),
+                ("n_plans", ctypes.c_int32), ("op", ctypes.c_int32)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2012_04553_b300/build.py`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    sig = {
+        "pm_set_allocator": [vp, vp, vp],
+        "pm_load_graph": [i64, i64, vp, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)],
+        "pm_graph_get_info": [vp, ctypes.POINTER(c_graph_info)],
+        "pm_graph_vertex_order": [vp, vp],
+        "pm_plan": [vp, ctypes.POINTER(c_pattern), i32, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)],
+        "pm_plan_get_info": [vp, ctypes.POINTER(c_plan_info)],
+        "pm_plan_matched": [vp, ctypes.POINTER(c_pattern)],
+        "pm_morph": [vp, vp, vp],
+        "pm_count": [vp, vp, dbl, vp, vp],
+        "pm_count_roots": [vp, vp, dbl, vp, i64, vp, vp],
+        "pm_support": [vp, vp, dbl, ctypes.c_uint64, vp, vp],
+        "pm_plan_export": [vp, vp, i64],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.pm_free_graph.argtypes = [vp]
+    lib.pm_free_graph.restype = None
+    lib.pm_free_plan.argtypes = [vp]
+    lib.pm_free_plan.restype = None
+    lib.pm_strerror.argtypes = [ctypes.c_int]
+    lib.pm_strerror.restype = ctypes.c_char_p
+    lib.pm_last_error.argtypes = []
+    lib.pm_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+# Exported symbols of the C ABI (include/pm.h).
+ABI_SYMBOLS = [
+    "pm_set_allocator", "pm_load_graph", "pm_graph_get_info", "pm_graph_vertex_order",
+    "pm_free_graph", "pm_plan", "pm_plan_get_info", "pm_plan_matched", "pm_free_plan",
+    "pm_morph", "pm_count", "pm_count_roots", "pm_support", "pm_strerror", "pm_last_error",
+    "pm_plan_export",
+]
+
+
+def lib():
+    return _lib
+
+
+def _check(status, where):
+    if status != PM_OK:
+        raise (PMTimeout if status == PM_ETIMEOUT else PMError)(status, where)
+
+
+def _ptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+_torch_alloc_refs = None
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through torch's caching allocator."""
+    global _torch_alloc_refs
+    import torch
+
+    def alloc(nbytes, device, _ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(nbytes, device)
+        except Exception:
+            return None
+
+    def free(ptr, _nbytes, _device, _ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    refs = (_ALLOC_FN(alloc), _FREE_FN(free))
+    _check(_lib.pm_set_allocator(ctypes.cast(refs[0], ctypes.c_void_p),
+                                 ctypes.cast(refs[1], ctypes.c_void_p), None), "pm_set_allocator")
+    _torch_alloc_refs = refs
+
+
+def use_cuda_allocator():
+    global _torch_alloc_refs
+    _check(_lib.pm_set_allocator(None, None, None), "pm_set_allocator")
+    _torch_alloc_refs = None
+
+
+def make_pattern(k, edge_mask, induced=EDGE_INDUCED, labels=None):
+    p = c_pattern()
+    p.k = k
+    p.edge_mask = edge_mask
+    for u in range(MAX_K):
+        p.label[u] = -1 if labels is None or u >= k else int(labels[u])
+    p.induced = induced
+    return p
+
+
+def _words_to_ints(words):
+    w = np.asarray(words, dtype=np.uint64).reshape(-1, 2)
+    return [int(lo) | (int(hi) << 64) for lo, hi in w]
+
+
+class Graph:
+    """A data graph resident on one GPU (pm_load_graph)."""
+
+    def __init__(self, n, src, dst, labels=None, device=0, stream=None):
+        src = np.ascontiguousarray(src, dtype=np.int32)
+        dst = np.ascontiguousarray(dst, dtype=np.int32)
+        lab = None if labels is None else np.ascontiguousarray(labels, dtype=np.uint8)
+        h = ctypes.c_void_p()
+        _check(_lib.pm_load_graph(int(n), len(src), _ptr(src), _ptr(dst), _ptr(lab), int(device),
+                                  _stream_handle(stream), ctypes.byref(h)), "pm_load_graph")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        i = c_graph_info()
+        _check(_lib.pm_graph_get_info(self._h, ctypes.byref(i)), "pm_graph_get_info")
+        return {f: getattr(i, f) for f, _ in c_graph_info._fields_}
+
+    def vertex_order(self):
+        n = self.info()["n"]
+        out = np.empty(n, dtype=np.int32)
+        _check(_lib.pm_graph_vertex_order(self._h, _ptr(out)), "pm_graph_vertex_order")
+        return out
+
+    def free(self):
+        if self._h:
+            _lib.pm_free_graph(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Plan:
+    """A planned query set (pm_plan): morph selection plus matching plans."""
+
+    def __init__(self, graph, patterns, op=OP_COUNT, mode=MORPH_NAIVE):
+        """graph may be None: the plan then only serves morph() / export_plans()."""
+        arr = (c_pattern * len(patterns))(*patterns)
+        h = ctypes.c_void_p()
+        _check(_lib.pm_plan(None if graph is None else graph.handle, arr, len(patterns), op, mode,
+                            ctypes.byref(h)), "pm_plan")
+        self._h = h
+        self.graph = graph      # keep the graph alive while the plan lives
+        i = c_plan_info()
+        _check(_lib.pm_plan_get_info(self._h, ctypes.byref(i)), "pm_plan_get_info")
+        self.n_queries, self.n_matched, self.n_plans = i.n_queries, i.n_matched, i.n_plans
+
+    def matched_patterns(self):
+        arr = (c_pattern * self.n_matched)()
+        _check(_lib.pm_plan_matched(self._h, arr), "pm_plan_matched")
+        return [(p.k, p.edge_mask, p.induced, list(p.label)[:p.k]) for p in arr]
+
+    def export_plans(self):
+        """The compiled plan table as a numpy structured array (see pm_plan_export)."""
+        level = np.dtype([("isect", "u1"), ("diff", "u1"), ("lt", "u1"), ("gt", "u1"),
+                          ("neq", "u1"), ("label", "i1"), ("column", "u1"), ("pad", "u1")])
+        rec = np.dtype([("k", "<i4"), ("n_enum", "<i4"), ("tail", "<i4"), ("closed", "<i4"),
+                        ("counter", "<i4"), ("dom_base", "<i4"), ("n_columns", "<i4"),
+                        ("pad", "<i4"), ("lv", level, (8,))])
+        out = np.zeros(self.n_plans, dtype=rec)
+        _check(_lib.pm_plan_export(self._h, _ptr(out), out.nbytes), "pm_plan_export")
+        return out
+
+    def morph(self, matched_counts):
+        m = np.zeros(2 * self.n_matched, dtype=np.uint64)
+        for j, v in enumerate(matched_counts):
+            v %= 1 << 128
+            m[2 * j], m[2 * j + 1] = v & ((1 << 64) - 1), v >> 64
+        out = np.zeros(2 * self.n_queries, dtype=np.uint64)
+        _check(_lib.pm_morph(self._h, _ptr(m), _ptr(out)), "pm_morph")
+        return _words_to_ints(out)
+
+    def count(self, stream=None, timeout_s=0.0, with_matched=False):
+        out = np.zeros(2 * self.n_queries, dtype=np.uint64)
+        mat = np.zeros(2 * self.n_matched, dtype=np.uint64)
+        _check(_lib.pm_count(self._h, _stream_handle(stream), float(timeout_s), _ptr(out), _ptr(mat)),
+               "pm_count")
+        return (_words_to_ints(out), _words_to_ints(mat)) if with_matched else _words_to_ints(out)
+
+    def count_roots(self, roots, stream=None, timeout_s=0.0, with_matched=False):
+        r = np.ascontiguousarray(roots, dtype=np.int32)
+        out = np.zeros(2 * self.n_queries, dtype=np.uint64)
+        mat = np.zeros(2 * self.n_matched, dtype=np.uint64)
+        _check(_lib.pm_count_roots(self._h, _stream_handle(stream), float(timeout_s), _ptr(r), len(r),
+                                   _ptr(out), _ptr(mat)), "pm_count_roots")
+        return (_words_to_ints(out), _words_to_ints(mat)) if with_matched else _words_to_ints(out)
+
+    def support(self, threshold=0, stream=None, timeout_s=0.0):
+        sup = np.zeros(self.n_queries, dtype=np.uint64)
+        freq = np.zeros(self.n_queries, dtype=np.uint8)
+        _check(_lib.pm_support(self._h, _stream_handle(stream), float(timeout_s), int(threshold),
+                               _ptr(sup), _ptr(freq)), "pm_support")
+        return [int(x) for x in sup], [bool(x) for x in freq]
+
+    def free(self):
+        if self._h:
+            _lib.pm_free_plan(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -1,0 +1,566 @@
+// C ABI (include/pm.h): argument checking, plan ownership, device buffers,
+// launches and the host half of the morph transform.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "internal.hpp"
+
+namespace pm {
+
+pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_t *dst,
+                      const uint8_t *labels, int device, void *stream, pm_graph **out);
+
+namespace {
+thread_local std::string g_last_error;
+std::mutex g_alloc_mu;
+pm_alloc_fn g_alloc = nullptr;
+pm_free_fn g_free = nullptr;
+void *g_alloc_ctx = nullptr;
+}  // namespace
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+void *dev_alloc(size_t bytes, int device) {
+    if (bytes == 0) bytes = 256;
+    pm_alloc_fn a;
+    void *ctx;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        a = g_alloc;
+        ctx = g_alloc_ctx;
+    }
+    if (a) return a(bytes, device, ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(void *ptr, size_t bytes, int device) {
+    if (!ptr) return;
+    if (bytes == 0) bytes = 256;
+    pm_free_fn f;
+    void *ctx;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        f = g_free;
+        ctx = g_alloc_ctx;
+    }
+    if (f) f(ptr, bytes, device, ctx);
+    else cudaFree(ptr);
+}
+
+}  // namespace pm
+
+using namespace pm;
+
+struct pm_query_plan {
+    const pm_graph *g = nullptr;
+    pm_op op = PM_OP_COUNT;
+    MorphPlan morph;
+    std::vector<DevPlan> plans;
+    DevPlan *d_plans = nullptr;
+    uint64_t *d_counters = nullptr;
+    Control *d_ctl = nullptr;
+    // MNI
+    int n_bitsets = 0;
+    int64_t words = 0;
+    uint32_t *d_bitsets = nullptr;
+    std::vector<int32_t> col_off, col_src;   // per query column: sources (bitset ids)
+    std::vector<int> query_col_base;         // first query column of each query
+    int32_t *d_col_off = nullptr, *d_col_src = nullptr;
+    unsigned long long *d_popc = nullptr;
+    std::vector<int> dom_base;               // per matched pattern
+    size_t bytes_plans = 0, bytes_counters = 0, bytes_bitsets = 0, bytes_cols = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = 0;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() { cudaSetDevice(prev); }
+};
+
+pm_status cuda_fail(const char *what, cudaError_t e) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return PM_ECUDA;
+}
+
+pm_status to_pat(const pm_pattern &q, bool graph_labeled, Pat *out) {
+    if (q.k < 2 || q.k > PM_MAX_K) {
+        set_error("pattern: k must be in [2, 8]");
+        return PM_EINVAL;
+    }
+    const int npairs = q.k * (q.k - 1) / 2;
+    if (npairs < 32 && (q.edge_mask >> npairs)) {
+        set_error("pattern: edge_mask has bits beyond the k*(k-1)/2 pairs");
+        return PM_EINVAL;
+    }
+    if (q.induced != PM_EDGE_INDUCED && q.induced != PM_VERTEX_INDUCED) {
+        set_error("pattern: induced must be PM_EDGE_INDUCED or PM_VERTEX_INDUCED");
+        return PM_EINVAL;
+    }
+    Pat p = Pat::from_mask(q.k, q.edge_mask, q.label, q.induced == PM_VERTEX_INDUCED);
+    for (int u = 0; u < q.k; u++) {
+        if (q.label[u] < -1) {
+            set_error("pattern: label must be -1 (any) or a label value in [0, 127]");
+            return PM_EINVAL;
+        }
+    }
+    if (!p.connected()) {
+        set_error("pattern: not connected (Section 2 requires connected patterns)");
+        return PM_EINVAL;
+    }
+    if (p.labeled() && !graph_labeled) {
+        set_error("pattern: labeled pattern on an unlabeled graph");
+        return PM_EINVAL;
+    }
+    *out = p;
+    return PM_OK;
+}
+
+void free_plan_device(pm_query_plan *p) {
+    const int dev = p->g ? p->g->device : 0;
+    dev_free(p->d_plans, p->bytes_plans, dev);
+    dev_free(p->d_counters, p->bytes_counters, dev);
+    dev_free(p->d_ctl, sizeof(Control), dev);
+    dev_free(p->d_bitsets, p->bytes_bitsets, dev);
+    dev_free(p->d_col_off, p->bytes_cols, dev);
+    dev_free(p->d_col_src, p->bytes_cols, dev);
+    dev_free(p->d_popc, p->bytes_cols, dev);
+    p->d_plans = nullptr;
+    p->d_counters = nullptr;
+    p->d_ctl = nullptr;
+    p->d_bitsets = nullptr;
+    p->d_col_off = p->d_col_src = nullptr;
+    p->d_popc = nullptr;
+}
+
+// Root list in internal ids with its oriented-edge offsets, on the device.
+struct RootTasks {
+    int32_t *d_roots = nullptr;
+    int64_t *d_off = nullptr;
+    size_t b_roots = 0, b_off = 0;
+    int device = 0;
+    ~RootTasks() {
+        dev_free(d_roots, b_roots, device);
+        dev_free(d_off, b_off, device);
+    }
+};
+
+pm_status make_tasks(const pm_query_plan *p, const int32_t *roots, int64_t nroots, cudaStream_t s,
+                     RootTasks &rt, DevTasks *out) {
+    const pm_graph *g = p->g;
+    if (!roots) {
+        *out = DevTasks{nullptr, g->d_off, g->n, 0};
+        int64_t total = 0;
+        for (int64_t v = 0; v < g->n; v++) total += g->lowdeg[v];
+        out->ntasks = total;
+        return PM_OK;
+    }
+    std::vector<int32_t> ids(nroots);
+    std::vector<int64_t> off(nroots + 1, 0);
+    for (int64_t i = 0; i < nroots; i++) {
+        if (roots[i] < 0 || roots[i] >= g->n) {
+            set_error("pm_count_roots: root id outside [0, n)");
+            return PM_EINVAL;
+        }
+        ids[i] = g->new_id[roots[i]];
+        off[i + 1] = off[i] + g->lowdeg[ids[i]];
+    }
+    rt.device = g->device;
+    rt.b_roots = sizeof(int32_t) * std::max<int64_t>(nroots, 1);
+    rt.b_off = sizeof(int64_t) * (nroots + 1);
+    rt.d_roots = (int32_t *)dev_alloc(rt.b_roots, g->device);
+    rt.d_off = (int64_t *)dev_alloc(rt.b_off, g->device);
+    if (!rt.d_roots || !rt.d_off) {
+        set_error("pm_count_roots: device allocation failed");
+        return PM_ENOMEM;
+    }
+    cudaError_t e1 = nroots ? cudaMemcpyAsync(rt.d_roots, ids.data(), sizeof(int32_t) * nroots,
+                                              cudaMemcpyHostToDevice, s) : cudaSuccess;
+    cudaError_t e2 = cudaMemcpyAsync(rt.d_off, off.data(), rt.b_off, cudaMemcpyHostToDevice, s);
+    if (e1 || e2) return cuda_fail("pm_count_roots: upload", e1 ? e1 : e2);
+    *out = DevTasks{rt.d_roots, rt.d_off, nroots, off[nroots]};
+    return PM_OK;
+}
+
+void u128_from_words(const uint64_t *w, unsigned __int128 *v) {
+    *v = (unsigned __int128)w[0] | ((unsigned __int128)w[1] << 64);
+}
+
+// Device buffers of a plan, made on first use (pm_plan itself is host-only).
+pm_status ensure_device(pm_query_plan *p) {
+    const pm_graph *g = p->g;
+    if (!g) {
+        set_error("plan was made without a graph; it cannot run");
+        return PM_EINVAL;
+    }
+    if (p->d_plans) return PM_OK;
+    const size_t nm = p->morph.matched.size();
+    p->bytes_plans = sizeof(DevPlan) * std::max<size_t>(p->plans.size(), 1);
+    p->bytes_counters = sizeof(uint64_t) * 2 * std::max<size_t>(nm, 1);
+    p->d_plans = (DevPlan *)dev_alloc(p->bytes_plans, g->device);
+    p->d_counters = (uint64_t *)dev_alloc(p->bytes_counters, g->device);
+    p->d_ctl = (Control *)dev_alloc(sizeof(Control), g->device);
+    if (!p->d_plans || !p->d_counters || !p->d_ctl) {
+        set_error("device allocation failed (plan tables)");
+        free_plan_device(p);
+        return PM_ENOMEM;
+    }
+    cudaError_t e = cudaMemcpy(p->d_plans, p->plans.data(), sizeof(DevPlan) * p->plans.size(),
+                               cudaMemcpyHostToDevice);
+    if (!e && p->op == PM_OP_SUPPORT) {
+        p->words = (g->n + 31) / 32;
+        p->bytes_bitsets = sizeof(uint32_t) * size_t(p->words) * std::max(p->n_bitsets, 1);
+        p->bytes_cols = sizeof(int64_t) * std::max(p->col_off.size(), p->col_src.size()) + 64;
+        p->d_bitsets = (uint32_t *)dev_alloc(p->bytes_bitsets, g->device);
+        p->d_col_off = (int32_t *)dev_alloc(p->bytes_cols, g->device);
+        p->d_col_src = (int32_t *)dev_alloc(p->bytes_cols, g->device);
+        p->d_popc = (unsigned long long *)dev_alloc(p->bytes_cols, g->device);
+        if (!p->d_bitsets || !p->d_col_off || !p->d_col_src || !p->d_popc) {
+            set_error("device allocation failed (MNI bitsets)");
+            free_plan_device(p);
+            return PM_ENOMEM;
+        }
+        e = cudaMemcpy(p->d_col_off, p->col_off.data(), sizeof(int32_t) * p->col_off.size(),
+                       cudaMemcpyHostToDevice);
+        if (!e && !p->col_src.empty())
+            e = cudaMemcpy(p->d_col_src, p->col_src.data(), sizeof(int32_t) * p->col_src.size(),
+                           cudaMemcpyHostToDevice);
+    }
+    if (e) {
+        free_plan_device(p);
+        return cuda_fail("plan upload", e);
+    }
+    return PM_OK;
+}
+
+pm_status run_count(pm_query_plan *p, void *stream, double timeout_s, const int32_t *roots,
+                    int64_t nroots, uint64_t *counts, uint64_t *matched) {
+    if (!p || !counts) {
+        set_error("pm_count: null argument");
+        return PM_EINVAL;
+    }
+    if (p->op != PM_OP_COUNT) {
+        set_error("pm_count: plan was made for PM_OP_SUPPORT");
+        return PM_EINVAL;
+    }
+    const pm_graph *g = p->g;
+    if (!g) {
+        set_error("pm_count: plan was made without a graph");
+        return PM_EINVAL;
+    }
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return PM_ECUDA;
+    pm_status st = ensure_device(p);
+    if (st != PM_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    RootTasks rt;
+    DevTasks tasks;
+    st = make_tasks(p, roots, nroots, s, rt, &tasks);
+    if (st != PM_OK) return st;
+    const size_t nm = p->morph.matched.size();
+    cudaError_t e = cudaMemsetAsync(p->d_counters, 0, p->bytes_counters, s);
+    if (e) return cuda_fail("pm_count: memset", e);
+    const uint64_t budget = timeout_s > 0 ? uint64_t(timeout_s * 1e9) : 0;
+    if (launch_arm(p->d_ctl, budget, stream)) return PM_ECUDA;
+    if (tasks.ntasks > 0 && !p->plans.empty()) {
+        if (launch_count(g->dev(), p->d_plans, int(p->plans.size()), tasks, p->d_counters,
+                         p->d_ctl, stream))
+            return PM_ECUDA;
+    }
+    std::vector<uint64_t> raw(2 * nm);
+    Control ctl;
+    e = cudaMemcpyAsync(raw.data(), p->d_counters, sizeof(uint64_t) * 2 * nm,
+                        cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(&ctl, p->d_ctl, sizeof(Control), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail("pm_count: kernel or readback", e);
+    if (ctl.status == 1) {
+        set_error("pm_count: deadline expired");
+        return PM_ETIMEOUT;
+    }
+    if (matched) std::memcpy(matched, raw.data(), sizeof(uint64_t) * 2 * nm);
+    return pm_morph(p, raw.data(), counts);
+}
+
+}  // namespace
+
+extern "C" {
+
+pm_status pm_set_allocator(pm_alloc_fn alloc, pm_free_fn release, void *ctx) {
+    if ((alloc == nullptr) != (release == nullptr)) {
+        set_error("pm_set_allocator: set both callbacks or neither");
+        return PM_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = alloc;
+    g_free = release;
+    g_alloc_ctx = ctx;
+    return PM_OK;
+}
+
+pm_status pm_load_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_t *dst,
+                        const uint8_t *labels, int device, void *stream, pm_graph **out) {
+    return build_graph(n, m_raw, src, dst, labels, device, stream, out);
+}
+
+pm_status pm_graph_get_info(const pm_graph *g, pm_graph_info *out) {
+    if (!g || !out) return PM_EINVAL;
+    out->n = g->n;
+    out->m = g->m;
+    out->self_loops = g->self_loops;
+    out->duplicates = g->duplicates;
+    out->max_degree = g->max_degree;
+    out->device_bytes = int64_t(g->bytes);
+    out->labeled = g->labeled;
+    out->device = g->device;
+    return PM_OK;
+}
+
+pm_status pm_graph_vertex_order(const pm_graph *g, int32_t *new_id) {
+    if (!g || !new_id) return PM_EINVAL;
+    std::memcpy(new_id, g->new_id.data(), sizeof(int32_t) * g->n);
+    return PM_OK;
+}
+
+void pm_free_graph(pm_graph *g) {
+    if (!g) return;
+    DeviceGuard dg(g->device);
+    const size_t b_rp = sizeof(int64_t) * (g->n + 1);
+    dev_free(g->d_rowptr, b_rp, g->device);
+    dev_free(g->d_col, sizeof(int32_t) * std::max<int64_t>(2 * g->m, 1), g->device);
+    dev_free(g->d_off, b_rp, g->device);
+    dev_free(g->d_labels, g->n, g->device);
+    delete g;
+}
+
+pm_status pm_plan(const pm_graph *g, const pm_pattern *queries, int32_t nq, pm_op op,
+                  pm_morph_mode mode, pm_query_plan **out) {
+    if (!queries || nq < 1 || !out) {
+        set_error("pm_plan: null argument or empty query set");
+        return PM_EINVAL;
+    }
+    if (op != PM_OP_COUNT && op != PM_OP_SUPPORT) {
+        set_error("pm_plan: unknown op");
+        return PM_EINVAL;
+    }
+    if (mode != PM_MORPH_NONE && mode != PM_MORPH_NAIVE && mode != PM_MORPH_COST) {
+        set_error("pm_plan: unknown morph mode");
+        return PM_EINVAL;
+    }
+    std::vector<Pat> pats(nq);
+    for (int32_t i = 0; i < nq; i++) {
+        pm_status st = to_pat(queries[i], g ? g->labeled : true, &pats[i]);
+        if (st != PM_OK) return st;
+        if (op == PM_OP_SUPPORT && pats[i].k > 6) {
+            set_error("pm_plan: MNI support handles patterns of at most 6 vertices");
+            return PM_EUNSUPPORTED;
+        }
+    }
+    auto *p = new (std::nothrow) pm_query_plan();
+    if (!p) return PM_ENOMEM;
+    p->g = g;
+    p->op = op;
+    std::string why;
+    pm_status st = morph_select(pats, op, mode, p->morph, &why);
+    if (st != PM_OK) {
+        set_error("pm_plan: " + why);
+        delete p;
+        return st;
+    }
+    const size_t nm = p->morph.matched.size();
+    p->dom_base.assign(nm, 0);
+    int nb = 0;
+    for (size_t j = 0; j < nm; j++) {
+        p->dom_base[j] = nb;
+        nb += p->morph.matched_columns[j];
+    }
+    p->n_bitsets = nb;
+    for (size_t j = 0; j < nm; j++) {
+        auto v = compile_plans(p->morph.matched[j], int(j), p->dom_base[j],
+                               p->morph.matched_orbit[j]);
+        p->plans.insert(p->plans.end(), v.begin(), v.end());
+    }
+    if (op == PM_OP_SUPPORT) {
+        // query columns -> bitset sources
+        p->col_off.push_back(0);
+        for (size_t i = 0; i < p->morph.mni_sources.size(); i++) {
+            p->query_col_base.push_back(int(p->col_off.size()) - 1);
+            for (auto &srcs : p->morph.mni_sources[i]) {
+                for (auto &pr : srcs) p->col_src.push_back(p->dom_base[pr.first] + pr.second);
+                p->col_off.push_back(int32_t(p->col_src.size()));
+            }
+        }
+    }
+    *out = p;
+    return PM_OK;
+}
+
+pm_status pm_plan_get_info(const pm_query_plan *p, pm_plan_info *out) {
+    if (!p || !out) return PM_EINVAL;
+    out->n_queries = int32_t(p->morph.queries.size());
+    out->n_matched = int32_t(p->morph.matched.size());
+    out->n_kernels_plans = int32_t(p->plans.size());
+    out->op = p->op;
+    return PM_OK;
+}
+
+pm_status pm_plan_matched(const pm_query_plan *p, pm_pattern *out) {
+    if (!p || !out) return PM_EINVAL;
+    for (size_t j = 0; j < p->morph.matched.size(); j++) {
+        const Pat &q = p->morph.matched[j];
+        pm_pattern r{};
+        r.k = q.k;
+        r.edge_mask = q.mask();
+        for (int u = 0; u < PM_MAX_K; u++) r.label[u] = u < q.k ? q.lab[u] : -1;
+        r.induced = q.vi ? PM_VERTEX_INDUCED : PM_EDGE_INDUCED;
+        out[j] = r;
+    }
+    return PM_OK;
+}
+
+pm_status pm_plan_export(const pm_query_plan *p, void *out, int64_t cap) {
+    static_assert(sizeof(DevPlan) == 96, "plan record layout is part of the ABI");
+    if (!p || !out) return PM_EINVAL;
+    const int64_t need = int64_t(sizeof(DevPlan) * p->plans.size());
+    if (cap < need) {
+        set_error("pm_plan_export: buffer too small");
+        return PM_EINVAL;
+    }
+    std::memcpy(out, p->plans.data(), size_t(need));
+    return PM_OK;
+}
+
+void pm_free_plan(pm_query_plan *p) {
+    if (!p) return;
+    if (p->g && p->d_plans) {
+        DeviceGuard dg(p->g->device);
+        free_plan_device(p);
+    }
+    delete p;
+}
+
+pm_status pm_morph(const pm_query_plan *p, const uint64_t *matched, uint64_t *requested) {
+    if (!p || !matched || !requested) return PM_EINVAL;
+    for (size_t i = 0; i < p->morph.terms.size(); i++) {
+        unsigned __int128 acc = 0;
+        for (const Term &t : p->morph.terms[i]) {
+            unsigned __int128 v;
+            u128_from_words(matched + 2 * t.matched, &v);
+            acc += (unsigned __int128)(__int128)t.coef * v;   // arithmetic modulo 2^128
+        }
+        requested[2 * i] = uint64_t(acc);
+        requested[2 * i + 1] = uint64_t(acc >> 64);
+    }
+    return PM_OK;
+}
+
+pm_status pm_count(pm_query_plan *p, void *stream, double timeout_s, uint64_t *counts,
+                   uint64_t *matched) {
+    return run_count(p, stream, timeout_s, nullptr, 0, counts, matched);
+}
+
+pm_status pm_count_roots(pm_query_plan *p, void *stream, double timeout_s, const int32_t *roots,
+                         int64_t nroots, uint64_t *counts, uint64_t *matched) {
+    if (!roots && nroots > 0) {
+        set_error("pm_count_roots: null roots");
+        return PM_EINVAL;
+    }
+    if (nroots < 0) return PM_EINVAL;
+    static const int32_t none = 0;
+    return run_count(p, stream, timeout_s, roots ? roots : &none, nroots, counts, matched);
+}
+
+pm_status pm_support(pm_query_plan *p, void *stream, double timeout_s, uint64_t threshold,
+                     uint64_t *support, uint8_t *frequent) {
+    if (!p || !support) {
+        set_error("pm_support: null argument");
+        return PM_EINVAL;
+    }
+    if (p->op != PM_OP_SUPPORT) {
+        set_error("pm_support: plan was made for PM_OP_COUNT");
+        return PM_EINVAL;
+    }
+    const pm_graph *g = p->g;
+    if (!g) {
+        set_error("pm_support: plan was made without a graph");
+        return PM_EINVAL;
+    }
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return PM_ECUDA;
+    pm_status st = ensure_device(p);
+    if (st != PM_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    RootTasks rt;
+    DevTasks tasks;
+    st = make_tasks(p, nullptr, 0, s, rt, &tasks);
+    if (st != PM_OK) return st;
+    const size_t ncols = p->col_off.size() - 1;
+    cudaError_t e = cudaMemsetAsync(p->d_bitsets, 0, p->bytes_bitsets, s);
+    if (!e) e = cudaMemsetAsync(p->d_popc, 0, sizeof(unsigned long long) * std::max<size_t>(ncols, 1), s);
+    if (e) return cuda_fail("pm_support: memset", e);
+    const uint64_t budget = timeout_s > 0 ? uint64_t(timeout_s * 1e9) : 0;
+    if (launch_arm(p->d_ctl, budget, stream)) return PM_ECUDA;
+    if (tasks.ntasks > 0 && !p->plans.empty()) {
+        if (launch_domains(g->dev(), p->d_plans, int(p->plans.size()), tasks, p->d_bitsets,
+                           p->words, p->d_ctl, stream))
+            return PM_ECUDA;
+    }
+    if (launch_mni_reduce(p->d_bitsets, p->words, p->d_col_off, p->d_col_src, int(ncols),
+                          p->d_popc, stream))
+        return PM_ECUDA;
+    std::vector<unsigned long long> popc(ncols);
+    Control ctl;
+    e = ncols ? cudaMemcpyAsync(popc.data(), p->d_popc, sizeof(unsigned long long) * ncols,
+                                cudaMemcpyDeviceToHost, s) : cudaSuccess;
+    if (!e) e = cudaMemcpyAsync(&ctl, p->d_ctl, sizeof(Control), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail("pm_support: kernel or readback", e);
+    if (ctl.status == 1) {
+        set_error("pm_support: deadline expired");
+        return PM_ETIMEOUT;
+    }
+    const size_t nq = p->morph.queries.size();
+    for (size_t i = 0; i < nq; i++) {
+        const int c0 = p->query_col_base[i];
+        const int c1 = (i + 1 < nq) ? p->query_col_base[i + 1] : int(ncols);
+        uint64_t best = UINT64_MAX;
+        for (int c = c0; c < c1; c++) best = std::min<uint64_t>(best, popc[c]);
+        support[i] = best == UINT64_MAX ? 0 : best;
+        if (frequent) frequent[i] = support[i] >= threshold ? 1 : 0;
+    }
+    return PM_OK;
+}
+
+const char *pm_strerror(pm_status s) {
+    switch (s) {
+        case PM_OK: return "ok";
+        case PM_EINVAL: return "invalid argument";
+        case PM_ENOMEM: return "out of memory";
+        case PM_ECUDA: return "CUDA error";
+        case PM_ETIMEOUT: return "deadline expired";
+        case PM_EOVERFLOW: return "result does not fit the output width";
+        case PM_EUNSUPPORTED: return "unsupported request";
+        case PM_ECANCELLED: return "cancelled";
+    }
+    return "unknown status";
+}
+
+const char *pm_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

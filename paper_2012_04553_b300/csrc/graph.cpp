@@ -1,0 +1,166 @@
+// Graph preparation (host) and upload: clean an undirected edge list, order
+// vertices by (degree, caller id), build a CSR with sorted rows, and copy it
+// to the device.  Every step is O(m) bucketing plus per-row sorts, spread
+// over the host's cores.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "internal.hpp"
+
+namespace pm {
+
+namespace {
+
+template <class F>
+void parallel_for(int64_t n, F f) {
+    unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    if (n < 100000) nt = 1;
+    std::vector<std::thread> th;
+    std::atomic<int64_t> next{0};
+    const int64_t grain = 4096;
+    auto body = [&]() {
+        for (;;) {
+            int64_t b = next.fetch_add(grain);
+            if (b >= n) break;
+            int64_t e = std::min(n, b + grain);
+            for (int64_t i = b; i < e; i++) f(i);
+        }
+    };
+    for (unsigned t = 1; t < nt; t++) th.emplace_back(body);
+    body();
+    for (auto &t : th) t.join();
+}
+
+}  // namespace
+
+pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_t *dst,
+                      const uint8_t *labels, int device, void *stream, pm_graph **out) {
+    if (!out || n < 1 || n > INT32_MAX || m_raw < 0 || (m_raw > 0 && (!src || !dst))) {
+        set_error("pm_load_graph: invalid argument");
+        return PM_EINVAL;
+    }
+    for (int64_t i = 0; i < m_raw; i++) {
+        if (src[i] < 0 || src[i] >= n || dst[i] < 0 || dst[i] >= n) {
+            set_error("pm_load_graph: edge " + std::to_string(i) + " has a vertex id outside [0, n)");
+            return PM_EINVAL;
+        }
+    }
+    auto *g = new (std::nothrow) pm_graph();
+    if (!g) return PM_ENOMEM;
+    g->device = device;
+    g->n = n;
+    g->labeled = labels != nullptr;
+    try {
+        // 1. bucket both directions by source, dropping self-loops
+        std::vector<int64_t> rp(n + 1, 0);
+        int64_t loops = 0;
+        for (int64_t i = 0; i < m_raw; i++) {
+            if (src[i] == dst[i]) { loops++; continue; }
+            rp[src[i] + 1]++;
+            rp[dst[i] + 1]++;
+        }
+        for (int64_t v = 0; v < n; v++) rp[v + 1] += rp[v];
+        std::vector<int32_t> adj(rp[n]);
+        {
+            std::vector<int64_t> fill(rp.begin(), rp.end() - 1);
+            for (int64_t i = 0; i < m_raw; i++) {
+                if (src[i] == dst[i]) continue;
+                adj[fill[src[i]]++] = dst[i];
+                adj[fill[dst[i]]++] = src[i];
+            }
+        }
+        // 2. sort and deduplicate each row
+        std::vector<int64_t> deg(n);
+        parallel_for(n, [&](int64_t v) {
+            int32_t *b = adj.data() + rp[v], *e = adj.data() + rp[v + 1];
+            std::sort(b, e);
+            deg[v] = std::unique(b, e) - b;
+        });
+        int64_t nnz = 0, maxd = 0;
+        for (int64_t v = 0; v < n; v++) { nnz += deg[v]; maxd = std::max(maxd, deg[v]); }
+        g->m = nnz / 2;
+        g->self_loops = loops;
+        g->duplicates = (m_raw - loops) - g->m;
+        g->max_degree = maxd;
+        // 3. order by (degree, id): counting sort on degree, stable in id
+        std::vector<int64_t> cnt(maxd + 2, 0);
+        for (int64_t v = 0; v < n; v++) cnt[deg[v] + 1]++;
+        for (int64_t d = 0; d <= maxd; d++) cnt[d + 1] += cnt[d];
+        g->new_id.assign(n, 0);
+        std::vector<int32_t> old_of(n);
+        for (int64_t v = 0; v < n; v++) {
+            int64_t r = cnt[deg[v]]++;
+            g->new_id[v] = int32_t(r);
+            old_of[r] = int32_t(v);
+        }
+        // 4. CSR in internal ids, rows sorted
+        std::vector<int64_t> rowptr(n + 1, 0);
+        for (int64_t r = 0; r < n; r++) rowptr[r + 1] = rowptr[r] + deg[old_of[r]];
+        std::vector<int32_t> col(nnz);
+        g->lowdeg.assign(n, 0);
+        parallel_for(n, [&](int64_t r) {
+            const int64_t v = old_of[r];
+            int32_t *o = col.data() + rowptr[r];
+            const int64_t d = deg[v];
+            for (int64_t i = 0; i < d; i++) o[i] = g->new_id[adj[rp[v] + i]];
+            std::sort(o, o + d);
+            g->lowdeg[r] = int32_t(std::lower_bound(o, o + d, int32_t(r)) - o);
+        });
+        if (labels) {
+            g->labels.resize(n);
+            for (int64_t r = 0; r < n; r++) g->labels[r] = labels[old_of[r]];
+        }
+        // 5. task offsets for the implicit root list n-1, ..., 0
+        std::vector<int64_t> off(n + 1, 0);
+        for (int64_t i = 0; i < n; i++) off[i + 1] = off[i] + g->lowdeg[n - 1 - i];
+
+        // 6. upload
+        int prev = 0;
+        cudaGetDevice(&prev);
+        if (cudaSetDevice(device) != cudaSuccess) {
+            set_error("pm_load_graph: cudaSetDevice failed");
+            delete g;
+            return PM_ECUDA;
+        }
+        cudaStream_t s = (cudaStream_t)stream;
+        const size_t b_rp = sizeof(int64_t) * (n + 1), b_col = sizeof(int32_t) * std::max<int64_t>(nnz, 1);
+        g->d_rowptr = (int64_t *)dev_alloc(b_rp, device);
+        g->d_col = (int32_t *)dev_alloc(b_col, device);
+        g->d_off = (int64_t *)dev_alloc(b_rp, device);
+        if (labels) g->d_labels = (uint8_t *)dev_alloc(n, device);
+        if (!g->d_rowptr || !g->d_col || !g->d_off || (labels && !g->d_labels)) {
+            set_error("pm_load_graph: device allocation failed");
+            pm_free_graph(g);
+            cudaSetDevice(prev);
+            return PM_ENOMEM;
+        }
+        g->bytes = 2 * b_rp + b_col + (labels ? n : 0);
+        cudaError_t e1 = cudaMemcpyAsync(g->d_rowptr, rowptr.data(), b_rp, cudaMemcpyHostToDevice, s);
+        cudaError_t e2 = nnz ? cudaMemcpyAsync(g->d_col, col.data(), sizeof(int32_t) * nnz,
+                                               cudaMemcpyHostToDevice, s) : cudaSuccess;
+        cudaError_t e3 = cudaMemcpyAsync(g->d_off, off.data(), b_rp, cudaMemcpyHostToDevice, s);
+        cudaError_t e4 = labels ? cudaMemcpyAsync(g->d_labels, g->labels.data(), n,
+                                                  cudaMemcpyHostToDevice, s) : cudaSuccess;
+        cudaError_t e5 = cudaStreamSynchronize(s);
+        cudaSetDevice(prev);
+        if (e1 || e2 || e3 || e4 || e5) {
+            set_error(std::string("pm_load_graph: upload failed: ") +
+                      cudaGetErrorString(e5 ? e5 : (e1 ? e1 : (e2 ? e2 : (e3 ? e3 : e4)))));
+            pm_free_graph(g);
+            return PM_ECUDA;
+        }
+    } catch (const std::bad_alloc &) {
+        set_error("pm_load_graph: host allocation failed");
+        pm_free_graph(g);
+        return PM_ENOMEM;
+    }
+    *out = g;
+    return PM_OK;
+}
+
+}  // namespace pm

@@ -1,0 +1,77 @@
+// Library-internal host structures behind the opaque handles of pm.h.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pm.h"
+#include "pattern.hpp"
+#include "plan.hpp"
+
+struct pm_graph {
+    int device = 0;
+    int64_t n = 0, m = 0, self_loops = 0, duplicates = 0, max_degree = 0;
+    bool labeled = false;
+    std::vector<int32_t> new_id;     // caller id -> internal id
+    std::vector<int32_t> lowdeg;     // internal id -> neighbours with smaller internal id
+    std::vector<uint8_t> labels;     // internal id -> label (labeled graphs)
+    int64_t *d_rowptr = nullptr;
+    int32_t *d_col = nullptr;
+    uint8_t *d_labels = nullptr;
+    int64_t *d_off = nullptr;        // task offsets for the implicit all-roots list
+    size_t bytes = 0;
+    pm::DevGraph dev() const {
+        return pm::DevGraph{n, 2 * m, d_rowptr, d_col, d_labels};
+    }
+};
+
+namespace pm {
+
+// One query's result as a signed combination of matched-pattern results
+// (counting), or for MNI as, per query column, the matched bitsets to OR.
+struct Term {
+    int matched;
+    int64_t coef;
+};
+
+struct MorphPlan {
+    std::vector<Pat> queries;
+    std::vector<Pat> matched;
+    std::vector<std::vector<Term>> terms;            // counting: per query
+    // MNI (support plans)
+    std::vector<int> matched_columns;                // per matched pattern: number of orbits
+    std::vector<std::vector<int>> matched_orbit;     // per matched pattern: column of each vertex
+    std::vector<std::vector<std::vector<std::pair<int, int>>>> mni_sources;
+    // mni_sources[query][query column] = list of (matched, matched column)
+};
+
+// Morph selection (Section 4.1, step a).  Returns PM_OK or an error status
+// with *why set.
+pm_status morph_select(const std::vector<Pat> &queries, pm_op op, pm_morph_mode mode,
+                       MorphPlan &out, std::string *why);
+
+// Matching plans of one pattern (one per automorphism orbit).
+std::vector<DevPlan> compile_plans(const Pat &p, int counter, int dom_base,
+                                   const std::vector<int> &column_of_vertex);
+
+// Device memory through the configured allocator.
+void *dev_alloc(size_t bytes, int device);
+void dev_free(void *ptr, size_t bytes, int device);
+
+void set_error(const std::string &msg);
+
+// Kernel launchers (match.cu).
+// Resets the control block and arms the deadline (budget_ns = 0: none).
+int launch_arm(Control *d_ctl, uint64_t budget_ns, void *stream);
+int launch_count(const DevGraph &g, const DevPlan *d_plans, int nplans, const DevTasks &tasks,
+                 uint64_t *d_counters, Control *d_ctl, void *stream);
+int launch_domains(const DevGraph &g, const DevPlan *d_plans, int nplans, const DevTasks &tasks,
+                   uint32_t *d_bitsets, int64_t words_per_bitset, Control *d_ctl, void *stream);
+int launch_mni_reduce(const uint32_t *d_bitsets, int64_t words_per_bitset, const int32_t *d_src_off,
+                      const int32_t *d_src, int n_columns, unsigned long long *d_popc,
+                      void *stream);
+int device_sm_count(int device);
+
+}  // namespace pm

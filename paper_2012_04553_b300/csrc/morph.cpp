@@ -1,0 +1,266 @@
+// Morph selection, morph transform coefficients and matching-plan compilation.
+//
+// Counting (sum aggregation, permute operator = identity, Section 3.2.3):
+//  * an edge-induced query p^E becomes its vertex-induced superpatterns
+//    (Theorem 3.1): count(p^E) = sum_q c(p, q) count(q^V), q = p included;
+//  * a vertex-induced query p^V becomes edge-induced superpatterns.  Applying
+//    Corollary 3.1 recursively until only cliques remain gives, in closed
+//    form, count(p^V) = sum_q (-1)^(e(q) - e(p)) c(p, q) count(q^E): the
+//    signed coefficients are the Moebius function of the "spanning copy"
+//    order, the inverse of the Theorem 3.1 matrix.
+// MNI (union aggregation, permute operator = column permutation): only the
+// edge-from-vertex direction exists (a union has no inverse, Section 3.2.3):
+//  D_{p^E}[u] = D_{p^V}[u]  u  U_q U_{f in phi(p^E, q^E)} D_{q^V}[f(u)].
+#include <algorithm>
+#include <map>
+#include <numeric>
+#include <string>
+
+#include "internal.hpp"
+
+namespace pm {
+
+namespace {
+
+struct MatchedSet {
+    std::map<Key, int> index;
+    std::vector<Pat> pats;
+    int add(const Pat &p) {
+        Pat c = canonical_form(p);
+        Key key = canonical(c);
+        auto it = index.find(key);
+        if (it != index.end()) return it->second;
+        int id = int(pats.size());
+        index[key] = id;
+        pats.push_back(c);
+        return id;
+    }
+};
+
+// Column (orbit index, orbits numbered by smallest member) of every vertex.
+std::vector<int> columns_of(const Pat &p, int *n_columns) {
+    std::vector<Perm> aut = automorphisms(p);
+    std::vector<int> orb = orbit_of(p, aut);
+    std::vector<int> col(p.k, -1), rep_col(p.k, -1);
+    int nc = 0;
+    for (int u = 0; u < p.k; u++) {
+        if (rep_col[orb[u]] < 0) rep_col[orb[u]] = nc++;
+        col[u] = rep_col[orb[u]];
+    }
+    if (n_columns) *n_columns = nc;
+    return col;
+}
+
+}  // namespace
+
+pm_status morph_select(const std::vector<Pat> &queries, pm_op op, pm_morph_mode mode,
+                       MorphPlan &out, std::string *why) {
+    if (mode == PM_MORPH_COST) {
+        if (why) *why = "cost-based morph selection is not implemented";
+        return PM_EUNSUPPORTED;
+    }
+    MatchedSet ms;
+    out.queries = queries;
+    out.terms.assign(queries.size(), {});
+    std::vector<std::vector<std::pair<int, std::vector<int>>>> mni_raw(queries.size());
+    // mni_raw[query] = list of (matched id, f-image of each query column rep)
+    for (size_t i = 0; i < queries.size(); i++) {
+        Pat p = queries[i];
+        if (p.is_clique()) p.vi = false;
+        bool morph = (mode == PM_MORPH_NAIVE) && !p.is_clique();
+        if (op == PM_OP_SUPPORT && p.vi) morph = false;   // no vertex-from-edge MNI rule
+        if (!morph) {
+            int id = ms.add(p);
+            out.terms[i].push_back({id, 1});
+            continue;
+        }
+        const int e_p = p.n_edges();
+        Pat pe = p;
+        pe.vi = false;
+        for (const Super &s : superpatterns(pe)) {
+            if (!p.vi) {
+                // Theorem 3.1: p^E from vertex-induced superpatterns
+                Pat q = s.q;
+                q.vi = !q.is_clique();
+                int id = ms.add(q);
+                out.terms[i].push_back({id, s.coef});
+            } else {
+                // Corollary 3.1, recursively: p^V from edge-induced superpatterns
+                Pat q = s.q;
+                q.vi = false;
+                int id = ms.add(q);
+                int64_t sign = ((q.n_edges() - e_p) & 1) ? -1 : 1;
+                out.terms[i].push_back({id, sign * s.coef});
+            }
+        }
+    }
+    out.matched = ms.pats;
+    // Merge repeated terms.
+    for (auto &t : out.terms) {
+        std::map<int, int64_t> acc;
+        for (const Term &x : t) acc[x.matched] += x.coef;
+        t.clear();
+        for (auto &kv : acc)
+            if (kv.second != 0) t.push_back({kv.first, kv.second});
+    }
+    out.matched_columns.assign(out.matched.size(), 0);
+    out.matched_orbit.assign(out.matched.size(), {});
+    for (size_t j = 0; j < out.matched.size(); j++)
+        out.matched_orbit[j] = columns_of(out.matched[j], &out.matched_columns[j]);
+
+    if (op == PM_OP_SUPPORT) {
+        out.mni_sources.assign(queries.size(), {});
+        for (size_t i = 0; i < queries.size(); i++) {
+            Pat p = queries[i];
+            if (p.is_clique()) p.vi = false;
+            int nqc = 0;
+            std::vector<int> qcol = columns_of(p, &nqc);
+            out.mni_sources[i].assign(nqc, {});
+            std::vector<int> rep(nqc, -1);
+            for (int u = 0; u < p.k; u++)
+                if (rep[qcol[u]] < 0) rep[qcol[u]] = u;
+            // Every matched pattern this query draws on, with the maps phi(p^E, q^E)
+            Pat pe = p;
+            pe.vi = false;
+            for (const Term &t : out.terms[i]) {
+                const Pat &q = out.matched[t.matched];
+                Pat qe = q;
+                qe.vi = false;
+                std::vector<Perm> fs = (q.vi || q.is_clique()) && !p.vi ? embeddings(pe, qe)
+                                                                         : embeddings(p, q);
+                for (int c = 0; c < nqc; c++) {
+                    auto &dst = out.mni_sources[i][c];
+                    for (const Perm &f : fs) {
+                        std::pair<int, int> src{t.matched, out.matched_orbit[t.matched][f[rep[c]]]};
+                        if (std::find(dst.begin(), dst.end(), src) == dst.end()) dst.push_back(src);
+                    }
+                }
+            }
+        }
+    }
+    return PM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Plan compilation.
+
+namespace {
+
+// Visiting order from the root: repeatedly the unvisited vertex with the most
+// edges into the visited set, then most anti-edges (vertex-induced), then
+// highest pattern degree, then smallest id.
+std::vector<int> matching_order(const Pat &p, int root) {
+    std::vector<int> order{root};
+    uint32_t visited = 1u << root;
+    while (int(order.size()) < p.k) {
+        int best = -1;
+        int bs[3] = {-1, -1, -1};
+        for (int w = 0; w < p.k; w++) {
+            if ((visited >> w) & 1) continue;
+            int e = __builtin_popcount(p.adj[w] & visited);
+            if (e == 0) continue;
+            int a = p.vi ? __builtin_popcount(~p.adj[w] & visited & ~(1u << w)) : 0;
+            int d = __builtin_popcount(p.adj[w]);
+            int s[3] = {e, a, d};
+            if (best < 0 || std::lexicographical_compare(bs, bs + 3, s, s + 3)) {
+                best = w;
+                std::copy(s, s + 3, bs);
+            }
+        }
+        order.push_back(best);
+        visited |= 1u << best;
+    }
+    return order;
+}
+
+bool same_common(const DevLevel &a, const DevLevel &b, uint8_t tail_bits) {
+    return a.isect == b.isect && a.diff == b.diff && a.lt == b.lt && a.neq == b.neq &&
+           a.label == b.label && (a.gt & ~tail_bits) == (b.gt & ~tail_bits);
+}
+
+}  // namespace
+
+std::vector<DevPlan> compile_plans(const Pat &p, int counter, int dom_base,
+                                   const std::vector<int> &column_of_vertex) {
+    std::vector<Perm> aut = automorphisms(p);
+    std::vector<int> orb = orbit_of(p, aut);
+    int n_columns = 0;
+    for (int c : column_of_vertex) n_columns = std::max(n_columns, c + 1);
+    std::vector<DevPlan> plans;
+    for (int root = 0; root < p.k; root++) {
+        if (orb[root] != root) continue;   // one plan per orbit, at its smallest vertex
+        std::vector<int> order = matching_order(p, root);
+        std::vector<int> level_of(p.k);
+        for (int i = 0; i < p.k; i++) level_of[order[i]] = i;
+
+        DevPlan plan{};
+        plan.k = p.k;
+        plan.counter = counter;
+        plan.dom_base = dom_base;
+        plan.n_columns = n_columns;
+        for (int i = 0; i < p.k; i++) {
+            int u = order[i];
+            DevLevel &lv = plan.lv[i];
+            lv.label = p.lab[u];
+            lv.column = uint8_t(column_of_vertex.empty() ? 0 : column_of_vertex[u]);
+            if (i == 0) continue;
+            lv.lt = 1;   // every non-root vertex ranks below the root
+            for (int j = 0; j < i; j++) {
+                int w = order[j];
+                if (p.adjacent(u, w)) lv.isect |= uint8_t(1u << j);
+                else if (p.vi) lv.diff |= uint8_t(1u << j);
+            }
+        }
+        // Symmetry breaking over the stabiliser of the root.
+        std::vector<Perm> H;
+        for (const Perm &s : aut)
+            if (s[root] == root) H.push_back(s);
+        for (int i = 1; i < p.k; i++) {
+            int v = order[i];
+            uint32_t orbit = 0;
+            for (const Perm &s : H) orbit |= 1u << s[v];
+            for (int w = 0; w < p.k; w++) {
+                if (w == v || !((orbit >> w) & 1)) continue;
+                // image of v below image of w; w comes later in the order
+                plan.lv[level_of[w]].gt |= uint8_t(1u << i);
+            }
+            std::vector<Perm> H2;
+            for (const Perm &s : H)
+                if (s[v] == v) H2.push_back(s);
+            H.swap(H2);
+        }
+        // Injectivity not implied by adjacency or ordering.
+        for (int i = 1; i < p.k; i++) {
+            DevLevel &lv = plan.lv[i];
+            uint8_t implied = lv.isect | lv.lt | lv.gt;
+            for (int j = 0; j < i; j++)
+                if (!((implied >> j) & 1)) lv.neq |= uint8_t(1u << j);
+        }
+        // Longest totally ordered tail with one shared candidate set.
+        int tail = 0;
+        if (p.k >= 3) {
+            tail = 1;
+            for (int r = p.k - 2; r >= 2; r--) {
+                int t0 = p.k - r;
+                uint8_t tail_bits = uint8_t(((1u << p.k) - 1) & ~((1u << t0) - 1));
+                bool ok = true;
+                for (int t = t0; t < p.k && ok; t++) {
+                    const DevLevel &lv = plan.lv[t];
+                    if (!same_common(lv, plan.lv[t0], tail_bits)) ok = false;
+                    if ((lv.isect | lv.diff | lv.lt | lv.neq) & tail_bits) ok = false;
+                    uint8_t before = uint8_t(((1u << t) - 1) & tail_bits);
+                    if ((lv.gt & tail_bits) != before) ok = false;
+                }
+                if (ok) { tail = r; break; }
+            }
+        }
+        plan.tail = tail;
+        plan.n_enum = p.k - tail;
+        const DevLevel &f = plan.lv[plan.n_enum < p.k ? plan.n_enum : p.k - 1];
+        plan.closed = tail > 0 && __builtin_popcount(f.isect) == 1 && f.diff == 0 && f.label < 0;
+        plans.push_back(plan);
+    }
+    return plans;
+}
+
+}  // namespace pm

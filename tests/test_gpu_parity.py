@@ -1,0 +1,197 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle, bit-exact.
+
+Counts and supports are integers, so every comparison is exact equality.
+Sizes span many 32-edge task chunks with ragged tails; the full-size scale-20
+graph is checked on sampled roots, whose counts the oracle computes exactly
+(occurrences partition by their highest-ranked vertex)."""
+import json
+import os
+from math import comb
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import algebra
+import paper_2012_04553_b300 as pm
+from pm_inputs import rmat_edges, cached_rmat, gnp_edges, zipf_labels, uniform_ints
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def motif_queries(k, vi=True):
+    return [pm.make_pattern(k, m, pm.VERTEX_INDUCED if vi else pm.EDGE_INDUCED)
+            for m in algebra.connected_classes(k)]
+
+
+def load(n, s, d, labels=None):
+    return pm.Graph(n, s, d, labels)
+
+
+def test_rmat_s12_4motifs_golden():
+    gold = json.load(open(os.path.join(GOLDEN, "rmat_s12_e8_seed1_motifs.json")))
+    s, d = rmat_edges(12, 8, seed=1)
+    g = load(4096, s, d)
+    assert g.info()["m"] == gold["m"]
+    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+        for k in (3, 4):
+            assert pm.Plan(g, motif_queries(k), mode=mode).count() == gold["vertex_induced"][str(k)]
+            assert pm.Plan(g, motif_queries(k, vi=False), mode=mode).count() == \
+                gold["edge_induced"][str(k)]
+
+
+@pytest.mark.parametrize("scale,ef,seed,kmax", [(7, 6, 100, 5), (8, 8, 101, 4), (9, 6, 102, 4),
+                                                (10, 4, 103, 4)])
+def test_motifs_small_rmat_against_oracle(scale, ef, seed, kmax):
+    n = 1 << scale
+    s, d = rmat_edges(scale, ef, seed=seed)
+    og = oracle.prepare_graph(n, s, d)
+    g = load(n, s, d)
+    for k in range(3, kmax + 1):
+        want_v = oracle.motif_counts_direct(og, k)
+        want_e = [oracle.count(og, algebra.Pattern.from_mask(k, m)) for m in algebra.connected_classes(k)]
+        for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+            assert pm.Plan(g, motif_queries(k), mode=mode).count() == want_v, (k, mode)
+            assert pm.Plan(g, motif_queries(k, False), mode=mode).count() == want_e, (k, mode)
+
+
+def test_six_vertex_patterns_against_oracle():
+    s, d = rmat_edges(7, 5, seed=104)
+    og = oracle.prepare_graph(128, s, d)
+    g = load(128, s, d)
+    masks = algebra.connected_classes(6)[::7]
+    for vi in (False, True):
+        qs = [pm.make_pattern(6, m, int(vi)) for m in masks]
+        want = [oracle.count(og, algebra.Pattern.from_mask(6, m, None, vi)) for m in masks]
+        assert pm.Plan(g, qs, mode=pm.MORPH_NONE).count() == want
+        assert pm.Plan(g, qs, mode=pm.MORPH_NAIVE).count() == want
+
+
+def test_labeled_counts_against_oracle():
+    n = 512
+    s, d = rmat_edges(9, 8, seed=105)
+    labels = zipf_labels(n, 3, seed=106)
+    og = oracle.prepare_graph(n, s, d, labels)
+    g = load(n, s, d, labels)
+    qs = oracle.labeled_edge_patterns(3, [0, 1, 2])[::3]
+    cq = [pm.make_pattern(p.k, p.mask, pm.EDGE_INDUCED, p.labels) for p in qs]
+    want = [oracle.count(og, p) for p in qs]
+    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+        assert pm.Plan(g, cq, mode=mode).count() == want
+    vq = [pm.make_pattern(p.k, p.mask, pm.VERTEX_INDUCED, p.labels) for p in qs]
+    want_v = [oracle.count(og, p.with_induced(True)) for p in qs]
+    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+        assert pm.Plan(g, vq, mode=mode).count() == want_v
+
+
+def test_closed_form_graphs():
+    # clique K_12, star S_40 and cycle C_50: closed forms of Section 2 counting
+    cases = []
+    n = 12
+    a, b = np.triu_indices(n, 1)
+    cases.append(("clique", n, a, b))
+    cases.append(("star", 41, np.zeros(40, dtype=np.int32), np.arange(1, 41)))
+    cases.append(("cycle", 50, np.arange(50), (np.arange(50) + 1) % 50))
+    for name, n, s, d in cases:
+        g = load(n, s, d)
+        for k in (3, 4, 5):
+            got_v = pm.Plan(g, motif_queries(k), mode=pm.MORPH_NAIVE).count()
+            got_e = pm.Plan(g, motif_queries(k, False), mode=pm.MORPH_NONE).count()
+            classes = algebra.connected_classes(k)
+            for i, m in enumerate(classes):
+                p = algebra.Pattern.from_mask(k, m)
+                aut = len(algebra.automorphisms(p))
+                degs = [sum(1 for e in p.edges if v in e) for v in range(k)]
+                star = len(p.edges) == k - 1 and max(degs) == k - 1
+                if name == "clique":
+                    assert got_v[i] == (comb(n, k) if p.is_clique else 0)
+                    assert got_e[i] == comb(n, k) * int(np.prod(range(1, k + 1))) // aut
+                if name == "star":
+                    assert got_v[i] == (comb(n - 1, k - 1) if star else 0)
+                if name == "cycle":
+                    is_path = len(p.edges) == k - 1 and max(degs) == 2
+                    assert got_v[i] == (n if is_path else 0)
+
+
+def test_edge_cases():
+    # one vertex, no edges; only self-loops and duplicates; a single edge
+    g = load(1, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    assert pm.Plan(g, motif_queries(4)).count() == [0] * 6
+    g = load(5, np.array([0, 1, 2, 1, 1]), np.array([0, 2, 1, 2, 1]))
+    info = g.info()
+    assert (info["m"], info["self_loops"], info["duplicates"]) == (1, 2, 2)
+    assert pm.Plan(g, [pm.make_pattern(2, 1)]).count() == [1]
+    assert pm.Plan(g, motif_queries(3)).count() == [0, 0]
+    with pytest.raises(pm.PMError):
+        pm.Plan(g, [pm.make_pattern(3, 0b011, 0, [0, 1, 0])])   # labels on unlabeled graph
+    with pytest.raises(pm.PMError):
+        pm.Graph(4, np.array([0, 5]), np.array([1, 2]))         # id out of range
+
+
+def test_root_subsets_partition_and_match_oracle():
+    n = 2048
+    s, d = rmat_edges(11, 8, seed=107)
+    og = oracle.prepare_graph(n, s, d)
+    g = load(n, s, d)
+    plan = pm.Plan(g, motif_queries(4), mode=pm.MORPH_NAIVE)
+    total = plan.count()
+    parts = np.array_split(np.arange(n, dtype=np.int32), 3)
+    got = [plan.count_roots(p) for p in parts]
+    assert [sum(x) for x in zip(*got)] == total
+    roots = uniform_ints(9, 1, 64, 0, n).astype(np.int32)
+    roots = np.unique(roots)
+    assert plan.count_roots(roots) == oracle.motif_counts_direct(og, 4, roots=roots)
+    assert plan.count_roots(np.zeros(0, np.int32)) == [0] * 6
+
+
+def sampled_roots(deg, seed, count, max_degree):
+    """Uniformly drawn vertices whose degree is at most max_degree (the oracle
+    enumerates every automorphic copy, about degree^(k-1) maps per root)."""
+    cand = np.nonzero(deg <= max_degree)[0]
+    pick = uniform_ints(seed, 3, count, 0, len(cand))
+    return np.unique(cand[pick]).astype(np.int32)
+
+
+def test_full_size_scale20_sampled_roots():
+    """The scale-20 R-MAT graph (edge factor 16, seed 2) in the bench's launch
+    configuration, checked exactly on sampled roots (uniform over vertices of
+    degree <= 160 for 4-motifs, <= 40 for 5-motifs), morphed and direct."""
+    s, d = cached_rmat(20, 16, seed=2)
+    n = 1 << 20
+    og = oracle.prepare_graph(n, s, d)
+    g = load(n, s, d)
+    roots = sampled_roots(og.degree, 2, 64, 160)
+    want = oracle.motif_counts_direct(og, 4, roots=roots)
+    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+        assert pm.Plan(g, motif_queries(4), mode=mode).count_roots(roots) == want
+    roots5 = sampled_roots(og.degree, 3, 32, 40)
+    want5 = oracle.motif_counts_direct(og, 5, roots=roots5)
+    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+        assert pm.Plan(g, motif_queries(5), mode=mode).count_roots(roots5) == want5
+
+
+def test_mni_support_against_oracle():
+    n = 512
+    s, d = rmat_edges(9, 8, seed=108)
+    labels = zipf_labels(n, 3, seed=109)
+    og = oracle.prepare_graph(n, s, d, labels)
+    g = load(n, s, d, labels)
+    qs = oracle.labeled_edge_patterns(3, [0, 1, 2])[::2] + oracle.labeled_edge_patterns(2, [0, 1, 2])
+    cq = [pm.make_pattern(p.k, p.mask, pm.EDGE_INDUCED, p.labels) for p in qs]
+    want = [oracle.support_direct(og, p) for p in qs]
+    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+        sup, freq = pm.Plan(g, cq, op=pm.OP_SUPPORT, mode=mode).support(threshold=20)
+        assert sup == want, mode
+        assert freq == [w >= 20 for w in want]
+
+
+def test_deadline_returns_timeout_and_context_survives():
+    s, d = rmat_edges(14, 16, seed=110)
+    g = load(1 << 14, s, d)
+    heavy = pm.Plan(g, motif_queries(5), mode=pm.MORPH_NONE)
+    with pytest.raises(pm.PMTimeout):
+        heavy.count(timeout_s=1e-4)
+    small = pm.Plan(g, motif_queries(3), mode=pm.MORPH_NAIVE)
+    a = small.count()
+    assert small.count(timeout_s=60.0) == a

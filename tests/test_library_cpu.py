@@ -1,0 +1,147 @@
+"""CPU tests of the library (no GPU): the C ABI loads and exports every
+declared symbol, compiled plans count correctly (checked with a plain-Python
+interpreter of the plan semantics against the oracle), and the host morph
+transform recovers oracle results."""
+import itertools
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import algebra
+import paper_2012_04553_b300 as pm
+from pm_inputs import rmat_edges, gnp_edges, zipf_labels
+from tests.plan_interp import degree_ordered, run_plans
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "pm.h")).read()
+    return sorted(set(re.findall(r"^(?:pm_status|void|const char \*)\s*(pm_\w+)\s*\(", text, re.M)))
+
+
+def test_abi_exports_every_declared_symbol():
+    names = declared_symbols()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(pm.lib(), name), name
+    assert sorted(pm.ABI_SYMBOLS) == names
+
+
+def test_errors_are_statuses_not_aborts():
+    disconnected = pm.make_pattern(4, 0b100001)  # edges (0,1) and (2,3)
+    with pytest.raises(pm.PMError) as e:
+        pm.Plan(None, [disconnected])
+    assert e.value.status == pm.PM_EINVAL
+    with pytest.raises(pm.PMError):
+        pm.Plan(None, [pm.make_pattern(1, 0)])
+    with pytest.raises(pm.PMError):
+        pm.Plan(None, [pm.make_pattern(3, 1 << 5)])
+    p = pm.Plan(None, [pm.make_pattern(3, 0b111)])
+    with pytest.raises(pm.PMError) as e:
+        p.count()
+    assert e.value.status == pm.PM_EINVAL
+    assert pm.lib().pm_strerror(pm.PM_ETIMEOUT) == b"deadline expired"
+
+
+def pats(k, vi):
+    return [pm.make_pattern(k, m, pm.VERTEX_INDUCED if vi else pm.EDGE_INDUCED)
+            for m in algebra.connected_classes(k)]
+
+
+def oracle_pattern(k, mask, induced, labels=None):
+    return algebra.Pattern.from_mask(k, mask, labels, induced == pm.VERTEX_INDUCED)
+
+
+@pytest.fixture(scope="module")
+def small_graph():
+    s, d = rmat_edges(6, 6, seed=31)
+    return oracle.prepare_graph(64, s, d)
+
+
+@pytest.mark.parametrize("k", [3, 4, 5])
+@pytest.mark.parametrize("vi", [False, True])
+def test_plans_count_matched_patterns(small_graph, k, vi):
+    g = small_graph
+    adj, labels = degree_ordered(g)
+    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+        plan = pm.Plan(None, pats(k, vi), mode=mode)
+        got = run_plans(plan.export_plans(), plan.n_matched, adj, labels)
+        for (kk, mask, ind, lab), c in zip(plan.matched_patterns(), got):
+            assert c == oracle.count(g, oracle_pattern(kk, mask, ind)), (kk, mask, ind, mode)
+
+
+def test_morph_transform_recovers_requested(small_graph):
+    g = small_graph
+    adj, labels = degree_ordered(g)
+    for k in (4, 5):
+        for vi in (False, True):
+            plan = pm.Plan(None, pats(k, vi), mode=pm.MORPH_NAIVE)
+            matched = run_plans(plan.export_plans(), plan.n_matched, adj, labels)
+            want = [oracle.count(g, algebra.Pattern.from_mask(k, m, None, vi))
+                    for m in algebra.connected_classes(k)]
+            assert plan.morph(matched) == want
+
+
+def test_plans_root_partition(small_graph):
+    g = small_graph
+    adj, labels = degree_ordered(g)
+    plan = pm.Plan(None, pats(4, True), mode=pm.MORPH_NAIVE)
+    tbl = plan.export_plans()
+    roots_caller = np.arange(0, g.n, 3)
+    roots_internal = [int(g.rank[v]) for v in roots_caller]
+    part = plan.morph(run_plans(tbl, plan.n_matched, adj, labels, roots=roots_internal))
+    want = oracle.motif_counts_direct(g, 4, roots=roots_caller)
+    assert part == want
+
+
+def test_labeled_plans(small_graph):
+    s, d = gnp_edges(14, 0.45, seed=8)
+    labels = np.array([0, 1, 2, 0, 1, 0, 0, 2, 1, 0, 1, 0, 2, 0])
+    g = oracle.prepare_graph(14, s, d, labels)
+    adj, lab = degree_ordered(g)
+    queries = oracle.labeled_edge_patterns(3, [0, 1])
+    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+        cq = [pm.make_pattern(p.k, p.mask, pm.EDGE_INDUCED, p.labels) for p in queries]
+        plan = pm.Plan(None, cq, mode=mode)
+        matched = run_plans(plan.export_plans(), plan.n_matched, adj, lab)
+        assert plan.morph(matched) == [oracle.count(g, p) for p in queries]
+
+
+def test_six_vertex_plans_on_tiny_graph():
+    s, d = gnp_edges(11, 0.5, seed=41)
+    g = oracle.prepare_graph(11, s, d)
+    adj, labels = degree_ordered(g)
+    masks = algebra.connected_classes(6)[::9]
+    for vi in (False, True):
+        plan = pm.Plan(None, [pm.make_pattern(6, m, int(vi)) for m in masks], mode=pm.MORPH_NONE)
+        got = plan.morph(run_plans(plan.export_plans(), plan.n_matched, adj, labels))
+        assert got == [oracle.count(g, algebra.Pattern.from_mask(6, m, None, vi)) for m in masks]
+
+
+def test_morph_coefficients_match_oracle_algebra():
+    # the library's transform applied to symbolic vertex-induced counts gives the
+    # edge-induced counts of the oracle's Theorem 3.1 implementation
+    rng = np.random.default_rng(3)
+    for k in (4, 5):
+        plan = pm.Plan(None, pats(k, False), mode=pm.MORPH_NAIVE)
+        matched = plan.matched_patterns()
+        vals = {}
+        for (kk, mask, ind, lab) in matched:
+            vals[algebra.canonical(oracle_pattern(kk, mask, pm.VERTEX_INDUCED))] = int(rng.integers(0, 10**9))
+        cv = lambda q: vals[algebra.canonical(q.with_induced(True))]
+        got = plan.morph([vals[algebra.canonical(oracle_pattern(kk, mask, pm.VERTEX_INDUCED))]
+                          for (kk, mask, ind, lab) in matched])
+        want = [algebra.count_E_from_V(algebra.Pattern.from_mask(k, m), cv)
+                for m in algebra.connected_classes(k)]
+        assert got == want
+
+
+def test_morph_is_modulo_2_128():
+    plan = pm.Plan(None, pats(4, True), mode=pm.MORPH_NAIVE)
+    big = [(1 << 127) + 12345] * plan.n_matched
+    out = plan.morph(big)
+    assert all(0 <= x < (1 << 128) for x in out)
