@@ -138,12 +138,31 @@ pm_status pm_plan_get_info(const pm_query_plan *p, pm_plan_info *out);
 /* The matched (alternative) patterns, n_matched entries. */
 pm_status pm_plan_matched(const pm_query_plan *p, pm_pattern *out);
 void pm_free_plan(pm_query_plan *p);
-/* Copy the compiled matching plans (the device plan table, n_kernels_plans
- * records of 96 bytes: int32 k, n_enum, tail, closed, counter, dom_base,
- * n_columns, pad; then 8 levels of uint8 isect, diff, lt, gt, neq, int8
- * label, uint8 column, pad) into out (cap bytes).  For inspection and tests;
- * returns PM_EINVAL if cap is too small. */
-pm_status pm_plan_export(const pm_query_plan *p, void *out, int64_t cap);
+/* Plan families.  Rooted plans (one per automorphism orbit of a matched
+ * pattern) pin the orbit to each occurrence's highest-ranked vertex, which
+ * makes per-root counts exact (pm_count_roots always uses them).  The free
+ * plan of a pattern counts every occurrence once from its cheapest vertex,
+ * breaking the whole automorphism group.  pm_count and pm_support use, per
+ * matched pattern, the family the autotuner found faster on the plan's graph
+ * (PM_PLANS_AUTO), unless pm_plan_select forces one. */
+#define PM_PLANS_AUTO (-1)
+#define PM_PLANS_ROOTED 0
+#define PM_PLANS_FREE 1
+pm_status pm_plan_select(pm_query_plan *p, int32_t family);
+/* Run the autotuner now (it otherwise runs inside the first pm_count or
+ * pm_support): for each matched pattern not yet decided on this graph, time
+ * its rooted and free plans on the same sample of about 4096 task chunks and
+ * keep the faster; decisions are cached on the graph.  families (nullable):
+ * n_matched entries receiving PM_PLANS_ROOTED or PM_PLANS_FREE. */
+pm_status pm_plan_autotune(pm_query_plan *p, void *stream, int32_t *families);
+/* Copy the compiled plans of one family (PM_PLANS_ROOTED: n_kernels_plans
+ * records; PM_PLANS_FREE: n_matched records) into out (cap bytes).  A record
+ * is 112 bytes: int32 k, n_enum, tail, closed, counter, dom_base, n_columns,
+ * split, task_space, kind (0 set operations, 1 wedge pairs), 2 x int32 pad;
+ * then 8 levels of uint8 isect, diff, lt,
+ * gt, neq, int8 label, uint8 column, pad.  For inspection and tests;
+ * PM_EINVAL if cap is too small. */
+pm_status pm_plan_export(const pm_query_plan *p, int32_t family, void *out, int64_t cap);
 
 /* Section 4.1 step b for counting: requested[2*i..] = sum_j T[i][j] *
  * matched[2*j..] modulo 2^128, where T holds the morph coefficients
@@ -167,6 +186,20 @@ pm_status pm_count(pm_query_plan *p, void *stream, double timeout_s, uint64_t *c
  * pm_count's result, so sampled roots give exactly checkable partial counts. */
 pm_status pm_count_roots(pm_query_plan *p, void *stream, double timeout_s, const int32_t *roots,
                          int64_t nroots, uint64_t *counts, uint64_t *matched);
+
+/* pm_count with an instrumented kernel that also returns the algorithmic
+ * bytes of the matching: 4 B per element of every set-operation operand,
+ * each operand cut to the plan's (lower, upper) id window (merge accounting
+ * |A'| + |B'| per intersection or difference), 16 B per row-offset pair,
+ * 28 B per task and 24 B plus 8 B per excluded vertex for each closed-form
+ * count.  Slower than pm_count; meant for roofline measurement. */
+pm_status pm_count_instrumented(pm_query_plan *p, void *stream, uint64_t *counts,
+                                uint64_t *alg_bytes);
+
+/* Device time (CUDA events on the launch stream) of the matching kernel of
+ * the plan's last completed pm_count / pm_count_roots / pm_support call;
+ * 0 if that call launched none. */
+pm_status pm_plan_last_kernel_ms(const pm_query_plan *p, float *ms);
 
 /* MNI support (Section 2, FSM) of every query of a PM_OP_SUPPORT plan:
  * one column per orbit of the query's label-preserving automorphism group,

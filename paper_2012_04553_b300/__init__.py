@@ -22,6 +22,7 @@ EDGE_INDUCED, VERTEX_INDUCED = 0, 1
 OP_COUNT, OP_SUPPORT = 0, 1
 MORPH_NONE, MORPH_NAIVE, MORPH_COST = 0, 1, 2
 MAX_K = 8
+PLANS_AUTO, PLANS_ROOTED, PLANS_FREE = -1, 0, 1
 
 
 class PMError(RuntimeError):
@@ -74,7 +75,11 @@ def _load():
         "pm_count": [vp, vp, dbl, vp, vp],
         "pm_count_roots": [vp, vp, dbl, vp, i64, vp, vp],
         "pm_support": [vp, vp, dbl, ctypes.c_uint64, vp, vp],
-        "pm_plan_export": [vp, vp, i64],
+        "pm_plan_export": [vp, i32, vp, i64],
+        "pm_plan_select": [vp, i32],
+        "pm_plan_autotune": [vp, vp, vp],
+        "pm_count_instrumented": [vp, vp, vp, vp],
+        "pm_plan_last_kernel_ms": [vp, ctypes.POINTER(ctypes.c_float)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -98,7 +103,8 @@ ABI_SYMBOLS = [
     "pm_set_allocator", "pm_load_graph", "pm_graph_get_info", "pm_graph_vertex_order",
     "pm_free_graph", "pm_plan", "pm_plan_get_info", "pm_plan_matched", "pm_free_plan",
     "pm_morph", "pm_count", "pm_count_roots", "pm_support", "pm_strerror", "pm_last_error",
-    "pm_plan_export",
+    "pm_plan_export", "pm_count_instrumented", "pm_plan_last_kernel_ms", "pm_plan_select",
+    "pm_plan_autotune",
 ]
 
 
@@ -232,16 +238,27 @@ class Plan:
         _check(_lib.pm_plan_matched(self._h, arr), "pm_plan_matched")
         return [(p.k, p.edge_mask, p.induced, list(p.label)[:p.k]) for p in arr]
 
-    def export_plans(self):
-        """The compiled plan table as a numpy structured array (see pm_plan_export)."""
+    def export_plans(self, family=PLANS_ROOTED):
+        """The compiled plans of one family as a numpy structured array (pm_plan_export)."""
         level = np.dtype([("isect", "u1"), ("diff", "u1"), ("lt", "u1"), ("gt", "u1"),
                           ("neq", "u1"), ("label", "i1"), ("column", "u1"), ("pad", "u1")])
         rec = np.dtype([("k", "<i4"), ("n_enum", "<i4"), ("tail", "<i4"), ("closed", "<i4"),
                         ("counter", "<i4"), ("dom_base", "<i4"), ("n_columns", "<i4"),
-                        ("pad", "<i4"), ("lv", level, (8,))])
-        out = np.zeros(self.n_plans, dtype=rec)
-        _check(_lib.pm_plan_export(self._h, _ptr(out), out.nbytes), "pm_plan_export")
+                        ("split", "<i4"), ("task_space", "<i4"), ("kind", "<i4"),
+                        ("pad", "<i4", (2,)),
+                        ("lv", level, (8,))])
+        out = np.zeros(self.n_plans if family == PLANS_ROOTED else self.n_matched, dtype=rec)
+        _check(_lib.pm_plan_export(self._h, family, _ptr(out), out.nbytes), "pm_plan_export")
         return out
+
+    def select(self, family):
+        """Force a plan family for count()/support() (PLANS_AUTO = autotuned)."""
+        _check(_lib.pm_plan_select(self._h, family), "pm_plan_select")
+
+    def autotune(self, stream=None):
+        fam = np.zeros(self.n_matched, dtype=np.int32)
+        _check(_lib.pm_plan_autotune(self._h, _stream_handle(stream), _ptr(fam)), "pm_plan_autotune")
+        return [int(x) for x in fam]
 
     def morph(self, matched_counts):
         m = np.zeros(2 * self.n_matched, dtype=np.uint64)
@@ -258,6 +275,20 @@ class Plan:
         _check(_lib.pm_count(self._h, _stream_handle(stream), float(timeout_s), _ptr(out), _ptr(mat)),
                "pm_count")
         return (_words_to_ints(out), _words_to_ints(mat)) if with_matched else _words_to_ints(out)
+
+    def last_kernel_ms(self):
+        """Device time of the matching kernel of the last count/support call."""
+        v = ctypes.c_float()
+        _check(_lib.pm_plan_last_kernel_ms(self._h, ctypes.byref(v)), "pm_plan_last_kernel_ms")
+        return float(v.value)
+
+    def count_instrumented(self, stream=None):
+        """(counts, algorithmic bytes read by the matching) from an instrumented run."""
+        out = np.zeros(2 * self.n_queries, dtype=np.uint64)
+        b = np.zeros(1, dtype=np.uint64)
+        _check(_lib.pm_count_instrumented(self._h, _stream_handle(stream), _ptr(out), _ptr(b)),
+               "pm_count_instrumented")
+        return _words_to_ints(out), int(b[0])
 
     def count_roots(self, roots, stream=None, timeout_s=0.0, with_matched=False):
         r = np.ascontiguousarray(roots, dtype=np.int32)

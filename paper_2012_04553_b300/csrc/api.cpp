@@ -1,7 +1,10 @@
 // C ABI (include/pm.h): argument checking, plan ownership, device buffers,
-// launches and the host half of the morph transform.
+// the plan-family autotuner, launches and the host half of the morph
+// transform.
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <mutex>
 #include <string>
@@ -62,12 +65,32 @@ void dev_free(void *ptr, size_t bytes, int device) {
 
 using namespace pm;
 
+namespace {
+
+// A device copy of a list of plans.
+struct PlanTable {
+    std::vector<DevPlan> plans;
+    DevPlan *d = nullptr;
+    size_t cap = 0;         // plans the device buffer holds
+    int max_enum = 2;
+    bool dirty = true;
+};
+
+}  // namespace
+
 struct pm_query_plan {
     const pm_graph *g = nullptr;
     pm_op op = PM_OP_COUNT;
     MorphPlan morph;
-    std::vector<DevPlan> plans;
-    DevPlan *d_plans = nullptr;
+    // per matched pattern: its rooted plans [rooted_begin[j], rooted_begin[j+1])
+    // and its free plan free_plans[j]
+    std::vector<DevPlan> rooted;
+    std::vector<int> rooted_begin;
+    std::vector<DevPlan> free_plans;
+    std::vector<int> choice;        // per matched pattern: 0 rooted, 1 free, -1 undecided
+    int forced = -1;                // pm_plan_select: -1 = autotuned per pattern
+    PlanTable active;               // pm_count / pm_support
+    PlanTable rooted_table;         // pm_count_roots
     uint64_t *d_counters = nullptr;
     Control *d_ctl = nullptr;
     // MNI
@@ -79,7 +102,16 @@ struct pm_query_plan {
     int32_t *d_col_off = nullptr, *d_col_src = nullptr;
     unsigned long long *d_popc = nullptr;
     std::vector<int> dom_base;               // per matched pattern
-    size_t bytes_plans = 0, bytes_counters = 0, bytes_bitsets = 0, bytes_cols = 0;
+    Deferred *d_defer = nullptr;             // deferred-chunk list and its piece scan
+    uint32_t *d_piece_off = nullptr;
+    uint32_t defer_cap = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // bracket the last matching launch
+    bool timed = false;
+    unsigned long long *d_stats = nullptr;
+    uint32_t *d_wedge = nullptr;             // wedge-kernel counters: blocks x n, kept zero
+    int wedge_nblocks = 0;
+    size_t bytes_counters = 0, bytes_bitsets = 0, bytes_cols = 0, bytes_wedge = 0;
+    bool device_ready = false;
 };
 
 namespace {
@@ -113,13 +145,13 @@ pm_status to_pat(const pm_pattern &q, bool graph_labeled, Pat *out) {
         set_error("pattern: induced must be PM_EDGE_INDUCED or PM_VERTEX_INDUCED");
         return PM_EINVAL;
     }
-    Pat p = Pat::from_mask(q.k, q.edge_mask, q.label, q.induced == PM_VERTEX_INDUCED);
     for (int u = 0; u < q.k; u++) {
         if (q.label[u] < -1) {
             set_error("pattern: label must be -1 (any) or a label value in [0, 127]");
             return PM_EINVAL;
         }
     }
+    Pat p = Pat::from_mask(q.k, q.edge_mask, q.label, q.induced == PM_VERTEX_INDUCED);
     if (!p.connected()) {
         set_error("pattern: not connected (Section 2 requires connected patterns)");
         return PM_EINVAL;
@@ -132,21 +164,65 @@ pm_status to_pat(const pm_pattern &q, bool graph_labeled, Pat *out) {
     return PM_OK;
 }
 
+void free_table(PlanTable &t, int dev) {
+    dev_free(t.d, sizeof(DevPlan) * std::max<size_t>(t.cap, 1), dev);
+    t.d = nullptr;
+    t.cap = 0;
+    t.dirty = true;
+}
+
+pm_status upload_table(PlanTable &t, int dev) {
+    if (!t.dirty) return PM_OK;
+    // set-operation plans first: the matching kernel takes a prefix of the table
+    std::stable_partition(t.plans.begin(), t.plans.end(),
+                          [](const DevPlan &dp) { return dp.kind == PLAN_SETOPS; });
+    t.max_enum = 2;
+    for (const DevPlan &dp : t.plans) t.max_enum = std::max(t.max_enum, int(dp.n_enum));
+    if (t.plans.size() > t.cap || !t.d) {
+        dev_free(t.d, sizeof(DevPlan) * std::max<size_t>(t.cap, 1), dev);
+        t.cap = std::max<size_t>(t.plans.size(), 1);
+        t.d = (DevPlan *)dev_alloc(sizeof(DevPlan) * t.cap, dev);
+        if (!t.d) {
+            t.cap = 0;
+            set_error("device allocation failed (plan table)");
+            return PM_ENOMEM;
+        }
+    }
+    if (!t.plans.empty()) {
+        cudaError_t e = cudaMemcpy(t.d, t.plans.data(), sizeof(DevPlan) * t.plans.size(),
+                                   cudaMemcpyHostToDevice);
+        if (e) return cuda_fail("plan table upload", e);
+    }
+    t.dirty = false;
+    return PM_OK;
+}
+
 void free_plan_device(pm_query_plan *p) {
     const int dev = p->g ? p->g->device : 0;
-    dev_free(p->d_plans, p->bytes_plans, dev);
+    free_table(p->active, dev);
+    free_table(p->rooted_table, dev);
     dev_free(p->d_counters, p->bytes_counters, dev);
     dev_free(p->d_ctl, sizeof(Control), dev);
     dev_free(p->d_bitsets, p->bytes_bitsets, dev);
     dev_free(p->d_col_off, p->bytes_cols, dev);
     dev_free(p->d_col_src, p->bytes_cols, dev);
     dev_free(p->d_popc, p->bytes_cols, dev);
-    p->d_plans = nullptr;
+    dev_free(p->d_stats, 256, dev);
+    dev_free(p->d_wedge, p->bytes_wedge, dev);
+    p->d_wedge = nullptr;
+    p->bytes_wedge = 0;
+    dev_free(p->d_defer, sizeof(Deferred) * std::max<uint32_t>(p->defer_cap, 1), dev);
+    dev_free(p->d_piece_off, sizeof(uint32_t) * std::max<uint32_t>(p->defer_cap, 1), dev);
     p->d_counters = nullptr;
     p->d_ctl = nullptr;
     p->d_bitsets = nullptr;
     p->d_col_off = p->d_col_src = nullptr;
     p->d_popc = nullptr;
+    p->d_stats = nullptr;
+    p->d_defer = nullptr;
+    p->d_piece_off = nullptr;
+    p->defer_cap = 0;
+    p->device_ready = false;
 }
 
 // Root list in internal ids with its oriented-edge offsets, on the device.
@@ -161,16 +237,19 @@ struct RootTasks {
     }
 };
 
-pm_status make_tasks(const pm_query_plan *p, const int32_t *roots, int64_t nroots, cudaStream_t s,
-                     RootTasks &rt, DevTasks *out) {
-    const pm_graph *g = p->g;
-    if (!roots) {
-        *out = DevTasks{nullptr, g->d_off, g->n, 0};
-        int64_t total = 0;
-        for (int64_t v = 0; v < g->n; v++) total += g->lowdeg[v];
-        out->ntasks = total;
-        return PM_OK;
+DevTasks all_tasks(const pm_graph *g) {
+    DevTasks t{};
+    t.roots = nullptr;
+    for (int s = 0; s < 3; s++) {
+        t.off[s] = g->d_off[s];
+        t.ntasks[s] = g->ntasks[s];
     }
+    t.nroots = g->n;
+    return t;
+}
+
+pm_status root_tasks(const pm_graph *g, const int32_t *roots, int64_t nroots, cudaStream_t s,
+                     RootTasks &rt, DevTasks *out) {
     std::vector<int32_t> ids(nroots);
     std::vector<int64_t> off(nroots + 1, 0);
     for (int64_t i = 0; i < nroots; i++) {
@@ -194,7 +273,12 @@ pm_status make_tasks(const pm_query_plan *p, const int32_t *roots, int64_t nroot
                                               cudaMemcpyHostToDevice, s) : cudaSuccess;
     cudaError_t e2 = cudaMemcpyAsync(rt.d_off, off.data(), rt.b_off, cudaMemcpyHostToDevice, s);
     if (e1 || e2) return cuda_fail("pm_count_roots: upload", e1 ? e1 : e2);
-    *out = DevTasks{rt.d_roots, rt.d_off, nroots, off[nroots]};
+    DevTasks t{};
+    t.roots = rt.d_roots;
+    t.off[0] = rt.d_off;
+    t.ntasks[0] = off[nroots];
+    t.nroots = nroots;
+    *out = t;
     return PM_OK;
 }
 
@@ -209,21 +293,24 @@ pm_status ensure_device(pm_query_plan *p) {
         set_error("plan was made without a graph; it cannot run");
         return PM_EINVAL;
     }
-    if (p->d_plans) return PM_OK;
+    if (p->device_ready) return PM_OK;
     const size_t nm = p->morph.matched.size();
-    p->bytes_plans = sizeof(DevPlan) * std::max<size_t>(p->plans.size(), 1);
     p->bytes_counters = sizeof(uint64_t) * 2 * std::max<size_t>(nm, 1);
-    p->d_plans = (DevPlan *)dev_alloc(p->bytes_plans, g->device);
     p->d_counters = (uint64_t *)dev_alloc(p->bytes_counters, g->device);
     p->d_ctl = (Control *)dev_alloc(sizeof(Control), g->device);
-    if (!p->d_plans || !p->d_counters || !p->d_ctl) {
-        set_error("device allocation failed (plan tables)");
+    // deferral list: one entry per first-pass chunk at most (capped)
+    const int64_t per_plan = (std::max(g->ntasks[2], int64_t(1)) + 31) / 32;
+    const int64_t nplans = int64_t(std::max(p->rooted.size(), p->free_plans.size()));
+    p->defer_cap = uint32_t(std::min<int64_t>(std::max<int64_t>(per_plan * nplans, 1024), 1 << 22));
+    p->d_defer = (Deferred *)dev_alloc(sizeof(Deferred) * p->defer_cap, g->device);
+    p->d_piece_off = (uint32_t *)dev_alloc(sizeof(uint32_t) * p->defer_cap, g->device);
+    if (!p->d_counters || !p->d_ctl || !p->d_defer || !p->d_piece_off) {
+        set_error("device allocation failed (plan buffers)");
         free_plan_device(p);
         return PM_ENOMEM;
     }
-    cudaError_t e = cudaMemcpy(p->d_plans, p->plans.data(), sizeof(DevPlan) * p->plans.size(),
-                               cudaMemcpyHostToDevice);
-    if (!e && p->op == PM_OP_SUPPORT) {
+    cudaError_t e = cudaSuccess;
+    if (p->op == PM_OP_SUPPORT) {
         p->words = (g->n + 31) / 32;
         p->bytes_bitsets = sizeof(uint32_t) * size_t(p->words) * std::max(p->n_bitsets, 1);
         p->bytes_cols = sizeof(int64_t) * std::max(p->col_off.size(), p->col_src.size()) + 64;
@@ -242,15 +329,180 @@ pm_status ensure_device(pm_query_plan *p) {
             e = cudaMemcpy(p->d_col_src, p->col_src.data(), sizeof(int32_t) * p->col_src.size(),
                            cudaMemcpyHostToDevice);
     }
+    if (!e && (!p->ev0 || !p->ev1)) {
+        e = cudaEventCreate(&p->ev0);
+        if (!e) e = cudaEventCreate(&p->ev1);
+    }
     if (e) {
         free_plan_device(p);
-        return cuda_fail("plan upload", e);
+        return cuda_fail("plan set-up", e);
+    }
+    p->device_ready = true;
+    return PM_OK;
+}
+
+int64_t echunks_for(const std::vector<DevPlan> &plans, const DevTasks &t) {
+    int64_t most = 0;
+    for (const DevPlan &dp : plans)
+        if (dp.kind == PLAN_SETOPS) most = std::max(most, t.ntasks[dp.task_space]);
+    return (most + 31) / 32;
+}
+
+// Counters of the wedge kernel (zeroed once; the kernel leaves them zero).
+pm_status ensure_wedge(pm_query_plan *p, cudaStream_t s) {
+    if (p->d_wedge) return PM_OK;
+    const pm_graph *g = p->g;
+    p->wedge_nblocks = wedge_blocks(g->device);
+    p->bytes_wedge = sizeof(uint32_t) * size_t(g->n) * size_t(p->wedge_nblocks);
+    p->d_wedge = (uint32_t *)dev_alloc(p->bytes_wedge, g->device);
+    if (!p->d_wedge) {
+        p->bytes_wedge = 0;
+        set_error("device allocation failed (wedge counters)");
+        return PM_ENOMEM;
+    }
+    cudaError_t e = cudaMemsetAsync(p->d_wedge, 0, p->bytes_wedge, s);
+    return e ? cuda_fail("wedge counters", e) : PM_OK;
+}
+
+// Launch both matching passes for one plan table on the given tasks.
+pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tasks,
+                       int sample_stride, bool domains, unsigned long long *stats,
+                       cudaStream_t s) {
+    const pm_graph *g = p->g;
+    MatchLaunch L{};
+    L.g = g->dev();
+    L.plans = t.d;
+    L.nplans = int(t.plans.size());
+    L.max_enum = t.max_enum;
+    L.tasks = tasks;
+    L.n_echunks = echunks_for(t.plans, tasks);
+    L.sample_stride = sample_stride;
+    L.counters = p->d_counters;
+    L.bitsets = p->d_bitsets;
+    L.words = p->words;
+    L.ctl = p->d_ctl;
+    L.defer = p->d_defer;
+    L.defer_cap = p->defer_cap;
+    L.piece_off = p->d_piece_off;
+    L.stats = stats;
+    int n_setops = 0;
+    while (n_setops < L.nplans && t.plans[n_setops].kind == PLAN_SETOPS) n_setops++;
+    if (n_setops > 0 && L.n_echunks > 0) {
+        L.nplans = n_setops;
+        const int rc = domains ? launch_domains(L, s) : launch_count(L, s);
+        if (rc) return PM_ECUDA;
+    }
+    for (size_t i = size_t(n_setops); i < t.plans.size(); i++) {
+        if (domains) {
+            set_error("wedge-pair plans count only");
+            return PM_EINVAL;
+        }
+        pm_status st = ensure_wedge(p, s);
+        if (st != PM_OK) return st;
+        if (launch_wedge_pairs(L.g, tasks, t.plans[i].counter, p->d_counters, p->d_wedge,
+                               p->wedge_nblocks, sample_stride, p->d_ctl, s))
+            return PM_ECUDA;
     }
     return PM_OK;
 }
 
+// After an expired deadline the wedge counters may be left non-zero.
+void rezero_wedge(pm_query_plan *p, cudaStream_t s) {
+    if (p->d_wedge) cudaMemsetAsync(p->d_wedge, 0, p->bytes_wedge, s);
+}
+
+// The plans of matched pattern j in family f (0 rooted, 1 free).
+std::vector<DevPlan> family_plans(const pm_query_plan *p, size_t j, int f) {
+    if (f == PM_PLANS_FREE) return {p->free_plans[j]};
+    return std::vector<DevPlan>(p->rooted.begin() + p->rooted_begin[j],
+                                p->rooted.begin() + p->rooted_begin[j + 1]);
+}
+
+// Autotuner: for every matched pattern without a decision, time its rooted
+// plans and its free plan (counting kernels) on the same sample of task
+// chunks (every stride-th chunk, about 4096 chunks, 2 s deadline each) and
+// keep the faster family.  Decisions are cached on the graph under the
+// pattern's canonical key, so later plans on the same graph reuse them.
+pm_status autotune(pm_query_plan *p, cudaStream_t s) {
+    const pm_graph *g = p->g;
+    const size_t nm = p->morph.matched.size();
+    for (size_t j = 0; j < nm; j++) {
+        if (p->choice[j] >= 0) continue;
+        const Key key = canonical(p->morph.matched[j]);
+        {
+            std::lock_guard<std::mutex> lk(g->tune_mu);
+            auto it = g->tuned.find(key);
+            if (it != g->tuned.end()) {
+                p->choice[j] = it->second;
+                continue;
+            }
+        }
+        const DevTasks tasks = all_tasks(g);
+        float best = std::numeric_limits<float>::infinity();
+        int best_f = PM_PLANS_ROOTED;
+        for (int f = PM_PLANS_ROOTED; f <= PM_PLANS_FREE; f++) {
+            PlanTable t;
+            t.plans = family_plans(p, j, f);
+            for (DevPlan &dp : t.plans) dp.counter = 0;
+            pm_status st = upload_table(t, g->device);
+            if (st != PM_OK) return st;
+            const int64_t ech = echunks_for(t.plans, tasks);
+            const int stride = int(std::max<int64_t>(1, ech / 4096));
+            cudaError_t e = cudaMemsetAsync(p->d_counters, 0, p->bytes_counters, s);
+            if (!e && launch_arm(p->d_ctl, uint64_t(2e9), s)) e = cudaErrorLaunchFailure;
+            if (!e) e = cudaEventRecord(p->ev0, s);
+            if (!e && launch_table(p, t, tasks, stride, false, nullptr, s) != PM_OK)
+                e = cudaErrorLaunchFailure;
+            if (!e) e = cudaEventRecord(p->ev1, s);
+            Control ctl{};
+            if (!e) e = cudaMemcpyAsync(&ctl, p->d_ctl, sizeof(Control), cudaMemcpyDeviceToHost, s);
+            if (!e) e = cudaStreamSynchronize(s);
+            float ms = 0.f;
+            if (!e) e = cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+            free_table(t, g->device);
+            if (e) return cuda_fail("autotune", e);
+            if (ctl.status == 1) {
+                ms = std::numeric_limits<float>::infinity();
+                rezero_wedge(p, s);
+            }
+            if (ms < best) { best = ms; best_f = f; }
+        }
+        p->choice[j] = best_f;
+        std::lock_guard<std::mutex> lk(g->tune_mu);
+        g->tuned[key] = best_f;
+    }
+    return PM_OK;
+}
+
+// The table pm_count / pm_support run: each matched pattern's chosen family.
+pm_status prepare_active(pm_query_plan *p, cudaStream_t s) {
+    const size_t nm = p->morph.matched.size();
+    std::vector<int> want(nm);
+    if (p->forced >= 0) {
+        std::fill(want.begin(), want.end(), p->forced);
+    } else {
+        pm_status st = autotune(p, s);
+        if (st != PM_OK) return st;
+        want = p->choice;
+    }
+    std::vector<DevPlan> plans;
+    for (size_t j = 0; j < nm; j++) {
+        std::vector<DevPlan> v = family_plans(p, j, want[j]);
+        plans.insert(plans.end(), v.begin(), v.end());
+    }
+    std::stable_partition(plans.begin(), plans.end(),
+                          [](const DevPlan &dp) { return dp.kind == PLAN_SETOPS; });
+    if (p->active.plans.size() != plans.size() ||
+        std::memcmp(p->active.plans.data(), plans.data(), sizeof(DevPlan) * plans.size()) != 0) {
+        p->active.plans = plans;
+        p->active.dirty = true;
+    }
+    return upload_table(p->active, p->g->device);
+}
+
 pm_status run_count(pm_query_plan *p, void *stream, double timeout_s, const int32_t *roots,
-                    int64_t nroots, uint64_t *counts, uint64_t *matched) {
+                    int64_t nroots, bool use_roots, uint64_t *counts, uint64_t *matched,
+                    uint64_t *alg_bytes = nullptr) {
     if (!p || !counts) {
         set_error("pm_count: null argument");
         return PM_EINVAL;
@@ -271,17 +523,43 @@ pm_status run_count(pm_query_plan *p, void *stream, double timeout_s, const int3
     cudaStream_t s = (cudaStream_t)stream;
     RootTasks rt;
     DevTasks tasks;
-    st = make_tasks(p, roots, nroots, s, rt, &tasks);
+    PlanTable *table;
+    if (use_roots) {
+        st = root_tasks(g, roots, nroots, s, rt, &tasks);
+        if (st != PM_OK) return st;
+        if (p->rooted_table.dirty) p->rooted_table.plans = p->rooted;   // (re)partitioned on upload
+        st = upload_table(p->rooted_table, g->device);
+        table = &p->rooted_table;
+    } else {
+        tasks = all_tasks(g);
+        st = prepare_active(p, s);
+        table = &p->active;
+    }
     if (st != PM_OK) return st;
     const size_t nm = p->morph.matched.size();
     cudaError_t e = cudaMemsetAsync(p->d_counters, 0, p->bytes_counters, s);
     if (e) return cuda_fail("pm_count: memset", e);
     const uint64_t budget = timeout_s > 0 ? uint64_t(timeout_s * 1e9) : 0;
-    if (launch_arm(p->d_ctl, budget, stream)) return PM_ECUDA;
-    if (tasks.ntasks > 0 && !p->plans.empty()) {
-        if (launch_count(g->dev(), p->d_plans, int(p->plans.size()), tasks, p->d_counters,
-                         p->d_ctl, stream))
-            return PM_ECUDA;
+    if (launch_arm(p->d_ctl, budget, s)) return PM_ECUDA;
+    if (alg_bytes && !p->d_stats) {
+        p->d_stats = (unsigned long long *)dev_alloc(256, g->device);
+        if (!p->d_stats) return PM_ENOMEM;
+    }
+    if (alg_bytes) {
+        e = cudaMemsetAsync(p->d_stats, 0, sizeof(unsigned long long), s);
+        if (e) return cuda_fail("pm_count: memset", e);
+    }
+    cudaEventRecord(p->ev0, s);
+    st = launch_table(p, *table, tasks, 1, false, alg_bytes ? p->d_stats : nullptr, s);
+    if (st != PM_OK) return st;
+    cudaEventRecord(p->ev1, s);
+    p->timed = true;
+    if (alg_bytes) {
+        unsigned long long v = 0;
+        e = cudaMemcpyAsync(&v, p->d_stats, sizeof(v), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        if (e) return cuda_fail("pm_count: stats readback", e);
+        *alg_bytes = v;
     }
     std::vector<uint64_t> raw(2 * nm);
     Control ctl;
@@ -291,6 +569,8 @@ pm_status run_count(pm_query_plan *p, void *stream, double timeout_s, const int3
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return cuda_fail("pm_count: kernel or readback", e);
     if (ctl.status == 1) {
+        rezero_wedge(p, s);
+        cudaStreamSynchronize(s);
         set_error("pm_count: deadline expired");
         return PM_ETIMEOUT;
     }
@@ -344,7 +624,7 @@ void pm_free_graph(pm_graph *g) {
     const size_t b_rp = sizeof(int64_t) * (g->n + 1);
     dev_free(g->d_rowptr, b_rp, g->device);
     dev_free(g->d_col, sizeof(int32_t) * std::max<int64_t>(2 * g->m, 1), g->device);
-    dev_free(g->d_off, b_rp, g->device);
+    for (int sp = 0; sp < 3; sp++) dev_free(g->d_off[sp], b_rp, g->device);
     dev_free(g->d_labels, g->n, g->device);
     delete g;
 }
@@ -391,11 +671,16 @@ pm_status pm_plan(const pm_graph *g, const pm_pattern *queries, int32_t nq, pm_o
         nb += p->morph.matched_columns[j];
     }
     p->n_bitsets = nb;
+    p->rooted_begin.push_back(0);
     for (size_t j = 0; j < nm; j++) {
         auto v = compile_plans(p->morph.matched[j], int(j), p->dom_base[j],
-                               p->morph.matched_orbit[j]);
-        p->plans.insert(p->plans.end(), v.begin(), v.end());
+                               p->morph.matched_orbit[j], op == PM_OP_COUNT);
+        p->rooted.insert(p->rooted.end(), v.begin(), v.end());
+        p->rooted_begin.push_back(int(p->rooted.size()));
+        p->free_plans.push_back(compile_free_plan(p->morph.matched[j], int(j), p->dom_base[j],
+                                                  p->morph.matched_orbit[j]));
     }
+    p->choice.assign(nm, -1);
     if (op == PM_OP_SUPPORT) {
         // query columns -> bitset sources
         p->col_off.push_back(0);
@@ -415,7 +700,7 @@ pm_status pm_plan_get_info(const pm_query_plan *p, pm_plan_info *out) {
     if (!p || !out) return PM_EINVAL;
     out->n_queries = int32_t(p->morph.queries.size());
     out->n_matched = int32_t(p->morph.matched.size());
-    out->n_kernels_plans = int32_t(p->plans.size());
+    out->n_kernels_plans = int32_t(p->rooted.size());
     out->op = p->op;
     return PM_OK;
 }
@@ -434,24 +719,60 @@ pm_status pm_plan_matched(const pm_query_plan *p, pm_pattern *out) {
     return PM_OK;
 }
 
-pm_status pm_plan_export(const pm_query_plan *p, void *out, int64_t cap) {
-    static_assert(sizeof(DevPlan) == 96, "plan record layout is part of the ABI");
-    if (!p || !out) return PM_EINVAL;
-    const int64_t need = int64_t(sizeof(DevPlan) * p->plans.size());
+pm_status pm_plan_export(const pm_query_plan *p, int32_t family, void *out, int64_t cap) {
+    static_assert(sizeof(DevPlan) == 112, "plan record layout is part of the ABI");
+    static_assert(offsetof(DevPlan, lv) == 48, "plan record layout is part of the ABI");
+    if (!p || !out || (family != PM_PLANS_ROOTED && family != PM_PLANS_FREE)) return PM_EINVAL;
+    const std::vector<DevPlan> &v = family == PM_PLANS_FREE ? p->free_plans : p->rooted;
+    const int64_t need = int64_t(sizeof(DevPlan) * v.size());
     if (cap < need) {
         set_error("pm_plan_export: buffer too small");
         return PM_EINVAL;
     }
-    std::memcpy(out, p->plans.data(), size_t(need));
+    std::memcpy(out, v.data(), size_t(need));
+    return PM_OK;
+}
+
+pm_status pm_plan_select(pm_query_plan *p, int32_t family) {
+    if (!p || family < PM_PLANS_AUTO || family > PM_PLANS_FREE) return PM_EINVAL;
+    p->forced = family;
+    return PM_OK;
+}
+
+pm_status pm_plan_autotune(pm_query_plan *p, void *stream, int32_t *families) {
+    if (!p) return PM_EINVAL;
+    if (!p->g) {
+        set_error("pm_plan_autotune: plan was made without a graph");
+        return PM_EINVAL;
+    }
+    DeviceGuard dg(p->g->device);
+    if (!dg.ok) return PM_ECUDA;
+    pm_status st = ensure_device(p);
+    if (st != PM_OK) return st;
+    st = autotune(p, (cudaStream_t)stream);
+    if (st != PM_OK) return st;
+    if (families)
+        for (size_t j = 0; j < p->choice.size(); j++) families[j] = p->choice[j];
+    return PM_OK;
+}
+
+pm_status pm_plan_last_kernel_ms(const pm_query_plan *p, float *ms) {
+    if (!p || !ms) return PM_EINVAL;
+    *ms = 0.f;
+    if (!p->timed) return PM_OK;
+    cudaError_t e = cudaEventElapsedTime(ms, p->ev0, p->ev1);
+    if (e) return cuda_fail("pm_plan_last_kernel_ms", e);
     return PM_OK;
 }
 
 void pm_free_plan(pm_query_plan *p) {
     if (!p) return;
-    if (p->g && p->d_plans) {
+    if (p->g && p->device_ready) {
         DeviceGuard dg(p->g->device);
         free_plan_device(p);
     }
+    if (p->ev0) cudaEventDestroy(p->ev0);
+    if (p->ev1) cudaEventDestroy(p->ev1);
     delete p;
 }
 
@@ -472,18 +793,26 @@ pm_status pm_morph(const pm_query_plan *p, const uint64_t *matched, uint64_t *re
 
 pm_status pm_count(pm_query_plan *p, void *stream, double timeout_s, uint64_t *counts,
                    uint64_t *matched) {
-    return run_count(p, stream, timeout_s, nullptr, 0, counts, matched);
+    return run_count(p, stream, timeout_s, nullptr, 0, false, counts, matched);
 }
 
 pm_status pm_count_roots(pm_query_plan *p, void *stream, double timeout_s, const int32_t *roots,
                          int64_t nroots, uint64_t *counts, uint64_t *matched) {
-    if (!roots && nroots > 0) {
-        set_error("pm_count_roots: null roots");
+    if ((!roots && nroots > 0) || nroots < 0) {
+        set_error("pm_count_roots: bad root list");
         return PM_EINVAL;
     }
-    if (nroots < 0) return PM_EINVAL;
     static const int32_t none = 0;
-    return run_count(p, stream, timeout_s, roots ? roots : &none, nroots, counts, matched);
+    return run_count(p, stream, timeout_s, roots ? roots : &none, nroots, true, counts, matched);
+}
+
+pm_status pm_count_instrumented(pm_query_plan *p, void *stream, uint64_t *counts,
+                                uint64_t *alg_bytes) {
+    if (!alg_bytes) {
+        set_error("pm_count_instrumented: null alg_bytes");
+        return PM_EINVAL;
+    }
+    return run_count(p, stream, 0.0, nullptr, 0, false, counts, nullptr, alg_bytes);
 }
 
 pm_status pm_support(pm_query_plan *p, void *stream, double timeout_s, uint64_t threshold,
@@ -506,23 +835,22 @@ pm_status pm_support(pm_query_plan *p, void *stream, double timeout_s, uint64_t 
     pm_status st = ensure_device(p);
     if (st != PM_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    RootTasks rt;
-    DevTasks tasks;
-    st = make_tasks(p, nullptr, 0, s, rt, &tasks);
+    st = prepare_active(p, s);
     if (st != PM_OK) return st;
+    const DevTasks tasks = all_tasks(g);
     const size_t ncols = p->col_off.size() - 1;
     cudaError_t e = cudaMemsetAsync(p->d_bitsets, 0, p->bytes_bitsets, s);
     if (!e) e = cudaMemsetAsync(p->d_popc, 0, sizeof(unsigned long long) * std::max<size_t>(ncols, 1), s);
     if (e) return cuda_fail("pm_support: memset", e);
     const uint64_t budget = timeout_s > 0 ? uint64_t(timeout_s * 1e9) : 0;
-    if (launch_arm(p->d_ctl, budget, stream)) return PM_ECUDA;
-    if (tasks.ntasks > 0 && !p->plans.empty()) {
-        if (launch_domains(g->dev(), p->d_plans, int(p->plans.size()), tasks, p->d_bitsets,
-                           p->words, p->d_ctl, stream))
-            return PM_ECUDA;
-    }
+    if (launch_arm(p->d_ctl, budget, s)) return PM_ECUDA;
+    cudaEventRecord(p->ev0, s);
+    st = launch_table(p, p->active, tasks, 1, true, nullptr, s);
+    if (st != PM_OK) return st;
+    cudaEventRecord(p->ev1, s);
+    p->timed = true;
     if (launch_mni_reduce(p->d_bitsets, p->words, p->d_col_off, p->d_col_src, int(ncols),
-                          p->d_popc, stream))
+                          p->d_popc, s))
         return PM_ECUDA;
     std::vector<unsigned long long> popc(ncols);
     Control ctl;

@@ -115,9 +115,23 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
             g->labels.resize(n);
             for (int64_t r = 0; r < n; r++) g->labels[r] = labels[old_of[r]];
         }
-        // 5. task offsets for the implicit root list n-1, ..., 0
-        std::vector<int64_t> off(n + 1, 0);
-        for (int64_t i = 0; i < n; i++) off[i + 1] = off[i] + g->lowdeg[n - 1 - i];
+        // 5. task offsets for the implicit root list n-1, ..., 0, per task
+        //    space: lower neighbours, higher neighbours, all neighbours
+        std::vector<int64_t> off[3];
+        for (int sp = 0; sp < 3; sp++) off[sp].assign(n + 1, 0);
+        for (int64_t i = 0; i < n; i++) {
+            const int64_t r = n - 1 - i;
+            const int64_t d = rowptr[r + 1] - rowptr[r];
+            off[0][i + 1] = off[0][i] + g->lowdeg[r];
+            off[1][i + 1] = off[1][i] + (d - g->lowdeg[r]);
+            off[2][i + 1] = off[2][i] + d;
+        }
+        for (int sp = 0; sp < 3; sp++) g->ntasks[sp] = off[sp][n];
+        if (nnz >= (int64_t(1) << 32)) {
+            set_error("pm_load_graph: more than 2^32 - 1 adjacency entries");
+            delete g;
+            return PM_EUNSUPPORTED;
+        }
 
         // 6. upload
         int prev = 0;
@@ -131,19 +145,22 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
         const size_t b_rp = sizeof(int64_t) * (n + 1), b_col = sizeof(int32_t) * std::max<int64_t>(nnz, 1);
         g->d_rowptr = (int64_t *)dev_alloc(b_rp, device);
         g->d_col = (int32_t *)dev_alloc(b_col, device);
-        g->d_off = (int64_t *)dev_alloc(b_rp, device);
+        for (int sp = 0; sp < 3; sp++) g->d_off[sp] = (int64_t *)dev_alloc(b_rp, device);
         if (labels) g->d_labels = (uint8_t *)dev_alloc(n, device);
-        if (!g->d_rowptr || !g->d_col || !g->d_off || (labels && !g->d_labels)) {
+        if (!g->d_rowptr || !g->d_col || !g->d_off[0] || !g->d_off[1] || !g->d_off[2] ||
+            (labels && !g->d_labels)) {
             set_error("pm_load_graph: device allocation failed");
             pm_free_graph(g);
             cudaSetDevice(prev);
             return PM_ENOMEM;
         }
-        g->bytes = 2 * b_rp + b_col + (labels ? n : 0);
+        g->bytes = 4 * b_rp + b_col + (labels ? n : 0);
         cudaError_t e1 = cudaMemcpyAsync(g->d_rowptr, rowptr.data(), b_rp, cudaMemcpyHostToDevice, s);
         cudaError_t e2 = nnz ? cudaMemcpyAsync(g->d_col, col.data(), sizeof(int32_t) * nnz,
                                                cudaMemcpyHostToDevice, s) : cudaSuccess;
-        cudaError_t e3 = cudaMemcpyAsync(g->d_off, off.data(), b_rp, cudaMemcpyHostToDevice, s);
+        cudaError_t e3 = cudaSuccess;
+        for (int sp = 0; sp < 3 && !e3; sp++)
+            e3 = cudaMemcpyAsync(g->d_off[sp], off[sp].data(), b_rp, cudaMemcpyHostToDevice, s);
         cudaError_t e4 = labels ? cudaMemcpyAsync(g->d_labels, g->labels.data(), n,
                                                   cudaMemcpyHostToDevice, s) : cudaSuccess;
         cudaError_t e5 = cudaStreamSynchronize(s);

@@ -3,6 +3,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -20,8 +22,13 @@ struct pm_graph {
     int64_t *d_rowptr = nullptr;
     int32_t *d_col = nullptr;
     uint8_t *d_labels = nullptr;
-    int64_t *d_off = nullptr;        // task offsets for the implicit all-roots list
+    int64_t *d_off[3] = {nullptr, nullptr, nullptr};  // task offsets per TaskSpace, all roots
+    int64_t ntasks[3] = {0, 0, 0};
     size_t bytes = 0;
+    // Autotuner cache: canonical pattern key -> chosen plan family
+    // (0 rooted, 1 free); shared by every plan made on this graph.
+    mutable std::mutex tune_mu;
+    mutable std::map<pm::Key, int> tuned;
     pm::DevGraph dev() const {
         return pm::DevGraph{n, 2 * m, d_rowptr, d_col, d_labels};
     }
@@ -52,9 +59,13 @@ struct MorphPlan {
 pm_status morph_select(const std::vector<Pat> &queries, pm_op op, pm_morph_mode mode,
                        MorphPlan &out, std::string *why);
 
-// Matching plans of one pattern (one per automorphism orbit).
+// Rooted matching plans of one pattern (one per automorphism orbit).
+// counting: the plans serve pm_count (a 4-cycle may then use the wedge kernel).
 std::vector<DevPlan> compile_plans(const Pat &p, int counter, int dom_base,
-                                   const std::vector<int> &column_of_vertex);
+                                   const std::vector<int> &column_of_vertex, bool counting);
+// The free matching plan of one pattern (whole automorphism group broken).
+DevPlan compile_free_plan(const Pat &p, int counter, int dom_base,
+                          const std::vector<int> &column_of_vertex);
 
 // Device memory through the configured allocator.
 void *dev_alloc(size_t bytes, int device);
@@ -65,10 +76,34 @@ void set_error(const std::string &msg);
 // Kernel launchers (match.cu).
 // Resets the control block and arms the deadline (budget_ns = 0: none).
 int launch_arm(Control *d_ctl, uint64_t budget_ns, void *stream);
-int launch_count(const DevGraph &g, const DevPlan *d_plans, int nplans, const DevTasks &tasks,
-                 uint64_t *d_counters, Control *d_ctl, void *stream);
-int launch_domains(const DevGraph &g, const DevPlan *d_plans, int nplans, const DevTasks &tasks,
-                   uint32_t *d_bitsets, int64_t words_per_bitset, Control *d_ctl, void *stream);
+// One matching launch (both passes).  max_enum: largest n_enum over the
+// plans (sizes the per-warp level buffers); stats (nullable): instrumented
+// run adding the algorithmic bytes read.
+struct MatchLaunch {
+    DevGraph g;
+    const DevPlan *plans;
+    int nplans;
+    int max_enum;
+    DevTasks tasks;
+    int64_t n_echunks;         // 32-task chunks per plan (largest task space in the launch)
+    int32_t sample_stride;     // 1 = every chunk; s > 1 = every s-th chunk (autotuning)
+    uint64_t *counters;        // counting
+    uint32_t *bitsets;         // MNI domains
+    int64_t words;
+    Control *ctl;
+    Deferred *defer;
+    uint32_t defer_cap;
+    uint32_t *piece_off;
+    unsigned long long *stats;
+};
+int launch_count(const MatchLaunch &L, void *stream);
+int launch_domains(const MatchLaunch &L, void *stream);
+// Wedge-pair kernel for one PLAN_WEDGE_PAIRS plan over the lower task space
+// of `tasks`; scratch: blocks * n uint32 counters, zero on entry and exit.
+int wedge_blocks(int device);
+int launch_wedge_pairs(const DevGraph &g, const DevTasks &tasks, int counter, uint64_t *counters,
+                       uint32_t *scratch, int blocks, int sample_stride, Control *ctl,
+                       void *stream);
 int launch_mni_reduce(const uint32_t *d_bitsets, int64_t words_per_bitset, const int32_t *d_src_off,
                       const int32_t *d_src, int n_columns, unsigned long long *d_popc,
                       void *stream);

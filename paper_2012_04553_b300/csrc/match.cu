@@ -5,18 +5,26 @@
 // Work decomposition.  A task chunk is one plan and 32 consecutive oriented
 // edges (root, v) with v < root, roots taken highest-ranked first so hub work
 // starts early.  Warps pull chunks from one global counter (persistent grid,
-// one launch for every plan of every matched pattern).
+// one launch for every plan of every matched pattern).  A chunk whose
+// flattened second-level candidate range exceeds the plan's split size keeps
+// only the first `split` candidates and appends the rest to a deferred list;
+// a scan kernel turns the list into split-sized pieces that a second pass
+// of the same kernel spreads over all warps (hub roots otherwise leave a
+// few warps running long after the rest have finished).
 //
 // Set operations.  A level's candidate set is never materialised: it is the
 // bounded slice of the smallest intersected adjacency list, cut by two binary
-// searches to the (gt, lt) id window, and filtered 32 elements at a time, one
-// per lane (membership in the other intersected lists and absence from the
-// differenced lists by binary search; injectivity and label tests).  Survivors
-// come from __ballot_sync and are walked in order, which gives the nested
-// depth-first enumeration with O(levels) state per warp and no scratch.
-// The last `tail` levels are counted as C(|C|, tail); when C is one adjacency
-// range minus known vertices, |C| comes from binary searches alone, and the
-// lanes of the warp each finish a different prefix in parallel.
+// searches to the (gt, lt) id window, and filtered one element per lane
+// (membership in the other intersected lists and absence from the
+// differenced lists by binary search; injectivity and label tests).  Each
+// warp buffers up to 64 prefixes per level in shared memory and flattens the
+// slices of all buffered prefixes into one index space, so a step always
+// gives every lane a (prefix, candidate) pair whatever the set sizes;
+// survivors are compacted with __ballot_sync into the next level's buffer,
+// which is expanded as soon as it holds 32 prefixes (depth-first over
+// batches).  The last `tail` levels are counted as C(|C|, tail); when C is
+// one adjacency range minus known vertices, |C| comes from binary searches
+// alone, one prefix per lane.
 //
 // Aggregation.  Counts accumulate per lane in 128 bits, are summed across the
 // warp, and are added to the pattern's 128-bit counter with a carry into the
@@ -33,17 +41,8 @@ namespace pm {
 typedef unsigned __int128 u128;
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int WARPS_PER_BLOCK = 8;
-constexpr int CHUNK = 32;
-
-struct WarpState {
-    int64_t base[PLAN_KMAX];
-    int32_t len[PLAN_KMAX];
-    int32_t pos[PLAN_KMAX];
-    int32_t cstart[PLAN_KMAX];
-    uint32_t mask[PLAN_KMAX];
-    int32_t src[PLAN_KMAX];
-};
+constexpr int CAP = 64;       // prefixes per level buffer
+constexpr int WARPS = 4;      // warps per block
 
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
@@ -51,11 +50,12 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-__device__ __forceinline__ int64_t lower_bound_dev(const int32_t *__restrict__ a, int64_t len,
+// First index in a[0, len) whose value is >= key.
+__device__ __forceinline__ int32_t lower_bound_dev(const int32_t *__restrict__ a, int32_t len,
                                                    int32_t key) {
-    int64_t lo = 0, hi = len;
+    int32_t lo = 0, hi = len;
     while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
+        const int32_t mid = int32_t((uint32_t(lo) + uint32_t(hi)) >> 1);
         if (__ldg(a + mid) < key) lo = mid + 1;
         else hi = mid;
     }
@@ -63,23 +63,15 @@ __device__ __forceinline__ int64_t lower_bound_dev(const int32_t *__restrict__ a
 }
 
 __device__ __forceinline__ bool contains(const DevGraph &g, int32_t v, int32_t x) {
-    const int64_t b = __ldg(g.rowptr + v), e = __ldg(g.rowptr + v + 1);
+    const int64_t b = __ldg(g.rowptr + v);
+    const int32_t len = int32_t(__ldg(g.rowptr + v + 1) - b);
     const int32_t *a = g.col + b;
-    const int64_t len = e - b;
-    const int64_t p = lower_bound_dev(a, len, x);
+    const int32_t p = lower_bound_dev(a, len, x);
     return p < len && __ldg(a + p) == x;
 }
 
-__device__ __forceinline__ u128 binom(int64_t c, int r) {
-    if (r == 0) return 1;
-    if (c < r) return 0;
-    u128 res = 1;
-    for (int i = 0; i < r; i++) res = res * u128(uint64_t(c - i)) / u128(uint64_t(i + 1));
-    return res;
-}
-
-// m[] holds bound vertices for levels < L in registers; every access uses a
-// compile-time index so the array never leaves registers.
+// Bound vertices of levels 0..L in registers; every access uses a
+// compile-time index (unrolled loops) so the array never leaves registers.
 struct Bound {
     int32_t v[PLAN_KMAX];
     __device__ __forceinline__ int32_t get(int j) const {
@@ -97,10 +89,10 @@ struct Bound {
 };
 
 struct Slice {
-    int64_t base;
+    uint32_t base;     // index into col
     int32_t len;
     int32_t src;
-    int32_t lo, hi;   // open id window (lo, hi)
+    int32_t lo, hi;    // open id window (lo, hi)
 };
 
 // Candidate slice of level `lv` given the bound prefix.
@@ -108,29 +100,30 @@ __device__ __forceinline__ Slice make_slice(const DevGraph &g, const DevLevel &l
     Slice s;
     int32_t hi = INT_MAX, lo = -1;
     int best = -1;
-    int64_t bestd = LLONG_MAX, bestb = 0;
+    int32_t bestd = INT_MAX;
+    int64_t bestb = 0;
 #pragma unroll
     for (int j = 0; j < PLAN_KMAX; j++) {
         if ((lv.lt >> j) & 1) hi = min(hi, m.v[j]);
         if ((lv.gt >> j) & 1) lo = max(lo, m.v[j]);
         if ((lv.isect >> j) & 1) {
             const int64_t b = __ldg(g.rowptr + m.v[j]);
-            const int64_t d = __ldg(g.rowptr + m.v[j] + 1) - b;
+            const int32_t d = int32_t(__ldg(g.rowptr + m.v[j] + 1) - b);
             if (d < bestd) { bestd = d; best = j; bestb = b; }
         }
     }
+    s.lo = lo;
+    s.hi = hi;
     if (best < 0) {   // no intersected list: cannot happen for levels >= 1
-        s.base = 0; s.len = 0; s.src = 0; s.lo = lo; s.hi = hi;
+        s.base = 0; s.len = 0; s.src = 0;
         return s;
     }
     const int32_t *a = g.col + bestb;
-    const int64_t a0 = lo < 0 ? 0 : lower_bound_dev(a, bestd, lo + 1);
-    const int64_t a1 = hi == INT_MAX ? bestd : lower_bound_dev(a, bestd, hi);
-    s.base = bestb + a0;
-    s.len = a1 > a0 ? int32_t(a1 - a0) : 0;
+    const int32_t a0 = lo < 0 ? 0 : lower_bound_dev(a, bestd, lo + 1);
+    const int32_t a1 = hi == INT_MAX ? bestd : lower_bound_dev(a, bestd, hi);
+    s.base = uint32_t(bestb + a0);
+    s.len = a1 > a0 ? a1 - a0 : 0;
     s.src = best;
-    s.lo = lo;
-    s.hi = hi;
     return s;
 }
 
@@ -165,157 +158,236 @@ __device__ __forceinline__ int64_t closed_count(const DevGraph &g, const DevLeve
     return c;
 }
 
-// |C| for a scanned final stage, computed by the whole warp (same on all lanes).
-__device__ __forceinline__ int64_t scan_count(const DevGraph &g, const DevLevel &lv, const Bound &m,
-                                              int lane) {
-    const Slice s = make_slice(g, lv, m);
-    int64_t c = 0;
-    for (int32_t off = 0; off < s.len; off += 32) {
-        const int32_t i = off + lane;
-        bool ok = false;
-        if (i < s.len) ok = admissible(g, lv, s.src, m, __ldg(g.col + s.base + i));
-        c += __popc(__ballot_sync(FULL, ok));
-    }
-    return c;
-}
-
 __device__ __forceinline__ void set_bit(uint32_t *bits, int32_t x) {
     uint32_t *w = bits + (x >> 5);
     const uint32_t b = 1u << (x & 31);
     if (!(*(volatile uint32_t *)w & b)) atomicOr(w, b);
 }
 
-// MNI: record the tail candidate set (all lanes cooperate) and the prefix.
-__device__ void record_domains(const DevGraph &g, const DevPlan &P, const Bound &m, int lane,
-                               uint32_t *bitsets, int64_t words) {
-    const DevLevel &lv = P.lv[P.n_enum];
-    const Slice s = make_slice(g, lv, m);
-    int64_t c = 0;
-    if (P.tail > 1) {
-        for (int32_t off = 0; off < s.len; off += 32) {
-            const int32_t i = off + lane;
-            bool ok = i < s.len && admissible(g, lv, s.src, m, __ldg(g.col + s.base + i));
-            c += __popc(__ballot_sync(FULL, ok));
-        }
-        if (c < P.tail) return;
+// Exact C(c, r) for r <= 6: 64-bit arithmetic for r <= 2, otherwise the
+// 128-bit falling product divided by r! with 32-bit-digit long division.
+__device__ __forceinline__ u128 binom_fast(int64_t c, int r) {
+    if (r <= 0) return r == 0 ? 1 : 0;
+    if (c < r) return 0;
+    const uint64_t uc = uint64_t(c);
+    if (r == 1) return uc;
+    if (r == 2) return (uc & 1) ? u128(uc) * ((uc - 1) >> 1) : u128(uc >> 1) * (uc - 1);
+    u128 num = 1;
+    uint32_t den = 1;
+    for (int i = 0; i < r; i++) {
+        num *= u128(uc - uint64_t(i));
+        den *= uint32_t(i + 1);
     }
-    uint32_t *tail_bits = bitsets + int64_t(P.dom_base + lv.column) * words;
-    bool any = false;
-    for (int32_t off = 0; off < s.len; off += 32) {
-        const int32_t i = off + lane;
-        bool ok = false;
-        int32_t x = 0;
-        if (i < s.len) {
-            x = __ldg(g.col + s.base + i);
-            ok = admissible(g, lv, s.src, m, x);
-        }
-        if (ok) set_bit(tail_bits, x);
-        any |= __any_sync(FULL, ok);
+    uint64_t rem = 0;
+    u128 q = 0;
+#pragma unroll
+    for (int d = 3; d >= 0; d--) {
+        const uint64_t cur = (rem << 32) | uint64_t(uint32_t(num >> (32 * d)));
+        q |= u128(cur / den) << (32 * d);
+        rem = cur % den;
     }
-    if (P.tail == 0) any = true;
-    if (any && lane < P.n_enum) {
-        const int32_t v = m.get(lane);
-        set_bit(bitsets + int64_t(P.dom_base + P.lv[lane].column) * words, v);
-    }
+    return q;
 }
 
-template <bool DOMAINS>
-__device__ u128 run_dfs(const DevGraph &g, const DevPlan &P, WarpState &S, Bound m, int lane,
-                        uint32_t *bitsets, int64_t words, uint64_t deadline, int *status) {
-    u128 acc = 0;
-    const int last = P.n_enum - 1;
-    if (P.n_enum == 2) {
+// ---------------------------------------------------------------------------
+// Warp-batched depth-first enumeration (see the file comment).
+
+struct LevelBuf {
+    int32_t v[CAP];
+    uint32_t base[CAP];    // slice start (index into col) for the next level
+    int32_t scan[CAP];     // inclusive prefix sum of slice lengths
+    uint8_t parent[CAP];
+    uint8_t src[CAP];      // intersected level used as the slice source
+    int32_t cnt, t, total, pad;
+};
+
+struct WarpTail {
+    int32_t fcount[CAP];   // per-prefix final-stage counts / flags
+};
+
+__device__ __forceinline__ Bound tuple_of(const LevelBuf *B, int L, int p) {
+    Bound m;
+    int q = p;
+#pragma unroll
+    for (int l = PLAN_KMAX - 1; l >= 0; l--) {
+        m.v[l] = 0;
+        if (l <= L) {
+            m.v[l] = B[l].v[q];
+            q = B[l].parent[q];
+        }
+    }
+    return m;
+}
+
+// Warp-wide inclusive scan over the (up to 64) slice lengths of a buffer.
+__device__ __forceinline__ void store_scan(LevelBuf &b, int lane, int32_t len0, int32_t len1) {
+    int32_t a = len0, c = len1;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int32_t ya = __shfl_up_sync(FULL, a, off);
+        const int32_t yc = __shfl_up_sync(FULL, c, off);
+        if (lane >= off) { a += ya; c += yc; }
+    }
+    const int32_t first = __shfl_sync(FULL, a, 31);
+    b.scan[lane] = a;
+    b.scan[lane + 32] = c + first;
+}
+
+template <bool STATS>
+__device__ __forceinline__ uint64_t operand_bytes(const DevGraph &g, const DevLevel &lv,
+                                                  const Slice &s, const Bound &m) {
+    if (!STATS) return 0;
+    uint64_t bytes = 4ull * uint64_t(s.len) + 16;
+#pragma unroll
+    for (int j = 0; j < PLAN_KMAX; j++) {
+        if ((((lv.isect >> j) & 1) && j != s.src) || ((lv.diff >> j) & 1)) {
+            const int64_t b = __ldg(g.rowptr + m.v[j]);
+            const int32_t d = int32_t(__ldg(g.rowptr + m.v[j] + 1) - b);
+            const int32_t a0 = s.lo < 0 ? 0 : lower_bound_dev(g.col + b, d, s.lo + 1);
+            const int32_t a1 = lower_bound_dev(g.col + b, d, s.hi);
+            bytes += 16 + 4ull * uint64_t(a1 > a0 ? a1 - a0 : 0);
+        }
+    }
+    return bytes;
+}
+
+// Slices of buffer L's prefixes for level L+1, and their scan.
+template <bool STATS>
+__device__ __forceinline__ void setup_level(const DevGraph &g, const DevPlan &P, LevelBuf *B, int L,
+                                            int lane, uint64_t &stat) {
+    LevelBuf &b = B[L];
+    const int cnt = b.cnt;
+    int32_t lens[2] = {0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int p = lane + 32 * h;
+        if (p < cnt) {
+            const Bound m = tuple_of(B, L, p);
+            const Slice s = make_slice(g, P.lv[L + 1], m);
+            b.base[p] = s.base;
+            b.src[p] = uint8_t(s.src);
+            lens[h] = s.len;
+            stat += operand_bytes<STATS>(g, P.lv[L + 1], s, m);
+        }
+    }
+    store_scan(b, lane, lens[0], lens[1]);
+    __syncwarp();
+    if (lane == 0) {
+        b.t = 0;
+        b.total = cnt > 0 ? b.scan[cnt - 1] : 0;
+    }
+    __syncwarp();
+}
+
+// Prefix that owns flattened candidate index e of a buffer.
+__device__ __forceinline__ int prefix_of(const LevelBuf &b, int32_t e) {
+    int lo = 0, hi = b.cnt;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (b.scan[mid] <= e) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool deadline_hit(uint64_t deadline, int *status, int lane, uint32_t &tick) {
+    if (!deadline || ((++tick & 63u) != 0)) return false;
+    int hit = 0;
+    if (lane == 0) {
+        hit = *(volatile int *)status;
+        if (!hit && global_ns() > deadline) {
+            atomicExch(status, 1);
+            hit = 1;
+        }
+    }
+    return __shfl_sync(FULL, hit, 0) != 0;
+}
+
+// Final stage over the prefixes of buffer L: levels n_enum .. k-1 counted.
+// For the flattened (scanned) stage only candidates [t_begin, t_end) are
+// visited; a range narrower than the whole buffer is used only when
+// tail == 1 in counting mode, where partial counts add up.
+template <bool DOMAINS, bool STATS>
+__device__ bool final_stage(const DevGraph &g, const DevPlan &P, LevelBuf *B, WarpTail &T, int L,
+                            int32_t t_begin, int32_t t_end, int lane, u128 &acc, uint64_t &stat,
+                            uint32_t *bitsets, int64_t words, uint64_t deadline, int *status,
+                            uint32_t &tick) {
+    LevelBuf &b = B[L];
+    const int cnt = b.cnt;
+    if (P.tail == 0) {   // k == 2: each prefix is a match
         if (DOMAINS) {
-            record_domains(g, P, m, lane, bitsets, words);
-        } else if (P.tail == 0) {
-            if (lane == 0) acc += 1;
-        } else {
-            const int64_t c = scan_count(g, P.lv[2], m, lane);
-            if (lane == 0) acc += binom(c, P.tail);
+            for (int p = lane; p < cnt; p += 32) {
+                const Bound m = tuple_of(B, L, p);
+#pragma unroll
+                for (int l = 0; l < 2; l++)
+                    set_bit(bitsets + int64_t(P.dom_base + P.lv[l].column) * words, m.v[l]);
+            }
+        } else if (lane == 0) {
+            acc += uint64_t(cnt);
         }
-        return acc;
+        return true;
     }
-    auto setup = [&](int L) {
-        const Slice s = make_slice(g, P.lv[L], m);
-        if (lane == 0) {
-            S.base[L] = s.base;
-            S.len[L] = s.len;
-            S.pos[L] = 0;
-            S.mask[L] = 0;
-            S.src[L] = s.src;
+    const DevLevel &lv = P.lv[P.n_enum];
+    if (!DOMAINS && P.closed) {
+        for (int p = lane; p < cnt; p += 32) {
+            const Bound m = tuple_of(B, L, p);
+            acc += binom_fast(closed_count(g, lv, m), P.tail);
+            if (STATS) stat += 24 + 8ull * __popc(lv.neq);
         }
+        return true;
+    }
+    setup_level<STATS>(g, P, B, L, lane, stat);
+    const int32_t total = min(b.total, t_end);
+    const int passes = (DOMAINS && P.tail > 1) ? 2 : 1;
+    for (int pass = 0; pass < passes; pass++) {
+        const bool counting = DOMAINS ? (pass == 0 && P.tail > 1) : true;
+        if (pass == 0)
+            for (int p = lane; p < CAP; p += 32) T.fcount[p] = 0;
         __syncwarp();
-    };
-    int L = 2;
-    setup(L);
-    uint32_t iter = 0;
-    while (L >= 2) {
-        if (deadline && ((++iter & 1023u) == 0)) {
-            uint64_t t = 0;
-            if (lane == 0) t = global_ns();
-            t = __shfl_sync(FULL, t, 0);
-            if (t > deadline) {
-                if (lane == 0) atomicExch(status, 1);
-                return acc;
-            }
-        }
-        const uint32_t mk = S.mask[L];
-        if (mk == 0) {
-            const int32_t pos = S.pos[L], len = S.len[L];
-            if (pos >= len) {
-                L--;
-                continue;
-            }
-            const int32_t i = pos + lane;
+        uint32_t *tail_bits = DOMAINS ? bitsets + int64_t(P.dom_base + lv.column) * words : nullptr;
+        for (int32_t t0 = t_begin; t0 < total; t0 += 32) {
+            if (deadline_hit(deadline, status, lane, tick)) return false;
+            const int32_t e = t0 + lane;
             bool ok = false;
+            int p = 0;
             int32_t x = 0;
-            if (i < len) {
-                x = __ldg(g.col + S.base[L] + i);
-                ok = admissible(g, P.lv[L], S.src[L], m, x);
+            if (e < total) {
+                p = prefix_of(b, e);
+                const int32_t off = e - (p ? b.scan[p - 1] : 0);
+                x = __ldg(g.col + b.base[p] + off);
+                const Bound m = tuple_of(B, L, p);
+                ok = admissible(g, lv, b.src[p], m, x);
             }
-            if (!DOMAINS && L == last && P.closed) {
-                // lanes finish different prefixes in parallel
-                if (ok) {
-                    Bound mm = m;
-                    mm.set(L, x);
-                    acc += binom(closed_count(g, P.lv[L + 1], mm), P.tail);
-                }
-                __syncwarp();
-                if (lane == 0) S.pos[L] = pos + 32;
-                __syncwarp();
-                continue;
-            }
-            const uint32_t b = __ballot_sync(FULL, ok);
-            __syncwarp();
-            if (lane == 0) {
-                S.mask[L] = b;
-                S.cstart[L] = pos;
-                S.pos[L] = pos + 32;
-            }
-            __syncwarp();
-            continue;
-        }
-        const int bit = __ffs(mk) - 1;
-        const int32_t x = __ldg(g.col + S.base[L] + S.cstart[L] + bit);
-        __syncwarp();
-        if (lane == 0) S.mask[L] = mk & (mk - 1);
-        __syncwarp();
-        m.set(L, x);
-        if (L == last) {
-            if (DOMAINS) {
-                record_domains(g, P, m, lane, bitsets, words);
-            } else if (P.tail == 0) {
-                if (lane == 0) acc += 1;
+            if (!DOMAINS && P.tail == 1) {
+                if (ok) acc += 1;
+            } else if (counting) {
+                if (ok) atomicAdd(&T.fcount[p], 1);
             } else {
-                const int64_t c = scan_count(g, P.lv[L + 1], m, lane);
-                if (lane == 0) acc += binom(c, P.tail);
+                // record domains: tail == 1 flags the prefix; tail > 1 needs >= tail survivors
+                if (ok && (P.tail == 1 || T.fcount[p] >= P.tail)) {
+                    set_bit(tail_bits, x);
+                    if (P.tail == 1) T.fcount[p] = 1;
+                }
             }
-        } else {
-            L++;
-            setup(L);
+        }
+        __syncwarp();
+    }
+    if (!DOMAINS && P.tail > 1) {
+        for (int p = lane; p < cnt; p += 32) acc += binom_fast(T.fcount[p], P.tail);
+    }
+    if (DOMAINS) {
+        for (int p = lane; p < cnt; p += 32) {
+            if (T.fcount[p] >= (P.tail > 1 ? P.tail : 1)) {
+                const Bound m = tuple_of(B, L, p);
+#pragma unroll
+                for (int l = 0; l < PLAN_KMAX; l++)
+                    if (l < P.n_enum)
+                        set_bit(bitsets + int64_t(P.dom_base + P.lv[l].column) * words, m.v[l]);
+            }
         }
     }
-    return acc;
+    __syncwarp();
+    return true;
 }
 
 __device__ __forceinline__ u128 shfl_xor_u128(u128 v, int mask) {
@@ -332,85 +404,263 @@ __device__ __forceinline__ void add_u128(uint64_t *counter, u128 v) {
     if (hi) atomicAdd((unsigned long long *)counter + 1, hi);
 }
 
-template <bool DOMAINS>
-__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
-match_kernel(DevGraph g, const DevPlan *__restrict__ plans, int nplans, DevTasks tasks,
-             uint64_t *counters, uint32_t *bitsets, int64_t words, Control *ctl) {
-    __shared__ WarpState warp_state[WARPS_PER_BLOCK];
+struct KernelArgs {
+    DevGraph g;
+    const DevPlan *plans;
+    int nplans;
+    int n_buf;
+    DevTasks tasks;
+    int64_t n_echunks;          // 32-task chunks per plan in the first pass
+    int32_t sample_stride;      // first pass visits chunks (c / nplans) % stride == 0 only
+    uint64_t *counters;
+    uint32_t *bitsets;
+    int64_t words;
+    Control *ctl;
+    Deferred *defer;            // deferred chunks (first pass appends, second pass reads)
+    uint32_t defer_cap;
+    const uint32_t *piece_off;  // exclusive scan of pieces per deferred chunk
+    unsigned long long *stats;
+};
+
+// One chunk (plan c % nplans, oriented edges (c / nplans) * 32 + 0..31),
+// restricted to flattened second-level candidates [t_begin, t_end).  In the
+// first pass (may_defer) a range larger than the plan's split is cut to the
+// split and the remainder deferred.  Returns false once the deadline expired.
+template <bool DOMAINS, bool STATS>
+__device__ bool process_chunk(const KernelArgs &A, LevelBuf *B, WarpTail &T, unsigned long long c,
+                              int32_t t_begin, int32_t t_end, bool may_defer, int lane,
+                              uint64_t deadline, uint32_t &tick, uint64_t &stat) {
+    const DevGraph &g = A.g;
+    int *status = &A.ctl->status;
+    const DevPlan &P = A.plans[c % A.nplans];
+    const int64_t e = int64_t(c / A.nplans) * 32 + lane;
+    const int sp = P.task_space;
+    const int64_t *off = A.tasks.off[sp];
+    int32_t root = -1, v1 = -1;
+    if (e < A.tasks.ntasks[sp]) {
+        int64_t lo = 0, hi = A.tasks.nroots;
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (__ldg(off + mid) <= e) lo = mid;
+            else hi = mid;
+        }
+        root = A.tasks.roots ? __ldg(A.tasks.roots + lo) : int32_t(g.n - 1 - lo);
+        const int64_t idx = e - __ldg(off + lo);
+        // lower and all-neighbour tasks index the row from its start, higher
+        // neighbour tasks from the first neighbour above the root
+        const int64_t row = sp == TASKS_UPPER
+            ? __ldg(g.rowptr + root + 1) - (__ldg(off + lo + 1) - __ldg(off + lo))
+            : __ldg(g.rowptr + root);
+        v1 = __ldg(g.col + row + idx);
+        if (P.lv[0].label >= 0 && __ldg(g.labels + root) != uint8_t(P.lv[0].label)) root = -1;
+        if (P.lv[1].label >= 0 && __ldg(g.labels + v1) != uint8_t(P.lv[1].label)) root = -1;
+        if (STATS && may_defer) stat += 28;   // a second-pass piece re-reads its chunk's tasks
+    }
+    // tasks -> buffers 0 (roots) and 1 (second vertices)
+    const uint32_t vm = __ballot_sync(FULL, root >= 0);
+    if (root >= 0) {
+        const int pos = __popc(vm & ((1u << lane) - 1));
+        B[0].v[pos] = root;
+        B[0].parent[pos] = 0;
+        B[1].v[pos] = v1;
+        B[1].parent[pos] = uint8_t(pos);
+    }
+    if (lane == 0) {
+        B[0].cnt = B[1].cnt = __popc(vm);
+        for (int l = 2; l < A.n_buf; l++) B[l].cnt = 0;
+    }
+    __syncwarp();
+    if (!vm) return true;
+    u128 acc = 0;
+    bool alive = true;
+    // second-level ranges may be split when the final stage adds up partial
+    // counts (n_enum > 2) or counts a single scanned level one by one
+    const bool splittable = P.n_enum > 2 || (!DOMAINS && !P.closed && P.tail == 1);
+    if (!splittable) {
+        alive = final_stage<DOMAINS, STATS>(g, P, B, T, 1, 0, INT_MAX, lane, acc, stat, A.bitsets,
+                                           A.words, deadline, status, tick);
+    } else {
+        uint64_t resetup = 0;
+        setup_level<STATS>(g, P, B, 1, lane, may_defer ? stat : resetup);
+        const int32_t T1 = B[1].total;
+        int32_t t_end_eff = min(t_end, T1);
+        if (may_defer && T1 > P.split) {
+            if (lane == 0) {
+                const uint32_t slot = atomicAdd(&A.ctl->n_deferred, 1u);
+                if (slot < A.defer_cap) {
+                    A.defer[slot].chunk = c;
+                    A.defer[slot].total = uint32_t(T1);
+                    t_end_eff = P.split;
+                }
+            }
+            t_end_eff = __shfl_sync(FULL, t_end_eff, 0);
+        }
+        if (P.n_enum == 2) {
+            alive = final_stage<DOMAINS, STATS>(g, P, B, T, 1, t_begin, t_end_eff, lane, acc, stat,
+                                               A.bitsets, A.words, deadline, status, tick);
+        } else {
+            if (lane == 0) {
+                B[1].t = t_begin;
+                B[1].total = t_end_eff;
+            }
+            __syncwarp();
+            int L = 1;
+            while (alive) {
+                if (L + 1 == P.n_enum) {
+                    alive = final_stage<DOMAINS, STATS>(g, P, B, T, L, 0, INT_MAX, lane, acc, stat,
+                                                       A.bitsets, A.words, deadline, status, tick);
+                    if (lane == 0) B[L].cnt = 0;
+                    __syncwarp();
+                    L--;
+                    continue;
+                }
+                LevelBuf &b = B[L];
+                LevelBuf &nb = B[L + 1];
+                const int32_t t = b.t, tot = b.total, ncnt = nb.cnt;
+                if (t < tot && ncnt < 32) {
+                    if (deadline_hit(deadline, status, lane, tick)) { alive = false; break; }
+                    const int32_t ei = t + lane;
+                    bool ok = false;
+                    int p = 0;
+                    int32_t x = 0;
+                    if (ei < tot) {
+                        p = prefix_of(b, ei);
+                        const int32_t off = ei - (p ? b.scan[p - 1] : 0);
+                        x = __ldg(g.col + b.base[p] + off);
+                        const Bound m = tuple_of(B, L, p);
+                        ok = admissible(g, P.lv[L + 1], b.src[p], m, x);
+                    }
+                    const uint32_t sm = __ballot_sync(FULL, ok);
+                    if (ok) {
+                        const int pos = ncnt + __popc(sm & ((1u << lane) - 1));
+                        nb.v[pos] = x;
+                        nb.parent[pos] = uint8_t(p);
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        nb.cnt = ncnt + __popc(sm);
+                        b.t = t + 32;
+                    }
+                    __syncwarp();
+                    continue;
+                }
+                if (ncnt > 0 && (ncnt >= 32 || t >= tot)) {
+                    L++;
+                    if (L + 1 < P.n_enum) setup_level<STATS>(g, P, B, L, lane, stat);
+                    continue;
+                }
+                if (lane == 0) b.cnt = 0;
+                __syncwarp();
+                L--;
+                if (L < 1) break;
+            }
+        }
+    }
+    if (!DOMAINS) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += shfl_xor_u128(acc, off);
+        if (lane == 0 && acc != 0) add_u128(A.counters + 2 * int64_t(P.counter), acc);
+    }
+    return alive;
+}
+
+// pass 0: chunks from the shared counter (deferring oversized ranges);
+// pass 1: split-sized pieces of the deferred chunks.
+template <bool DOMAINS, bool STATS>
+__global__ void __launch_bounds__(WARPS * 32)
+match_kernel(KernelArgs A, int pass) {
+    extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
-    unsigned long long *work = &ctl->work;
+    const int warp = threadIdx.x >> 5;
+    const size_t per_warp = sizeof(LevelBuf) * A.n_buf + sizeof(WarpTail);
+    LevelBuf *B = reinterpret_cast<LevelBuf *>(smem + per_warp * warp);
+    WarpTail &T = *reinterpret_cast<WarpTail *>(smem + per_warp * warp + sizeof(LevelBuf) * A.n_buf);
+    Control *ctl = A.ctl;
     int *status = &ctl->status;
     const uint64_t deadline = *(volatile unsigned long long *)&ctl->deadline;
-    WarpState &S = warp_state[threadIdx.x >> 5];
-    const unsigned long long n_echunks = (unsigned long long)((tasks.ntasks + CHUNK - 1) / CHUNK);
-    const unsigned long long total = n_echunks * (unsigned long long)nplans;
+    const unsigned long long stride = (unsigned long long)(A.sample_stride > 1 ? A.sample_stride : 1);
+    const unsigned long long n_sampled = ((unsigned long long)A.n_echunks + stride - 1) / stride;
+    const unsigned long long total = pass == 0
+        ? n_sampled * (unsigned long long)A.nplans
+        : (unsigned long long)(*(volatile uint32_t *)&ctl->n_pieces);
+    const uint32_t n_def = pass == 0 ? 0u
+        : min(*(volatile uint32_t *)&ctl->n_deferred, A.defer_cap);
+    uint32_t tick = 0;
+    uint64_t stat = 0;
     while (true) {
-        unsigned long long c = 0;
+        unsigned long long w = 0;
         int stop = 0;
         if (lane == 0) {
-            c = atomicAdd(work, 1ull);
+            w = atomicAdd(pass == 0 ? &ctl->work : &ctl->work2, 1ull);
             stop = *(volatile int *)status;
             if (!stop && deadline && global_ns() > deadline) {
                 atomicExch(status, 1);
                 stop = 1;
             }
         }
-        c = __shfl_sync(FULL, c, 0);
+        w = __shfl_sync(FULL, w, 0);
         stop = __shfl_sync(FULL, stop, 0);
-        if (c >= total || stop) break;
-        const DevPlan &P = plans[c % nplans];
-        const int64_t e = int64_t(c / nplans) * CHUNK + lane;
-        int32_t root = -1, v1 = -1;
-        if (e < tasks.ntasks) {
-            // root index: last i with off[i] <= e
-            int64_t lo = 0, hi = tasks.nroots;
+        if (w >= total || stop) break;
+        bool alive;
+        if (pass == 0) {
+            const unsigned long long c = (w / A.nplans) * stride * A.nplans + w % A.nplans;
+            alive = process_chunk<DOMAINS, STATS>(A, B, T, c, 0, INT_MAX, true, lane, deadline,
+                                                 tick, stat);
+        } else {
+            // piece w: deferred chunk i with piece_off[i] <= w < piece_off[i+1]
+            uint32_t lo = 0, hi = n_def;
             while (hi - lo > 1) {
-                const int64_t mid = (lo + hi) >> 1;
-                if (__ldg(tasks.off + mid) <= e) lo = mid;
+                const uint32_t mid = (lo + hi) >> 1;
+                if (__ldg(A.piece_off + mid) <= w) lo = mid;
                 else hi = mid;
             }
-            root = tasks.roots ? __ldg(tasks.roots + lo) : int32_t(g.n - 1 - lo);
-            v1 = __ldg(g.col + __ldg(g.rowptr + root) + (e - __ldg(tasks.off + lo)));
-            if (P.lv[0].label >= 0 && __ldg(g.labels + root) != uint8_t(P.lv[0].label)) root = -1;
-            if (P.lv[1].label >= 0 && __ldg(g.labels + v1) != uint8_t(P.lv[1].label)) root = -1;
+            const unsigned long long chunk = A.defer[lo].chunk;
+            const uint32_t tot = A.defer[lo].total;
+            const DevPlan &P = A.plans[chunk % A.nplans];
+            const int32_t j = int32_t(w - __ldg(A.piece_off + lo)) + 1;   // piece 0 ran in pass 0
+            const int32_t tb = j * P.split;
+            const int32_t te = min(int32_t(tot), tb + P.split);
+            alive = process_chunk<DOMAINS, STATS>(A, B, T, chunk, tb, te, false, lane, deadline,
+                                                 tick, stat);
         }
-        u128 acc = 0;
-        if (!DOMAINS && P.k == 2) {
-            acc = root >= 0 ? 1 : 0;
-        } else if (!DOMAINS && P.n_enum == 2 && P.closed) {
-            if (root >= 0) {
-                Bound m;
+        if (!alive) break;
+    }
+    if (STATS) {
 #pragma unroll
-                for (int i = 0; i < PLAN_KMAX; i++) m.v[i] = 0;
-                m.v[0] = root;
-                m.v[1] = v1;
-                acc = binom(closed_count(g, P.lv[2], m), P.tail);
-            }
-        } else {
-            uint32_t tm = __ballot_sync(FULL, root >= 0);
-            while (tm) {
-                const int j = __ffs(tm) - 1;
-                tm &= tm - 1;
-                Bound m;
-#pragma unroll
-                for (int i = 0; i < PLAN_KMAX; i++) m.v[i] = 0;
-                m.v[0] = __shfl_sync(FULL, root, j);
-                m.v[1] = __shfl_sync(FULL, v1, j);
-                if (DOMAINS && P.k == 2) {
-                    if (lane < 2) {
-                        const int32_t v = m.v[lane];
-                        set_bit(bitsets + int64_t(P.dom_base + P.lv[lane].column) * words, v);
-                    }
-                    continue;
-                }
-                acc += run_dfs<DOMAINS>(g, P, S, m, lane, bitsets, words, deadline, status);
-            }
+        for (int off = 16; off > 0; off >>= 1) stat += __shfl_xor_sync(FULL, stat, off);
+        if (lane == 0) atomicAdd(A.stats, (unsigned long long)stat);
+    }
+}
+
+// Pieces per deferred chunk (all but the first) -> exclusive scan (one block).
+__global__ void piece_scan_kernel(const Deferred *defer, uint32_t cap, const DevPlan *plans,
+                                  int nplans, uint32_t *piece_off, Control *ctl) {
+    __shared__ uint32_t partial[1024];
+    const uint32_t n = min(*(volatile uint32_t *)&ctl->n_deferred, cap);
+    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+    const uint32_t b = threadIdx.x * per, e = min(n, b + per);
+    uint32_t sum = 0;
+    for (uint32_t i = b; i < e; i++) {
+        const uint32_t split = uint32_t(plans[defer[i].chunk % nplans].split);
+        sum += (defer[i].total + split - 1) / split - 1;
+    }
+    partial[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (unsigned t = 0; t < blockDim.x; t++) {
+            const uint32_t v = partial[t];
+            partial[t] = run;
+            run += v;
         }
-        if (!DOMAINS) {
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) acc += shfl_xor_u128(acc, off);
-            if (lane == 0 && acc != 0) add_u128(counters + 2 * int64_t(P.counter), acc);
-        }
+        ctl->n_pieces = run;
+    }
+    __syncthreads();
+    uint32_t run = partial[threadIdx.x];
+    for (uint32_t i = b; i < e; i++) {
+        piece_off[i] = run;
+        const uint32_t split = uint32_t(plans[defer[i].chunk % nplans].split);
+        run += (defer[i].total + split - 1) / split - 1;
     }
 }
 
@@ -442,9 +692,93 @@ int device_sm_count(int device) {
     return sms;
 }
 
+// Wedge-pair counting for the edge-induced 4-cycle (see PlanKind): one block
+// per root a, highest-ranked first; warps take lower neighbours b of a, lanes
+// the neighbours c < a of b; atomicAdd on the block's dense per-c counters
+// returns the old value, whose running sum is sum_c C(w_c, 2); a second walk
+// over the same 2-paths resets the touched counters to zero.
+constexpr int WEDGE_THREADS = 512;
+
+__global__ void __launch_bounds__(WEDGE_THREADS)
+wedge_pairs_kernel(DevGraph g, DevTasks tasks, int counter, uint64_t *counters, uint32_t *scratch,
+                   int sample_stride, Control *ctl) {
+    __shared__ unsigned long long s_root;
+    __shared__ int s_stop;
+    __shared__ unsigned long long s_acc[WEDGE_THREADS / 32];
+    uint32_t *cnt = scratch + size_t(blockIdx.x) * size_t(g.n);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint64_t deadline = *(volatile unsigned long long *)&ctl->deadline;
+    const int64_t stride = sample_stride > 1 ? sample_stride : 1;
+    const int64_t nr = (tasks.nroots + stride - 1) / stride;
+    unsigned long long acc = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_root = atomicAdd(&ctl->work3, 1ull);
+            int stop = *(volatile int *)&ctl->status;
+            if (!stop && deadline && global_ns() > deadline) {
+                atomicExch(&ctl->status, 1);
+                stop = 1;
+            }
+            s_stop = stop;
+        }
+        __syncthreads();
+        const int64_t r = int64_t(s_root) * stride;
+        const bool done = s_root >= (unsigned long long)nr || s_stop;
+        __syncthreads();
+        if (done) break;
+        const int32_t a = tasks.roots ? __ldg(tasks.roots + r) : int32_t(g.n - 1 - r);
+        const int32_t lo = int32_t(__ldg(tasks.off[0] + r + 1) - __ldg(tasks.off[0] + r));
+        const int64_t abase = __ldg(g.rowptr + a);
+        for (int pass = 0; pass < 2; pass++) {
+            for (int i = warp; i < lo; i += nwarps) {
+                const int32_t b = __ldg(g.col + abase + i);
+                const int64_t bb = __ldg(g.rowptr + b);
+                const int32_t bd = int32_t(__ldg(g.rowptr + b + 1) - bb);
+                const int32_t bl = lower_bound_dev(g.col + bb, bd, a);   // neighbours of b below a
+                for (int32_t j = lane; j < bl; j += 32) {
+                    const int32_t c = __ldg(g.col + bb + j);
+                    if (pass == 0) acc += atomicAdd(cnt + c, 1u);
+                    else cnt[c] = 0;
+                }
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
+    if (lane == 0) s_acc[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u128 total = 0;
+        for (int w = 0; w < nwarps; w++) total += s_acc[w];
+        if (total) add_u128(counters + 2 * int64_t(counter), total);
+    }
+}
+
+int wedge_blocks(int device) { return device_sm_count(device); }
+
+int launch_wedge_pairs(const DevGraph &g, const DevTasks &tasks, int counter, uint64_t *counters,
+                       uint32_t *scratch, int blocks, int sample_stride, Control *ctl,
+                       void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemsetAsync(&ctl->work3, 0, sizeof(unsigned long long), s);
+    wedge_pairs_kernel<<<blocks, WEDGE_THREADS, 0, s>>>(g, tasks, counter, counters, scratch,
+                                                       sample_stride, ctl);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) {
+        set_error(std::string("wedge kernel launch: ") + cudaGetErrorString(err));
+        return -1;
+    }
+    return 0;
+}
+
 __global__ void arm_kernel(Control *ctl, uint64_t budget_ns) {
     ctl->work = 0;
+    ctl->work3 = 0;
+    ctl->work2 = 0;
     ctl->status = 0;
+    ctl->n_deferred = 0;
+    ctl->n_pieces = 0;
     ctl->deadline = budget_ns ? global_ns() + budget_ns : 0;
 }
 
@@ -458,23 +792,45 @@ int launch_arm(Control *d_ctl, uint64_t budget_ns, void *stream) {
     return 0;
 }
 
-template <bool DOMAINS>
-static int launch_match(const DevGraph &g, const DevPlan *d_plans, int nplans, const DevTasks &tasks,
-                        uint64_t *d_counters, uint32_t *d_bitsets, int64_t words, Control *d_ctl,
-                        void *stream) {
+template <bool DOMAINS, bool STATS>
+static int launch_match(const MatchLaunch &L, void *stream) {
     int device = 0;
     cudaGetDevice(&device);
     const int sms = device_sm_count(device);
+    const int n_buf = L.max_enum < 2 ? 2 : L.max_enum;
+    const size_t smem = (sizeof(LevelBuf) * n_buf + sizeof(WarpTail)) * WARPS;
+    auto kern = match_kernel<DOMAINS, STATS>;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, match_kernel<DOMAINS>,
-                                                  WARPS_PER_BLOCK * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
     if (per_sm < 1) per_sm = 1;
-    const int64_t chunks = ((tasks.ntasks + CHUNK - 1) / CHUNK) * int64_t(nplans);
-    int64_t blocks = int64_t(sms) * per_sm;
-    const int64_t need = (chunks + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
-    if (need < blocks) blocks = need > 0 ? need : 1;
-    match_kernel<DOMAINS><<<unsigned(blocks), WARPS_PER_BLOCK * 32, 0, (cudaStream_t)stream>>>(
-        g, d_plans, nplans, tasks, d_counters, d_bitsets, words, d_ctl);
+    const int64_t stride = L.sample_stride > 1 ? L.sample_stride : 1;
+    const int64_t chunks = ((L.n_echunks + stride - 1) / stride) * int64_t(L.nplans);
+    const int64_t blocks = int64_t(sms) * per_sm;
+    const int64_t need = (chunks + WARPS - 1) / WARPS;
+    const int64_t blocks0 = need < blocks ? (need > 0 ? need : 1) : blocks;
+    KernelArgs A;
+    A.g = L.g;
+    A.plans = L.plans;
+    A.nplans = L.nplans;
+    A.n_buf = n_buf;
+    A.tasks = L.tasks;
+    A.n_echunks = L.n_echunks;
+    A.sample_stride = L.sample_stride;
+    A.counters = L.counters;
+    A.bitsets = L.bitsets;
+    A.words = L.words;
+    A.ctl = L.ctl;
+    A.defer = L.defer;
+    A.defer_cap = L.defer_cap;
+    A.piece_off = L.piece_off;
+    A.stats = L.stats;
+    cudaStream_t s = (cudaStream_t)stream;
+    kern<<<unsigned(blocks0), WARPS * 32, smem, s>>>(A, 0);
+    piece_scan_kernel<<<1, 1024, 0, s>>>(L.defer, L.defer_cap, L.plans, L.nplans, L.piece_off,
+                                         L.ctl);
+    kern<<<unsigned(blocks), WARPS * 32, smem, s>>>(A, 1);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) {
         set_error(std::string("match kernel launch: ") + cudaGetErrorString(err));
@@ -483,14 +839,13 @@ static int launch_match(const DevGraph &g, const DevPlan *d_plans, int nplans, c
     return 0;
 }
 
-int launch_count(const DevGraph &g, const DevPlan *d_plans, int nplans, const DevTasks &tasks,
-                 uint64_t *d_counters, Control *d_ctl, void *stream) {
-    return launch_match<false>(g, d_plans, nplans, tasks, d_counters, nullptr, 0, d_ctl, stream);
+int launch_count(const MatchLaunch &L, void *stream) {
+    if (L.stats) return launch_match<false, true>(L, stream);
+    return launch_match<false, false>(L, stream);
 }
 
-int launch_domains(const DevGraph &g, const DevPlan *d_plans, int nplans, const DevTasks &tasks,
-                   uint32_t *d_bitsets, int64_t words, Control *d_ctl, void *stream) {
-    return launch_match<true>(g, d_plans, nplans, tasks, nullptr, d_bitsets, words, d_ctl, stream);
+int launch_domains(const MatchLaunch &L, void *stream) {
+    return launch_match<true, false>(L, stream);
 }
 
 int launch_mni_reduce(const uint32_t *d_bitsets, int64_t words, const int32_t *d_src_off,

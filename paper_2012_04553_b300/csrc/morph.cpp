@@ -180,87 +180,126 @@ bool same_common(const DevLevel &a, const DevLevel &b, uint8_t tail_bits) {
 
 }  // namespace
 
-std::vector<DevPlan> compile_plans(const Pat &p, int counter, int dom_base,
-                                   const std::vector<int> &column_of_vertex) {
-    std::vector<Perm> aut = automorphisms(p);
-    std::vector<int> orb = orbit_of(p, aut);
+// One plan: `order[0]` is the root; `H` is the group whose symmetry the
+// ordering constraints break (the root's stabiliser for rooted plans, the
+// whole automorphism group for free plans); rooted plans bound every vertex
+// below the root.
+static DevPlan build_plan(const Pat &p, const std::vector<int> &order, std::vector<Perm> H,
+                          bool rooted, int counter, int dom_base,
+                          const std::vector<int> &column_of_vertex) {
     int n_columns = 0;
     for (int c : column_of_vertex) n_columns = std::max(n_columns, c + 1);
+    std::vector<int> level_of(p.k);
+    for (int i = 0; i < p.k; i++) level_of[order[i]] = i;
+    DevPlan plan{};
+    plan.k = p.k;
+    plan.counter = counter;
+    plan.dom_base = dom_base;
+    plan.n_columns = n_columns;
+    for (int i = 0; i < p.k; i++) {
+        int u = order[i];
+        DevLevel &lv = plan.lv[i];
+        lv.label = p.lab[u];
+        lv.column = uint8_t(column_of_vertex.empty() ? 0 : column_of_vertex[u]);
+        if (i == 0) continue;
+        if (rooted) lv.lt = 1;   // every non-root vertex ranks below the root
+        for (int j = 0; j < i; j++) {
+            int w = order[j];
+            if (p.adjacent(u, w)) lv.isect |= uint8_t(1u << j);
+            else if (p.vi) lv.diff |= uint8_t(1u << j);
+        }
+    }
+    // Symmetry breaking (Grochow & Kellis): in matching order, v's image is
+    // the smallest over v's orbit under H, then H shrinks to v's stabiliser.
+    for (int i = rooted ? 1 : 0; i < p.k; i++) {
+        int v = order[i];
+        uint32_t orbit = 0;
+        for (const Perm &s : H) orbit |= 1u << s[v];
+        for (int w = 0; w < p.k; w++) {
+            if (w == v || !((orbit >> w) & 1)) continue;
+            // image of v below image of w; w comes later in the order
+            plan.lv[level_of[w]].gt |= uint8_t(1u << i);
+        }
+        std::vector<Perm> H2;
+        for (const Perm &s : H)
+            if (s[v] == v) H2.push_back(s);
+        H.swap(H2);
+    }
+    // Injectivity not implied by adjacency or ordering.
+    for (int i = 1; i < p.k; i++) {
+        DevLevel &lv = plan.lv[i];
+        uint8_t implied = lv.isect | lv.lt | lv.gt;
+        for (int j = 0; j < i; j++)
+            if (!((implied >> j) & 1)) lv.neq |= uint8_t(1u << j);
+    }
+    // Longest totally ordered tail with one shared candidate set.
+    int tail = 0;
+    if (p.k >= 3) {
+        tail = 1;
+        for (int r = p.k - 2; r >= 2; r--) {
+            int t0 = p.k - r;
+            uint8_t tail_bits = uint8_t(((1u << p.k) - 1) & ~((1u << t0) - 1));
+            bool ok = true;
+            for (int t = t0; t < p.k && ok; t++) {
+                const DevLevel &lv = plan.lv[t];
+                if (!same_common(lv, plan.lv[t0], tail_bits)) ok = false;
+                if ((lv.isect | lv.diff | lv.lt | lv.neq) & tail_bits) ok = false;
+                uint8_t before = uint8_t(((1u << t) - 1) & tail_bits);
+                if ((lv.gt & tail_bits) != before) ok = false;
+            }
+            if (ok) { tail = r; break; }
+        }
+    }
+    plan.tail = tail;
+    plan.n_enum = p.k - tail;
+    const DevLevel &f = plan.lv[plan.n_enum < p.k ? plan.n_enum : p.k - 1];
+    plan.closed = tail > 0 && __builtin_popcount(f.isect) == 1 && f.diff == 0 && f.label < 0;
+    // second-level candidates per chunk before the rest is deferred: deeper
+    // plans do more work per candidate, so they split finer
+    plan.split = plan.n_enum <= 2 ? 4096 : std::max(32, 1024 >> (2 * (plan.n_enum - 3)));
+    // task space: rooted plans take (root, lower neighbour); free plans take
+    // (root, higher neighbour) when symmetry orders them, else both directions
+    if (rooted) plan.task_space = TASKS_LOWER;
+    else plan.task_space = (plan.lv[1].gt & 1) ? TASKS_UPPER : TASKS_BOTH;
+    return plan;
+}
+
+// Unlabeled edge-induced 4-cycle: every vertex of degree 2, four edges.
+static bool is_plain_c4(const Pat &p) {
+    if (p.k != 4 || p.vi || p.labeled() || p.n_edges() != 4) return false;
+    for (int u = 0; u < 4; u++)
+        if (__builtin_popcount(p.adj[u]) != 2) return false;
+    return true;
+}
+
+std::vector<DevPlan> compile_plans(const Pat &p, int counter, int dom_base,
+                                   const std::vector<int> &column_of_vertex, bool counting) {
+    std::vector<Perm> aut = automorphisms(p);
+    std::vector<int> orb = orbit_of(p, aut);
     std::vector<DevPlan> plans;
     for (int root = 0; root < p.k; root++) {
         if (orb[root] != root) continue;   // one plan per orbit, at its smallest vertex
-        std::vector<int> order = matching_order(p, root);
-        std::vector<int> level_of(p.k);
-        for (int i = 0; i < p.k; i++) level_of[order[i]] = i;
-
-        DevPlan plan{};
-        plan.k = p.k;
-        plan.counter = counter;
-        plan.dom_base = dom_base;
-        plan.n_columns = n_columns;
-        for (int i = 0; i < p.k; i++) {
-            int u = order[i];
-            DevLevel &lv = plan.lv[i];
-            lv.label = p.lab[u];
-            lv.column = uint8_t(column_of_vertex.empty() ? 0 : column_of_vertex[u]);
-            if (i == 0) continue;
-            lv.lt = 1;   // every non-root vertex ranks below the root
-            for (int j = 0; j < i; j++) {
-                int w = order[j];
-                if (p.adjacent(u, w)) lv.isect |= uint8_t(1u << j);
-                else if (p.vi) lv.diff |= uint8_t(1u << j);
-            }
-        }
-        // Symmetry breaking over the stabiliser of the root.
         std::vector<Perm> H;
         for (const Perm &s : aut)
             if (s[root] == root) H.push_back(s);
-        for (int i = 1; i < p.k; i++) {
-            int v = order[i];
-            uint32_t orbit = 0;
-            for (const Perm &s : H) orbit |= 1u << s[v];
-            for (int w = 0; w < p.k; w++) {
-                if (w == v || !((orbit >> w) & 1)) continue;
-                // image of v below image of w; w comes later in the order
-                plan.lv[level_of[w]].gt |= uint8_t(1u << i);
-            }
-            std::vector<Perm> H2;
-            for (const Perm &s : H)
-                if (s[v] == v) H2.push_back(s);
-            H.swap(H2);
-        }
-        // Injectivity not implied by adjacency or ordering.
-        for (int i = 1; i < p.k; i++) {
-            DevLevel &lv = plan.lv[i];
-            uint8_t implied = lv.isect | lv.lt | lv.gt;
-            for (int j = 0; j < i; j++)
-                if (!((implied >> j) & 1)) lv.neq |= uint8_t(1u << j);
-        }
-        // Longest totally ordered tail with one shared candidate set.
-        int tail = 0;
-        if (p.k >= 3) {
-            tail = 1;
-            for (int r = p.k - 2; r >= 2; r--) {
-                int t0 = p.k - r;
-                uint8_t tail_bits = uint8_t(((1u << p.k) - 1) & ~((1u << t0) - 1));
-                bool ok = true;
-                for (int t = t0; t < p.k && ok; t++) {
-                    const DevLevel &lv = plan.lv[t];
-                    if (!same_common(lv, plan.lv[t0], tail_bits)) ok = false;
-                    if ((lv.isect | lv.diff | lv.lt | lv.neq) & tail_bits) ok = false;
-                    uint8_t before = uint8_t(((1u << t) - 1) & tail_bits);
-                    if ((lv.gt & tail_bits) != before) ok = false;
-                }
-                if (ok) { tail = r; break; }
-            }
-        }
-        plan.tail = tail;
-        plan.n_enum = p.k - tail;
-        const DevLevel &f = plan.lv[plan.n_enum < p.k ? plan.n_enum : p.k - 1];
-        plan.closed = tail > 0 && __builtin_popcount(f.isect) == 1 && f.diff == 0 && f.label < 0;
-        plans.push_back(plan);
+        plans.push_back(build_plan(p, matching_order(p, root), H, true, counter, dom_base,
+                                   column_of_vertex));
     }
+    // the 4-cycle's single rooted plan is counted by the wedge kernel (its
+    // levels still describe the same occurrences: root, two lower neighbours
+    // and the opposite vertex)
+    if (counting && is_plain_c4(p) && plans.size() == 1) plans[0].kind = PLAN_WEDGE_PAIRS;
     return plans;
+}
+
+DevPlan compile_free_plan(const Pat &p, int counter, int dom_base,
+                          const std::vector<int> &column_of_vertex) {
+    // root at a vertex of highest pattern degree (most intersections early)
+    int root = 0;
+    for (int u = 1; u < p.k; u++)
+        if (__builtin_popcount(p.adj[u]) > __builtin_popcount(p.adj[root])) root = u;
+    return build_plan(p, matching_order(p, root), automorphisms(p), false, counter, dom_base,
+                      column_of_vertex);
 }
 
 }  // namespace pm

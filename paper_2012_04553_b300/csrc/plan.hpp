@@ -1,14 +1,19 @@
 // Matching plans and device-side data layouts shared by host and kernels.
 //
-// A plan matches one pattern p with one automorphism orbit O of p pinned to
-// the task's root: the root is the highest-ranked (largest internal id)
+// A rooted plan matches one pattern p with one automorphism orbit O of p
+// pinned to the task's root: the root is the highest-ranked (largest internal id)
 // vertex of the occurrence and is the image of O's representative.  Every
 // occurrence of p has exactly one highest-ranked vertex, whose preimage lies
 // in exactly one orbit, so the plans of p partition p's occurrences; within a
 // plan the remaining symmetry (the stabiliser of the representative) is
 // broken by ordering constraints chosen as in Grochow & Kellis (RECOMB 2007):
 // at each vertex v, in matching order, v's image is the smallest over v's
-// orbit under the current stabiliser, which then shrinks to fix v.
+// orbit under the current stabiliser, which then shrinks to fix v.  Rooted
+// plans make per-root counts exact (pm_count_roots).  A free plan counts all
+// of p's occurrences with a single plan: it breaks the whole automorphism
+// group the same way and bounds nothing by the root, so it can start at the
+// cheapest vertex (e.g. a diamond's chord, whose two other vertices then form
+// one binomial tail per chord edge).
 //
 // Level i of a plan binds pattern vertex order[i].  Its candidates are the
 // data vertices x with
@@ -42,6 +47,21 @@ struct DevLevel {
     uint8_t pad;
 };
 
+// Which oriented edges (root, v) a plan's tasks range over.
+enum TaskSpace : int32_t {
+    TASKS_LOWER = 0,   // v < root: rooted plans (root = highest-ranked vertex)
+    TASKS_UPPER = 1,   // v > root: free plans whose symmetry orders root and v
+    TASKS_BOTH = 2     // every directed edge: free plans without that order
+};
+
+// How a plan is executed.  Set-operation plans run in the matching kernel.
+// The rooted plan of the edge-induced 4-cycle runs in a wedge kernel: for the
+// root a and each opposite vertex c < a, the occurrences with a as highest-
+// ranked vertex are C(w, 2) with w = |N(a) n N(c) n [0, a)|; counting the
+// 2-paths a-b-c into per-c counters and adding each counter's old value
+// gives that sum, since C(w, 2) = 0 + 1 + ... + (w - 1).
+enum PlanKind : int32_t { PLAN_SETOPS = 0, PLAN_WEDGE_PAIRS = 1 };
+
 struct DevPlan {
     int32_t k;
     int32_t n_enum;
@@ -50,7 +70,10 @@ struct DevPlan {
     int32_t counter;      // output slot: index of the matched pattern
     int32_t dom_base;     // first MNI bitset of the matched pattern (support plans)
     int32_t n_columns;    // MNI columns of the matched pattern
-    int32_t pad;
+    int32_t split;        // second-level candidates a task chunk keeps before deferring the rest
+    int32_t task_space;   // TaskSpace
+    int32_t kind;         // PlanKind
+    int32_t pad[2];
     DevLevel lv[PLAN_KMAX];
 };
 
@@ -64,15 +87,16 @@ struct DevGraph {
     const uint8_t *labels;     // n, or nullptr
 };
 
-// Task space: oriented edges (root, v) with v < root, grouped by root.
+// Task spaces: oriented edges (root, v) grouped by root, for each TaskSpace.
 // roots == nullptr means the implicit root list n-1, n-2, ..., 0 (highest
-// ranked first).  off[i] = number of oriented edges of roots 0..i-1 of the
-// list (nroots + 1 entries).
+// ranked first); an explicit list serves TASKS_LOWER only.  off[s][i] =
+// number of tasks of roots 0..i-1 of the list in space s (nroots + 1
+// entries); ntasks[s] = off[s][nroots].
 struct DevTasks {
     const int32_t *roots;
-    const int64_t *off;
+    const int64_t *off[3];
     int64_t nroots;
-    int64_t ntasks;
+    int64_t ntasks[3];
 };
 
 // Per-launch control block in device memory: the shared chunk counter, a
@@ -80,10 +104,22 @@ struct DevTasks {
 // timer (0 = none), written on the device by the arming kernel so host and
 // device clocks never need to agree.
 struct Control {
-    unsigned long long work;
+    unsigned long long work;      // first-pass chunk counter
     int status;
     int pad;
     unsigned long long deadline;
+    unsigned long long work2;     // second-pass piece counter
+    unsigned int n_deferred;      // chunks appended to the deferred list
+    unsigned int n_pieces;        // pieces of the deferred chunks (after the scan)
+    unsigned long long work3;     // root counter of the wedge kernel
+};
+
+// A chunk whose second-level candidate range [split, total) awaits the
+// second pass.
+struct Deferred {
+    unsigned long long chunk;
+    uint32_t total;
+    uint32_t pad;
 };
 
 }  // namespace pm

@@ -37,6 +37,7 @@ def run_plans(plans, n_matched, adj, labels, roots=None):
         def candidates(L, m):
             d = lv[L]
             lo = max([m[j] for j in _bits(d["gt"])], default=-1)
+            # (levels 1+ of every plan intersect at least one earlier list)
             hi = min([m[j] for j in _bits(d["lt"])], default=n)
             c = set.intersection(*[adj[m[j]] for j in _bits(d["isect"])])
             for j in _bits(d["diff"]):
@@ -55,11 +56,12 @@ def run_plans(plans, n_matched, adj, labels, roots=None):
                 total += dfs(L + 1, m + [x])
             return total
 
+        space = int(P["task_space"])   # 0: v1 < root, 1: v1 > root, 2: any neighbour
         for root in (range(n) if roots is None else roots):
             if lv[0]["label"] >= 0 and labels[root] != lv[0]["label"]:
                 continue
             for v1 in sorted(adj[root]):
-                if v1 >= root:
+                if (space == 0 and v1 >= root) or (space == 1 and v1 <= root):
                     continue
                 if lv[1]["label"] >= 0 and labels[v1] != lv[1]["label"]:
                     continue

@@ -52,8 +52,13 @@ def test_motifs_small_rmat_against_oracle(scale, ef, seed, kmax):
         want_v = oracle.motif_counts_direct(og, k)
         want_e = [oracle.count(og, algebra.Pattern.from_mask(k, m)) for m in algebra.connected_classes(k)]
         for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
-            assert pm.Plan(g, motif_queries(k), mode=mode).count() == want_v, (k, mode)
-            assert pm.Plan(g, motif_queries(k, False), mode=mode).count() == want_e, (k, mode)
+            for family in (pm.PLANS_AUTO, pm.PLANS_ROOTED, pm.PLANS_FREE):
+                pv = pm.Plan(g, motif_queries(k), mode=mode)
+                pv.select(family)
+                assert pv.count() == want_v, (k, mode, family)
+                pe = pm.Plan(g, motif_queries(k, False), mode=mode)
+                pe.select(family)
+                assert pe.count() == want_e, (k, mode, family)
 
 
 def test_six_vertex_patterns_against_oracle():
@@ -64,8 +69,11 @@ def test_six_vertex_patterns_against_oracle():
     for vi in (False, True):
         qs = [pm.make_pattern(6, m, int(vi)) for m in masks]
         want = [oracle.count(og, algebra.Pattern.from_mask(6, m, None, vi)) for m in masks]
-        assert pm.Plan(g, qs, mode=pm.MORPH_NONE).count() == want
-        assert pm.Plan(g, qs, mode=pm.MORPH_NAIVE).count() == want
+        for family in (pm.PLANS_ROOTED, pm.PLANS_FREE):
+            for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+                plan = pm.Plan(g, qs, mode=mode)
+                plan.select(family)
+                assert plan.count() == want, (vi, family, mode)
 
 
 def test_labeled_counts_against_oracle():
@@ -78,7 +86,10 @@ def test_labeled_counts_against_oracle():
     cq = [pm.make_pattern(p.k, p.mask, pm.EDGE_INDUCED, p.labels) for p in qs]
     want = [oracle.count(og, p) for p in qs]
     for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
-        assert pm.Plan(g, cq, mode=mode).count() == want
+        for family in (pm.PLANS_ROOTED, pm.PLANS_FREE):
+            plan = pm.Plan(g, cq, mode=mode)
+            plan.select(family)
+            assert plan.count() == want
     vq = [pm.make_pattern(p.k, p.mask, pm.VERTEX_INDUCED, p.labels) for p in qs]
     want_v = [oracle.count(og, p.with_induced(True)) for p in qs]
     for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
@@ -181,9 +192,23 @@ def test_mni_support_against_oracle():
     cq = [pm.make_pattern(p.k, p.mask, pm.EDGE_INDUCED, p.labels) for p in qs]
     want = [oracle.support_direct(og, p) for p in qs]
     for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
-        sup, freq = pm.Plan(g, cq, op=pm.OP_SUPPORT, mode=mode).support(threshold=20)
-        assert sup == want, mode
-        assert freq == [w >= 20 for w in want]
+        for family in (pm.PLANS_ROOTED, pm.PLANS_FREE):
+            plan = pm.Plan(g, cq, op=pm.OP_SUPPORT, mode=mode)
+            plan.select(family)
+            sup, freq = plan.support(threshold=20)
+            assert sup == want, (mode, family)
+            assert freq == [w >= 20 for w in want]
+
+
+def test_autotune_choices_are_cached_per_graph():
+    s, d = rmat_edges(11, 8, seed=111)
+    g = load(2048, s, d)
+    a = pm.Plan(g, motif_queries(4), mode=pm.MORPH_NAIVE)
+    fam = a.autotune()
+    assert len(fam) == a.n_matched and set(fam) <= {pm.PLANS_ROOTED, pm.PLANS_FREE}
+    b = pm.Plan(g, motif_queries(4), mode=pm.MORPH_NAIVE)
+    assert b.autotune() == fam
+    assert a.count() == b.count()
 
 
 def test_deadline_returns_timeout_and_context_survives():

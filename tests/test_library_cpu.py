@@ -64,14 +64,24 @@ def small_graph():
 
 @pytest.mark.parametrize("k", [3, 4, 5])
 @pytest.mark.parametrize("vi", [False, True])
-def test_plans_count_matched_patterns(small_graph, k, vi):
+@pytest.mark.parametrize("family", [pm.PLANS_ROOTED, pm.PLANS_FREE])
+def test_plans_count_matched_patterns(small_graph, k, vi, family):
     g = small_graph
     adj, labels = degree_ordered(g)
     for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
         plan = pm.Plan(None, pats(k, vi), mode=mode)
-        got = run_plans(plan.export_plans(), plan.n_matched, adj, labels)
+        got = run_plans(plan.export_plans(family), plan.n_matched, adj, labels)
         for (kk, mask, ind, lab), c in zip(plan.matched_patterns(), got):
             assert c == oracle.count(g, oracle_pattern(kk, mask, ind)), (kk, mask, ind, mode)
+
+
+def test_free_plans_shapes():
+    # diamond: chord rooted, the two degree-2 vertices a binomial tail of 2;
+    # paw: rooted at the degree-3 vertex with a closed single-vertex tail
+    diamond = pm.Plan(None, [pm.make_pattern(4, 31)], mode=pm.MORPH_NONE).export_plans(pm.PLANS_FREE)[0]
+    assert (diamond["tail"], diamond["task_space"]) == (2, 1)
+    paw = pm.Plan(None, [pm.make_pattern(4, 15)], mode=pm.MORPH_NONE).export_plans(pm.PLANS_FREE)[0]
+    assert (paw["tail"], paw["closed"], paw["task_space"]) == (1, 1, 2)
 
 
 def test_morph_transform_recovers_requested(small_graph):
@@ -105,10 +115,11 @@ def test_labeled_plans(small_graph):
     adj, lab = degree_ordered(g)
     queries = oracle.labeled_edge_patterns(3, [0, 1])
     for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
-        cq = [pm.make_pattern(p.k, p.mask, pm.EDGE_INDUCED, p.labels) for p in queries]
-        plan = pm.Plan(None, cq, mode=mode)
-        matched = run_plans(plan.export_plans(), plan.n_matched, adj, lab)
-        assert plan.morph(matched) == [oracle.count(g, p) for p in queries]
+        for family in (pm.PLANS_ROOTED, pm.PLANS_FREE):
+            cq = [pm.make_pattern(p.k, p.mask, pm.EDGE_INDUCED, p.labels) for p in queries]
+            plan = pm.Plan(None, cq, mode=mode)
+            matched = run_plans(plan.export_plans(family), plan.n_matched, adj, lab)
+            assert plan.morph(matched) == [oracle.count(g, p) for p in queries]
 
 
 def test_six_vertex_plans_on_tiny_graph():
@@ -117,9 +128,10 @@ def test_six_vertex_plans_on_tiny_graph():
     adj, labels = degree_ordered(g)
     masks = algebra.connected_classes(6)[::9]
     for vi in (False, True):
-        plan = pm.Plan(None, [pm.make_pattern(6, m, int(vi)) for m in masks], mode=pm.MORPH_NONE)
-        got = plan.morph(run_plans(plan.export_plans(), plan.n_matched, adj, labels))
-        assert got == [oracle.count(g, algebra.Pattern.from_mask(6, m, None, vi)) for m in masks]
+        for family in (pm.PLANS_ROOTED, pm.PLANS_FREE):
+            plan = pm.Plan(None, [pm.make_pattern(6, m, int(vi)) for m in masks], mode=pm.MORPH_NONE)
+            got = plan.morph(run_plans(plan.export_plans(family), plan.n_matched, adj, labels))
+            assert got == [oracle.count(g, algebra.Pattern.from_mask(6, m, None, vi)) for m in masks]
 
 
 def test_morph_coefficients_match_oracle_algebra():
