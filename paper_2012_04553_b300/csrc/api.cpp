@@ -420,7 +420,7 @@ std::vector<DevPlan> family_plans(const pm_query_plan *p, size_t j, int f) {
 
 // Autotuner: for every matched pattern without a decision, time its rooted
 // plans and its free plan (counting kernels) on the same sample of task
-// chunks (every stride-th chunk, about 4096 chunks, 2 s deadline each) and
+// chunks (every stride-th chunk, about 4096 chunks, 0.5 s deadline each) and
 // keep the faster family.  Decisions are cached on the graph under the
 // pattern's canonical key, so later plans on the same graph reuse them.
 pm_status autotune(pm_query_plan *p, cudaStream_t s) {
@@ -449,7 +449,7 @@ pm_status autotune(pm_query_plan *p, cudaStream_t s) {
             const int64_t ech = echunks_for(t.plans, tasks);
             const int stride = int(std::max<int64_t>(1, ech / 4096));
             cudaError_t e = cudaMemsetAsync(p->d_counters, 0, p->bytes_counters, s);
-            if (!e && launch_arm(p->d_ctl, uint64_t(2e9), s)) e = cudaErrorLaunchFailure;
+            if (!e && launch_arm(p->d_ctl, uint64_t(5e8), s)) e = cudaErrorLaunchFailure;
             if (!e) e = cudaEventRecord(p->ev0, s);
             if (!e && launch_table(p, t, tasks, stride, false, nullptr, s) != PM_OK)
                 e = cudaErrorLaunchFailure;
