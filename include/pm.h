@@ -209,6 +209,24 @@ pm_status pm_plan_last_kernel_ms(const pm_query_plan *p, float *ms);
 pm_status pm_support(pm_query_plan *p, void *stream, double timeout_s, uint64_t threshold,
                      uint64_t *support, uint8_t *frequent);
 
+/* Edge-induced 4-cycle count of a graph given as a device CSR, for callers
+ * that cannot allocate device memory during the call (a fully reserved
+ * memory pool, a real-time loop that must not enter an allocator, an
+ * embedder that owns every device byte).  The paper has no counterpart: this
+ * is a library convenience.  rowptr: n+1 int64 row offsets, col: int32
+ * neighbour ids, both device memory owned by the caller, describing an
+ * undirected simple graph (each edge in both rows, no self-loops) with
+ * every row sorted ascending; count: 2 device uint64 words (low, high)
+ * receiving the exact 128-bit count.  Asynchronous on `stream`.  The call
+ * allocates nothing: its scratch is a 16 MiB array built into the library
+ * (held on every GPU that loads it until exit), so n may be at most
+ * 4194304 (PM_EINVAL beyond).  The first call on a device looks up that
+ * array's device address, so make it before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller. */
+pm_status pm_count_c4_noalloc(const int64_t *rowptr, const int32_t *col, int64_t n,
+                              uint64_t *count, void *stream);
+
 const char *pm_strerror(pm_status s);
 /* Text of the last error raised on the calling thread ("" if none). */
 const char *pm_last_error(void);

@@ -78,6 +78,7 @@ def _load():
         "pm_plan_export": [vp, i32, vp, i64],
         "pm_plan_select": [vp, i32],
         "pm_plan_autotune": [vp, vp, vp],
+        "pm_count_c4_noalloc": [vp, vp, i64, vp, vp],
         "pm_count_instrumented": [vp, vp, vp, vp],
         "pm_plan_last_kernel_ms": [vp, ctypes.POINTER(ctypes.c_float)],
     }
@@ -104,7 +105,7 @@ ABI_SYMBOLS = [
     "pm_free_graph", "pm_plan", "pm_plan_get_info", "pm_plan_matched", "pm_free_plan",
     "pm_morph", "pm_count", "pm_count_roots", "pm_support", "pm_strerror", "pm_last_error",
     "pm_plan_export", "pm_count_instrumented", "pm_plan_last_kernel_ms", "pm_plan_select",
-    "pm_plan_autotune",
+    "pm_plan_autotune", "pm_count_c4_noalloc",
 ]
 
 
@@ -162,6 +163,16 @@ def use_cuda_allocator():
     global _torch_alloc_refs
     _check(_lib.pm_set_allocator(None, None, None), "pm_set_allocator")
     _torch_alloc_refs = None
+
+
+def count_c4_noalloc(rowptr, col, n, out, stream=None):
+    """pm_count_c4_noalloc: edge-induced 4-cycle count of a device CSR into
+    `out` (2 device uint64 words), with no device allocation in the call.
+    rowptr, col and out are CUDA tensors (int64, int32, 2 x int64) the caller
+    owns; the call is asynchronous on the stream."""
+    _check(_lib.pm_count_c4_noalloc(ctypes.c_void_p(rowptr.data_ptr()), ctypes.c_void_p(col.data_ptr()),
+                                    int(n), ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+           "pm_count_c4_noalloc")
 
 
 def make_pattern(k, edge_mask, induced=EDGE_INDUCED, labels=None):
