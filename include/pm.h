@@ -187,6 +187,14 @@ pm_status pm_count(pm_query_plan *p, void *stream, double timeout_s, uint64_t *c
 pm_status pm_count_roots(pm_query_plan *p, void *stream, double timeout_s, const int32_t *roots,
                          int64_t nroots, uint64_t *counts, uint64_t *matched);
 
+/* Record the whole of pm_count for this plan (counter reset, arming, both
+ * matching passes and the piece scan, the wedge kernel, the copy of the raw
+ * counts into pinned host memory) as one CUDA graph; later pm_count calls on
+ * the plan replay it with one cudaGraphLaunch on their stream.  Autotuning
+ * and all buffer set-up happen here, before capture.  timeout_s (<= 0: none)
+ * is fixed into the graph; pm_count's own timeout_s is then ignored. */
+pm_status pm_plan_capture(pm_query_plan *p, void *stream, double timeout_s);
+
 /* pm_count with an instrumented kernel that also returns the algorithmic
  * bytes of the matching: 4 B per element of every set-operation operand,
  * each operand cut to the plan's (lower, upper) id window (merge accounting
@@ -208,6 +216,22 @@ pm_status pm_plan_last_kernel_ms(const pm_query_plan *p, float *ms);
  * bytes, 1 when support >= threshold. */
 pm_status pm_support(pm_query_plan *p, void *stream, double timeout_s, uint64_t threshold,
                      uint64_t *support, uint8_t *frequent);
+
+/* Frequent subgraph mining with MNI support (Section 2, FSM), level-wise
+ * up to max_edges (1..5) edges on a labeled graph.  Level 1: every labeled
+ * edge whose two labels occur in the graph.  Level j+1: connected labeled
+ * patterns made by adding one edge (between existing vertices, or to a new
+ * vertex with a label that occurs) to a frequent level-j pattern, kept only
+ * if every connected one-edge-smaller subpattern is frequent; MNI support is
+ * anti-monotone, so no frequent pattern is lost.  Each level runs pm_plan
+ * (PM_OP_SUPPORT, mode) + pm_support(threshold); frequent means support >=
+ * threshold.  Outputs every candidate of every level, in level order:
+ * out[i] (edge-induced labeled pattern), support[i], frequent[i] (nullable).
+ * cap: entries the caller provides; *n_out: entries produced (PM_EOVERFLOW
+ * with *n_out = the size needed when cap is too small). */
+pm_status pm_fsm(const pm_graph *g, int32_t max_edges, uint64_t threshold, pm_morph_mode mode,
+                 void *stream, double timeout_s, pm_pattern *out, uint64_t *support,
+                 uint8_t *frequent, int32_t cap, int32_t *n_out);
 
 /* Edge-induced 4-cycle count of a graph given as a device CSR, for callers
  * that cannot allocate device memory during the call (a fully reserved

@@ -79,6 +79,8 @@ def _load():
         "pm_plan_select": [vp, i32],
         "pm_plan_autotune": [vp, vp, vp],
         "pm_count_c4_noalloc": [vp, vp, i64, vp, vp],
+        "pm_plan_capture": [vp, vp, dbl],
+        "pm_fsm": [vp, i32, ctypes.c_uint64, ctypes.c_int, vp, dbl, vp, vp, vp, i32, ctypes.POINTER(i32)],
         "pm_count_instrumented": [vp, vp, vp, vp],
         "pm_plan_last_kernel_ms": [vp, ctypes.POINTER(ctypes.c_float)],
     }
@@ -105,7 +107,7 @@ ABI_SYMBOLS = [
     "pm_free_graph", "pm_plan", "pm_plan_get_info", "pm_plan_matched", "pm_free_plan",
     "pm_morph", "pm_count", "pm_count_roots", "pm_support", "pm_strerror", "pm_last_error",
     "pm_plan_export", "pm_count_instrumented", "pm_plan_last_kernel_ms", "pm_plan_select",
-    "pm_plan_autotune", "pm_count_c4_noalloc",
+    "pm_plan_autotune", "pm_count_c4_noalloc", "pm_fsm", "pm_plan_capture",
 ]
 
 
@@ -163,6 +165,24 @@ def use_cuda_allocator():
     global _torch_alloc_refs
     _check(_lib.pm_set_allocator(None, None, None), "pm_set_allocator")
     _torch_alloc_refs = None
+
+
+def fsm(graph, max_edges, threshold, mode=MORPH_NAIVE, stream=None, timeout_s=0.0, cap=1 << 16):
+    """pm_fsm: every candidate of every level as (k, edge_mask, labels),
+    with its MNI support and frequent flag."""
+    while True:
+        arr = (c_pattern * cap)()
+        sup = np.zeros(cap, dtype=np.uint64)
+        freq = np.zeros(cap, dtype=np.uint8)
+        n = ctypes.c_int32()
+        st = _lib.pm_fsm(graph.handle, int(max_edges), int(threshold), int(mode), _stream_handle(stream),
+                         float(timeout_s), arr, _ptr(sup), _ptr(freq), int(cap), ctypes.byref(n))
+        if st == PM_EOVERFLOW:
+            cap = int(n.value)
+            continue
+        _check(st, "pm_fsm")
+        pats = [(arr[i].k, arr[i].edge_mask, list(arr[i].label)[:arr[i].k]) for i in range(n.value)]
+        return pats, [int(x) for x in sup[:n.value]], [bool(x) for x in freq[:n.value]]
 
 
 def count_c4_noalloc(rowptr, col, n, out, stream=None):
@@ -265,6 +285,10 @@ class Plan:
     def select(self, family):
         """Force a plan family for count()/support() (PLANS_AUTO = autotuned)."""
         _check(_lib.pm_plan_select(self._h, family), "pm_plan_select")
+
+    def capture(self, stream=None, timeout_s=0.0):
+        """Record this plan's pm_count as a CUDA graph; count() then replays it."""
+        _check(_lib.pm_plan_capture(self._h, _stream_handle(stream), float(timeout_s)), "pm_plan_capture")
 
     def autotune(self, stream=None):
         fam = np.zeros(self.n_matched, dtype=np.int32)

@@ -112,6 +112,9 @@ struct pm_query_plan {
     int wedge_nblocks = 0;
     size_t bytes_counters = 0, bytes_bitsets = 0, bytes_cols = 0, bytes_wedge = 0;
     bool device_ready = false;
+    // CUDA graph of a whole pm_count (pm_plan_capture): replayed by pm_count
+    cudaGraphExec_t graph_exec = nullptr;
+    uint64_t *h_pinned = nullptr;            // counters (2 per matched) then the Control block
 };
 
 namespace {
@@ -771,6 +774,8 @@ void pm_free_plan(pm_query_plan *p) {
         DeviceGuard dg(p->g->device);
         free_plan_device(p);
     }
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->h_pinned) cudaFreeHost(p->h_pinned);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
     delete p;
@@ -793,7 +798,92 @@ pm_status pm_morph(const pm_query_plan *p, const uint64_t *matched, uint64_t *re
 
 pm_status pm_count(pm_query_plan *p, void *stream, double timeout_s, uint64_t *counts,
                    uint64_t *matched) {
+    if (p && p->graph_exec) {
+        if (!counts) return PM_EINVAL;
+        DeviceGuard dg(p->g->device);
+        cudaStream_t s = (cudaStream_t)stream;
+        cudaError_t e = cudaGraphLaunch(p->graph_exec, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        if (e) return cuda_fail("pm_count (graph replay)", e);
+        const size_t nm = p->morph.matched.size();
+        Control ctl;
+        std::memcpy(&ctl, p->h_pinned + 2 * nm, sizeof(Control));
+        if (ctl.status == 1) {
+            rezero_wedge(p, s);
+            cudaStreamSynchronize(s);
+            set_error("pm_count: deadline expired");
+            return PM_ETIMEOUT;
+        }
+        p->timed = true;
+        if (matched) std::memcpy(matched, p->h_pinned, sizeof(uint64_t) * 2 * nm);
+        (void)timeout_s;
+        return pm_morph(p, p->h_pinned, counts);
+    }
     return run_count(p, stream, timeout_s, nullptr, 0, false, counts, matched);
+}
+
+pm_status pm_plan_capture(pm_query_plan *p, void *stream, double timeout_s) {
+    if (!p || !p->g) {
+        set_error("pm_plan_capture: plan without a graph");
+        return PM_EINVAL;
+    }
+    if (p->op != PM_OP_COUNT) {
+        set_error("pm_plan_capture: counting plans only");
+        return PM_EINVAL;
+    }
+    const pm_graph *g = p->g;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return PM_ECUDA;
+    cudaStream_t user = (cudaStream_t)stream;
+    // everything that allocates or tunes happens before capture
+    pm_status st = ensure_device(p);
+    if (st == PM_OK) st = prepare_active(p, user);
+    if (st != PM_OK) return st;
+    bool needs_wedge = false;
+    for (const DevPlan &dp : p->active.plans) needs_wedge |= dp.kind == PLAN_WEDGE_PAIRS;
+    if (needs_wedge) {
+        st = ensure_wedge(p, user);
+        if (st != PM_OK) return st;
+    }
+    const size_t nm = p->morph.matched.size();
+    if (!p->h_pinned) {
+        cudaError_t e = cudaMallocHost(&p->h_pinned, sizeof(uint64_t) * 2 * nm + sizeof(Control));
+        if (e) return cuda_fail("pm_plan_capture: pinned buffer", e);
+    }
+    cudaError_t e = cudaStreamSynchronize(user);
+    if (e) return cuda_fail("pm_plan_capture", e);
+    cudaStream_t cs;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e) return cuda_fail("pm_plan_capture: stream", e);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (!e) {
+        const DevTasks tasks = all_tasks(g);
+        cudaMemsetAsync(p->d_counters, 0, p->bytes_counters, cs);
+        const uint64_t budget = timeout_s > 0 ? uint64_t(timeout_s * 1e9) : 0;
+        launch_arm(p->d_ctl, budget, cs);
+        cudaEventRecord(p->ev0, cs);
+        st = launch_table(p, p->active, tasks, 1, false, nullptr, cs);
+        cudaEventRecord(p->ev1, cs);
+        cudaMemcpyAsync(p->h_pinned, p->d_counters, sizeof(uint64_t) * 2 * nm,
+                        cudaMemcpyDeviceToHost, cs);
+        cudaMemcpyAsync(p->h_pinned + 2 * nm, p->d_ctl, sizeof(Control), cudaMemcpyDeviceToHost, cs);
+        e = cudaStreamEndCapture(cs, &graph);
+    }
+    cudaStreamDestroy(cs);
+    if (st != PM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e) return cuda_fail("pm_plan_capture: capture", e);
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    e = cudaGraphInstantiate(&p->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e) {
+        p->graph_exec = nullptr;
+        return cuda_fail("pm_plan_capture: instantiate", e);
+    }
+    return PM_OK;
 }
 
 pm_status pm_count_roots(pm_query_plan *p, void *stream, double timeout_s, const int32_t *roots,

@@ -200,6 +200,49 @@ def test_mni_support_against_oracle():
             assert freq == [w >= 20 for w in want]
 
 
+def test_fsm_against_oracle():
+    """Level-wise 3-edge FSM with MNI support (Section 2): the candidates of
+    every level, their supports and the frequent sets, morphed and direct."""
+    n = 512
+    s, d = rmat_edges(9, 8, seed=112)
+    labels = zipf_labels(n, 3, seed=113)
+    og = oracle.prepare_graph(n, s, d, labels)
+    g = load(n, s, d, labels)
+    threshold = 40
+    want_last, want_levels = oracle.fsm(og, 3, threshold)
+    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+        pats, sup, freq = pm.fsm(g, 3, threshold, mode=mode)
+        got = {}
+        for (k, mask, lab), sp, fr in zip(pats, sup, freq):
+            key = algebra.canonical(algebra.Pattern.from_mask(k, mask, lab, False))
+            got[key] = (sp, fr)
+        edges = lambda key: len(key[2])
+        assert {key: v[0] for key, v in got.items() if edges(key) == 3} == want_last
+        for j, level in enumerate(want_levels, start=1):
+            assert sorted(key for key, v in got.items() if edges(key) == j and v[1]) == level
+        assert all(v[1] == (v[0] >= threshold) for v in got.values())
+
+
+def test_batched_random_patterns_captured_graph():
+    """A batch of random connected 3-6 vertex patterns (half vertex-induced,
+    half edge-induced) counted in one plan, replayed from a captured CUDA
+    graph, against the oracle."""
+    from pm_inputs import random_patterns
+    s, d = rmat_edges(7, 6, seed=114)
+    og = oracle.prepare_graph(128, s, d)
+    g = load(128, s, d)
+    pats = random_patterns(48, seed=115)
+    qs = [pm.make_pattern(k, m, ind) for k, m, ind in pats]
+    want = [oracle.count(og, algebra.Pattern.from_mask(k, m, None, bool(ind))) for k, m, ind in pats]
+    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+        plan = pm.Plan(g, qs, mode=mode)
+        direct = plan.count()
+        assert direct == want
+        plan.capture()
+        assert plan.count() == want
+        assert plan.count() == want
+
+
 def test_autotune_choices_are_cached_per_graph():
     s, d = rmat_edges(11, 8, seed=111)
     g = load(2048, s, d)
