@@ -251,6 +251,49 @@ pm_status pm_fsm(const pm_graph *g, int32_t max_edges, uint64_t threshold, pm_mo
 pm_status pm_count_c4_noalloc(const int64_t *rowptr, const int32_t *col, int64_t n,
                               uint64_t *count, void *stream);
 
+/* Serving (continuous batching of count requests against device-resident
+ * graphs).  Each graph gets workers_per_graph worker threads with their own
+ * CUDA streams.  A free worker takes the requests queued for its graph (up
+ * to max_batch_patterns patterns) as one batch: one pm_plan over all their
+ * queries (morph selection with `mode` deduplicates the matched patterns the
+ * requests share) and one pm_count with batch_timeout_s; each request then
+ * receives its own slice of the counts.  Requests arriving while batches run
+ * join the next batch as soon as a worker is free and the batch's device
+ * memory estimate fits hbm_budget_bytes beside the batches in flight;
+ * batches on different workers overlap on the device.  Latency is measured
+ * from pm_server_submit to the end of the request's batch. */
+typedef struct pm_server pm_server;
+typedef struct {
+    int32_t workers_per_graph;
+    int32_t max_batch_patterns;
+    int64_t hbm_budget_bytes;
+    double batch_timeout_s;     /* <= 0: no deadline */
+    int32_t mode;               /* pm_morph_mode */
+    int32_t pad;
+} pm_server_config;
+typedef struct {
+    int64_t requests_submitted, requests_done, batches, patterns_done;
+    int64_t matched_alone;      /* sum over requests of matched patterns if planned alone */
+    int64_t matched_batched;    /* sum over batches of matched patterns (after deduplication) */
+    int64_t timeouts, failures; /* requests whose batch hit the deadline / failed otherwise */
+} pm_server_stats;
+/* graphs stay owned by the caller and must outlive the server. */
+pm_status pm_server_create(const pm_graph *const *graphs, int32_t n_graphs,
+                           const pm_server_config *cfg, pm_server **out);
+/* Queue a request of nq patterns (copied) for graphs[graph]; malformed
+ * patterns are rejected here.  *id identifies it for pm_server_wait. */
+pm_status pm_server_submit(pm_server *s, int32_t graph, const pm_pattern *queries, int32_t nq,
+                           uint64_t *id);
+/* Wait up to timeout_s (< 0: forever, 0: poll) for request id.  *done = 1
+ * when it finished: counts (2*nq words, nullable), *latency_s and
+ * *request_status (the batch's pm_count status) are then filled and the
+ * request is forgotten. */
+pm_status pm_server_wait(pm_server *s, uint64_t id, double timeout_s, int32_t *done,
+                         uint64_t *counts, double *latency_s, pm_status *request_status);
+pm_status pm_server_get_stats(pm_server *s, pm_server_stats *out);
+/* Stops the workers after their current batches; queued requests are dropped. */
+void pm_server_destroy(pm_server *s);
+
 const char *pm_strerror(pm_status s);
 /* Text of the last error raised on the calling thread ("" if none). */
 const char *pm_last_error(void);

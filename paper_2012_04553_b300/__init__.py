@@ -54,6 +54,18 @@ class c_plan_info(ctypes.Structure):
                 ("n_plans", ctypes.c_int32), ("op", ctypes.c_int32)]
 
 
+class c_server_config(ctypes.Structure):
+    _fields_ = [("workers_per_graph", ctypes.c_int32), ("max_batch_patterns", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_int64), ("batch_timeout_s", ctypes.c_double),
+                ("mode", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class c_server_stats(ctypes.Structure):
+    _fields_ = [(nm, ctypes.c_int64) for nm in (
+        "requests_submitted", "requests_done", "batches", "patterns_done", "matched_alone",
+        "matched_batched", "timeouts", "failures")]
+
+
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)
 
@@ -80,6 +92,11 @@ def _load():
         "pm_plan_autotune": [vp, vp, vp],
         "pm_count_c4_noalloc": [vp, vp, i64, vp, vp],
         "pm_plan_capture": [vp, vp, dbl],
+        "pm_server_create": [vp, i32, ctypes.POINTER(c_server_config), ctypes.POINTER(vp)],
+        "pm_server_submit": [vp, i32, ctypes.POINTER(c_pattern), i32, ctypes.POINTER(ctypes.c_uint64)],
+        "pm_server_wait": [vp, ctypes.c_uint64, dbl, ctypes.POINTER(i32), vp, ctypes.POINTER(dbl),
+                           ctypes.POINTER(ctypes.c_int)],
+        "pm_server_get_stats": [vp, ctypes.POINTER(c_server_stats)],
         "pm_fsm": [vp, i32, ctypes.c_uint64, ctypes.c_int, vp, dbl, vp, vp, vp, i32, ctypes.POINTER(i32)],
         "pm_count_instrumented": [vp, vp, vp, vp],
         "pm_plan_last_kernel_ms": [vp, ctypes.POINTER(ctypes.c_float)],
@@ -90,6 +107,8 @@ def _load():
         f.restype = ctypes.c_int
     lib.pm_free_graph.argtypes = [vp]
     lib.pm_free_graph.restype = None
+    lib.pm_server_destroy.argtypes = [vp]
+    lib.pm_server_destroy.restype = None
     lib.pm_free_plan.argtypes = [vp]
     lib.pm_free_plan.restype = None
     lib.pm_strerror.argtypes = [ctypes.c_int]
@@ -108,6 +127,8 @@ ABI_SYMBOLS = [
     "pm_morph", "pm_count", "pm_count_roots", "pm_support", "pm_strerror", "pm_last_error",
     "pm_plan_export", "pm_count_instrumented", "pm_plan_last_kernel_ms", "pm_plan_select",
     "pm_plan_autotune", "pm_count_c4_noalloc", "pm_fsm", "pm_plan_capture",
+    "pm_server_create", "pm_server_submit", "pm_server_wait", "pm_server_get_stats",
+    "pm_server_destroy",
 ]
 
 
@@ -348,5 +369,59 @@ class Plan:
     def __del__(self):
         try:
             self.free()
+        except Exception:
+            pass
+
+
+class Server:
+    """pm_server: continuous batching of count requests over loaded graphs."""
+
+    def __init__(self, graphs, workers_per_graph=2, max_batch_patterns=256,
+                 hbm_budget_bytes=64 << 30, batch_timeout_s=0.0, mode=MORPH_NAIVE):
+        self.graphs = list(graphs)
+        arr = (ctypes.c_void_p * len(self.graphs))(*[g.handle for g in self.graphs])
+        cfg = c_server_config(workers_per_graph, max_batch_patterns, int(hbm_budget_bytes),
+                              float(batch_timeout_s), mode, 0)
+        h = ctypes.c_void_p()
+        _check(_lib.pm_server_create(arr, len(self.graphs), ctypes.byref(cfg), ctypes.byref(h)),
+               "pm_server_create")
+        self._h = h
+        self._nq = {}
+
+    def submit(self, graph, patterns):
+        arr = (c_pattern * len(patterns))(*patterns)
+        rid = ctypes.c_uint64()
+        _check(_lib.pm_server_submit(self._h, int(graph), arr, len(patterns), ctypes.byref(rid)),
+               "pm_server_submit")
+        self._nq[rid.value] = len(patterns)
+        return rid.value
+
+    def wait(self, rid, timeout_s=-1.0):
+        """(done, counts or None, latency_s, status)."""
+        nq = self._nq[rid]
+        out = np.zeros(2 * nq, dtype=np.uint64)
+        done = ctypes.c_int32()
+        lat = ctypes.c_double()
+        st = ctypes.c_int()
+        _check(_lib.pm_server_wait(self._h, ctypes.c_uint64(rid), float(timeout_s), ctypes.byref(done),
+                                   _ptr(out), ctypes.byref(lat), ctypes.byref(st)), "pm_server_wait")
+        if not done.value:
+            return False, None, None, None
+        del self._nq[rid]
+        return True, _words_to_ints(out), lat.value, st.value
+
+    def stats(self):
+        s = c_server_stats()
+        _check(_lib.pm_server_get_stats(self._h, ctypes.byref(s)), "pm_server_get_stats")
+        return {f: getattr(s, f) for f, _ in c_server_stats._fields_}
+
+    def close(self):
+        if self._h:
+            _lib.pm_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass

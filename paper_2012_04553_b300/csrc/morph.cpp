@@ -13,6 +13,7 @@
 //  D_{p^E}[u] = D_{p^V}[u]  u  U_q U_{f in phi(p^E, q^E)} D_{q^V}[f(u)].
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
 
@@ -36,6 +37,25 @@ struct MatchedSet {
         return id;
     }
 };
+
+// superpatterns() of an edge-induced pattern depends only on its class, so
+// the result is cached by canonical key (serving re-plans the same patterns
+// for every batch).
+std::mutex g_super_mu;
+std::map<Key, std::vector<Super>> g_super_cache;
+
+std::vector<Super> cached_superpatterns(const Pat &pe) {
+    const Key key = canonical(pe);
+    {
+        std::lock_guard<std::mutex> lk(g_super_mu);
+        auto it = g_super_cache.find(key);
+        if (it != g_super_cache.end()) return it->second;
+    }
+    std::vector<Super> v = superpatterns(pe);
+    std::lock_guard<std::mutex> lk(g_super_mu);
+    g_super_cache.emplace(key, v);
+    return v;
+}
 
 // Column (orbit index, orbits numbered by smallest member) of every vertex.
 std::vector<int> columns_of(const Pat &p, int *n_columns) {
@@ -77,7 +97,7 @@ pm_status morph_select(const std::vector<Pat> &queries, pm_op op, pm_morph_mode 
         const int e_p = p.n_edges();
         Pat pe = p;
         pe.vi = false;
-        for (const Super &s : superpatterns(pe)) {
+        for (const Super &s : cached_superpatterns(pe)) {
             if (!p.vi) {
                 // Theorem 3.1: p^E from vertex-induced superpatterns
                 Pat q = s.q;

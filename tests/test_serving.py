@@ -1,0 +1,71 @@
+"""Serving loop: every request's result is the same served alone and in a
+concurrent mix (continuous batching across two graphs), and matches the
+oracle; batching deduplicates matched patterns across requests."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import algebra
+import paper_2012_04553_b300 as pm
+from pm_inputs import rmat_edges, random_patterns, uniform_ints
+
+pytestmark = pytest.mark.gpu
+
+
+def make_requests(seed, count, kmax):
+    pats = random_patterns(count * 4, kmin=3, kmax=kmax, seed=seed)
+    sizes = uniform_ints(seed, 2, count, 1, 8)
+    reqs, at = [], 0
+    for i, sz in enumerate(sizes):
+        reqs.append((i % 2, pats[at:at + sz]))
+        at += sz
+        if at >= len(pats):
+            at = 0
+    return reqs
+
+
+def test_results_alone_equal_results_in_mix_and_oracle():
+    graphs_raw = [(256, rmat_edges(8, 8, seed=121)), (512, rmat_edges(9, 6, seed=122))]
+    graphs = [pm.Graph(n, s, d) for n, (s, d) in graphs_raw]
+    ograph = [oracle.prepare_graph(n, s, d) for n, (s, d) in graphs_raw]
+    reqs = make_requests(123, 24, 5)
+    queries = [[pm.make_pattern(k, m, ind) for k, m, ind in pats] for _, pats in reqs]
+    # alone: one request at a time through the server
+    alone = []
+    srv = pm.Server(graphs, workers_per_graph=2, max_batch_patterns=64)
+    for (gi, _), q in zip(reqs, queries):
+        rid = srv.submit(gi, q)
+        done, counts, lat, st = srv.wait(rid)
+        assert done and st == pm.PM_OK
+        alone.append(counts)
+    srv.close()
+    # mix: everything submitted at once, batched and overlapped
+    srv = pm.Server(graphs, workers_per_graph=2, max_batch_patterns=64)
+    ids = [srv.submit(gi, q) for (gi, _), q in zip(reqs, queries)]
+    mixed = []
+    for rid in ids:
+        done, counts, lat, st = srv.wait(rid)
+        assert done and st == pm.PM_OK and lat > 0
+        mixed.append(counts)
+    stats = srv.stats()
+    srv.close()
+    assert mixed == alone
+    assert stats["requests_done"] == len(reqs)
+    assert stats["batches"] < len(reqs)                 # requests were batched
+    assert stats["matched_batched"] < stats["matched_alone"]   # shared patterns matched once
+    # a few requests against the oracle
+    for (gi, pats), counts in list(zip(reqs, alone))[:6]:
+        want = [oracle.count(ograph[gi], algebra.Pattern.from_mask(k, m, None, bool(ind)))
+                for k, m, ind in pats]
+        assert counts == want
+
+
+def test_server_rejects_bad_requests():
+    s, d = rmat_edges(7, 4, seed=124)
+    g = pm.Graph(128, s, d)
+    srv = pm.Server([g])
+    with pytest.raises(pm.PMError):
+        srv.submit(0, [pm.make_pattern(4, 0b100001)])   # disconnected
+    with pytest.raises(pm.PMError):
+        srv.submit(3, [pm.make_pattern(3, 0b111)])      # no such graph
+    srv.close()
