@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--motifs", choices=["4", "45"], default="4")
     ap.add_argument("--direct-deadline", type=float, default=30.0)
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--workload", choices=["mc", "fsm", "batch", "serve"], default="mc",
+                    help="mc: the timed motif-counting line (default); fsm / batch / serve: "
+                         "one measurement line of the other workloads")
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
     return ap.parse_args()
 
 
@@ -267,11 +271,143 @@ def workload_config(args):
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 
+def run_fsm(args):
+    """3-edge FSM with MNI support, threshold 20,000, on R-MAT scale 18 (ef 16,
+    seed 3) with 16 vertex labels drawn Zipf(1.2) (seed 4): wall time of the
+    whole level-wise mining, morphed (edge-induced candidates from
+    vertex-induced superpatterns) and direct."""
+    import torch
+    import paper_2012_04553_b300 as pm
+    from pm_inputs import zipf_labels
+    n = 1 << 18
+    src, dst = cached_rmat(18, 16, 3)
+    labels = zipf_labels(n, 16, s=1.2, seed=4)
+    g = pm.Graph(n, src, dst, labels)
+    out = {}
+    for name, mode in (("morphed", pm.MORPH_NAIVE), ("direct", pm.MORPH_NONE)):
+        pm.fsm(g, 3, 20000, mode=mode)                      # warm-up (autotuning cached)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        pats, sup, freq = pm.fsm(g, 3, 20000, mode=mode)
+        torch.cuda.synchronize()
+        out[name] = {"wall_s": time.time() - t0, "candidates": len(pats),
+                     "frequent": int(sum(freq)),
+                     "frequent_3edge": int(sum(f for (k, m, l), f in zip(pats, freq) if bin(m).count("1") == 3))}
+    line = {"metric": "3-edge FSM wall time (morphed), R-MAT scale 18, 16 Zipf labels, MNI >= 20000",
+            "value": out["morphed"]["wall_s"], "unit": "s", "higher_is_better": False,
+            "n_gpus": 1, "dtype": "int64", "data": "synthetic", "morphed": out["morphed"],
+            "direct": out["direct"],
+            "config": {"workload": "3-edge frequent subgraph mining, MNI support, threshold 20000, "
+                                   "R-MAT scale 18 ef 16 seed 3, 16 labels Zipf(1.2) seed 4"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args):
+    """512 random connected 3-6 vertex patterns (half vertex-, half
+    edge-induced; seed 5) counted with one plan on the scale-20 graph,
+    replayed from a captured CUDA graph, under a 300 s deadline."""
+    import torch
+    import paper_2012_04553_b300 as pm
+    from pm_inputs import random_patterns
+    n = 1 << SCALE
+    src, dst = cached_rmat(SCALE, EDGE_FACTOR, SEED)
+    g = pm.Graph(n, src, dst)
+    pats = random_patterns(512, seed=5)
+    qs = [pm.make_pattern(k, m, ind) for k, m, ind in pats]
+    t0 = time.time()
+    plan = pm.Plan(g, qs, mode=pm.MORPH_NAIVE)
+    t_plan = time.time() - t0
+    t0 = time.time()
+    plan.capture(timeout_s=300.0)
+    t_tune = time.time() - t0
+    torch.cuda.synchronize()
+    t0 = time.time()
+    try:
+        counts = plan.count()
+        status = "ok"
+    except pm.PMTimeout:
+        counts, status = None, "deadline (300 s) expired"
+    wall = time.time() - t0
+    line = {"metric": "batched 512-pattern counting wall time, R-MAT scale 20", "value": wall,
+            "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "int64",
+            "data": "synthetic", "status": status, "n_matched": plan.n_matched,
+            "plan_s": t_plan, "autotune_and_capture_s": t_tune,
+            "patterns_per_s": (512 / wall) if counts else None,
+            "config": {"workload": "512 random connected patterns of 3-6 vertices (uniform over sizes, "
+                                   "alternating vertex-/edge-induced, seed 5), naive morph, one plan, "
+                                   "captured CUDA graph, R-MAT scale 20 ef 16 seed 2"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Poisson stream (200 req/s) of requests of 1-64 random 3-6 vertex
+    patterns against R-MAT graphs of scale 16, 20 and 22 (ef 16; the scale-22
+    graph carries 8 labels Zipf(1.2) and its queries label each vertex with
+    probability 1/2), through the serving loop."""
+    import paper_2012_04553_b300 as pm
+    from pm_inputs import poisson_arrivals, random_patterns, uniform_ints, zipf_labels, uniform01
+    specs = [(16, 16, 61, None), (20, 16, 2, None), (22, 16, 62, 8)]
+    graphs = []
+    for sc, ef, sd, nl in specs:
+        src, dst = cached_rmat(sc, ef, sd)
+        lab = zipf_labels(1 << sc, nl, s=1.2, seed=63) if nl else None
+        graphs.append(pm.Graph(1 << sc, src, dst, lab))
+    arrivals = poisson_arrivals(200.0, args.serve_seconds, seed=6)
+    nreq = len(arrivals)
+    sizes = uniform_ints(6, 40, nreq, 1, 65)
+    which = uniform_ints(6, 41, nreq, 0, 3)
+    pool = random_patterns(int(sizes.sum()), seed=64)
+    nv = sum(k for k, _, _ in pool)
+    label_draw = zipf_labels(nv, 8, s=1.2, seed=66)            # one label per query vertex
+    coin = uniform01(65, 0, np.arange(nv, dtype=np.uint64))    # labeled with probability 1/2
+    srv = pm.Server(graphs, workers_per_graph=2, max_batch_patterns=512,
+                    hbm_budget_bytes=100 << 30, batch_timeout_s=2.0)
+    ids, at, vat, t0 = [], 0, 0, time.time()
+    for i in range(nreq):
+        wait = arrivals[i] - (time.time() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        qs = []
+        for k, m, ind in pool[at:at + sizes[i]]:
+            labels = None
+            if which[i] == 2:
+                labels = [int(label_draw[vat + v]) if coin[vat + v] < 0.5 else -1 for v in range(k)]
+            vat += k
+            qs.append(pm.make_pattern(k, m, ind, labels))
+        at += int(sizes[i])
+        ids.append((srv.submit(int(which[i]), qs), len(qs)))
+    lats, ok_pat, statuses = [], 0, {}
+    for rid, nq in ids:
+        done, counts, lat, st = srv.wait(rid)
+        lats.append(lat)
+        statuses[st] = statuses.get(st, 0) + 1
+        if st == pm.PM_OK:
+            ok_pat += nq
+    wall = time.time() - t0
+    stats = srv.stats()
+    srv.close()
+    line = {"metric": "serving p50/p99 request latency and patterns/s (Poisson 200 req/s)",
+            "value": float(np.percentile(lats, 50)), "unit": "s", "higher_is_better": False,
+            "p50_s": float(np.percentile(lats, 50)), "p99_s": float(np.percentile(lats, 99)),
+            "patterns_per_s_completed": ok_pat / wall, "requests": nreq,
+            "status_counts": {str(k): v for k, v in statuses.items()}, "server": stats,
+            "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"Poisson 200 req/s for {args.serve_seconds:.0f} s, 1-64 random 3-6 vertex "
+                                   "patterns per request, R-MAT scale 16/20/22 ef 16 (scale 22 with 8 "
+                                   "Zipf(1.2) labels, half the query vertices labeled), naive morph, "
+                                   "2 workers per graph, 2 s batch deadline"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload != "mc":
+        if rank == 0:
+            {"fsm": run_fsm, "batch": run_batch, "serve": run_serve}[args.workload](args)
         return
     import torch
     import paper_2012_04553_b300 as pm
