@@ -62,7 +62,14 @@ typedef enum { PM_OP_COUNT = 0, PM_OP_SUPPORT = 1 } pm_op;
 /* Section 4.2 variants: no morphing (query patterns matched as given),
  * naive morphing (edge-induced queries -> vertex-induced superpatterns,
  * vertex-induced queries -> edge-induced superpatterns), and cost-based
- * selection among the alternative sets (Section 4.1). */
+ * selection among the alternative sets (Section 4.1): every count is
+ * obtained the cheapest way — a vertex-induced count by matching it or as
+ * its edge-induced count minus its superpatterns' vertex-induced counts
+ * (Corollary 3.1, recursively), an edge-induced count by matching it or as
+ * a sum over vertex-induced superpatterns (Theorem 3.1) — where the cost of
+ * a pattern is the autotuner's sampled GPU time on the plan's graph (counting
+ * kernels, also for MNI) and patterns already selected for other queries
+ * cost nothing.  PM_MORPH_COST needs a graph in pm_plan. */
 typedef enum { PM_MORPH_NONE = 0, PM_MORPH_NAIVE = 1, PM_MORPH_COST = 2 } pm_morph_mode;
 
 #define PM_MAX_K 8

@@ -2,6 +2,7 @@
 // the plan-family autotuner, launches and the host half of the morph
 // transform.
 #include <algorithm>
+#include <cmath>
 #include <cstddef>
 #include <cstring>
 #include <limits>
@@ -473,6 +474,7 @@ pm_status autotune(pm_query_plan *p, cudaStream_t s) {
         p->choice[j] = best_f;
         std::lock_guard<std::mutex> lk(g->tune_mu);
         g->tuned[key] = best_f;
+        g->tuned_ms[key] = best;
     }
     return PM_OK;
 }
@@ -501,6 +503,33 @@ pm_status prepare_active(pm_query_plan *p, cudaStream_t s) {
         p->active.dirty = true;
     }
     return upload_table(p->active, p->g->device);
+}
+
+// Cost of matching one pattern on a graph, for cost-based morph selection:
+// the autotuner's sampled time of its faster plan family (cached per graph);
+// a pattern whose sampled runs both hit the deadline costs 1e9 ms.
+double pattern_cost(const pm_graph *g, const Pat &q) {
+    const Key key = canonical(q);
+    {
+        std::lock_guard<std::mutex> lk(g->tune_mu);
+        auto it = g->tuned_ms.find(key);
+        if (it != g->tuned_ms.end()) return std::isfinite(it->second) ? it->second : 1e9;
+    }
+    pm_pattern r{};
+    r.k = q.k;
+    r.edge_mask = q.mask();
+    for (int u = 0; u < PM_MAX_K; u++) r.label[u] = u < q.k ? q.lab[u] : -1;
+    r.induced = q.vi ? PM_VERTEX_INDUCED : PM_EDGE_INDUCED;
+    pm_query_plan *tmp = nullptr;
+    if (pm_plan(g, &r, 1, PM_OP_COUNT, PM_MORPH_NONE, &tmp) != PM_OK) return 1e9;
+    double ms = 1e9;
+    if (pm_plan_autotune(tmp, nullptr, nullptr) == PM_OK) {
+        std::lock_guard<std::mutex> lk(g->tune_mu);
+        auto it = g->tuned_ms.find(canonical(tmp->morph.matched[0]));
+        if (it != g->tuned_ms.end() && std::isfinite(it->second)) ms = it->second;
+    }
+    pm_free_plan(tmp);
+    return ms;
 }
 
 pm_status run_count(pm_query_plan *p, void *stream, double timeout_s, const int32_t *roots,
@@ -660,7 +689,9 @@ pm_status pm_plan(const pm_graph *g, const pm_pattern *queries, int32_t nq, pm_o
     p->g = g;
     p->op = op;
     std::string why;
-    pm_status st = morph_select(pats, op, mode, p->morph, &why);
+    std::function<double(const Pat &)> cost;
+    if (mode == PM_MORPH_COST && g) cost = [g](const Pat &q) { return pattern_cost(g, q); };
+    pm_status st = morph_select(pats, op, mode, p->morph, &why, g ? &cost : nullptr);
     if (st != PM_OK) {
         set_error("pm_plan: " + why);
         delete p;

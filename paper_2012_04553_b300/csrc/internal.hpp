@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <string>
@@ -29,6 +30,7 @@ struct pm_graph {
     // (0 rooted, 1 free); shared by every plan made on this graph.
     mutable std::mutex tune_mu;
     mutable std::map<pm::Key, int> tuned;
+    mutable std::map<pm::Key, double> tuned_ms;   // sampled time of the chosen family
     pm::DevGraph dev() const {
         return pm::DevGraph{n, 2 * m, d_rowptr, d_col, d_labels};
     }
@@ -56,8 +58,10 @@ struct MorphPlan {
 
 // Morph selection (Section 4.1, step a).  Returns PM_OK or an error status
 // with *why set.
+// cost (PM_MORPH_COST only): device cost of matching one pattern as given.
 pm_status morph_select(const std::vector<Pat> &queries, pm_op op, pm_morph_mode mode,
-                       MorphPlan &out, std::string *why);
+                       MorphPlan &out, std::string *why,
+                       const std::function<double(const Pat &)> *cost = nullptr);
 
 // Rooted matching plans of one pattern (one per automorphism orbit).
 // counting: the plans serve pm_count (a 4-cycle may then use the wedge kernel).

@@ -12,8 +12,10 @@
 // edge-from-vertex direction exists (a union has no inverse, Section 3.2.3):
 //  D_{p^E}[u] = D_{p^V}[u]  u  U_q U_{f in phi(p^E, q^E)} D_{q^V}[f(u)].
 #include <algorithm>
+#include <functional>
 #include <map>
 #include <mutex>
+#include <set>
 #include <numeric>
 #include <string>
 
@@ -73,11 +75,151 @@ std::vector<int> columns_of(const Pat &p, int *n_columns) {
 
 }  // namespace
 
+// For every query column, the matched bitsets (matched pattern, column)
+// whose union is the column's MNI domain (Theorem 3.2).
+void fill_mni_sources(MorphPlan &out) {
+    const std::vector<Pat> &queries = out.queries;
+    {
+        out.mni_sources.assign(queries.size(), {});
+        for (size_t i = 0; i < queries.size(); i++) {
+            Pat p = queries[i];
+            if (p.is_clique()) p.vi = false;
+            int nqc = 0;
+            std::vector<int> qcol = columns_of(p, &nqc);
+            out.mni_sources[i].assign(nqc, {});
+            std::vector<int> rep(nqc, -1);
+            for (int u = 0; u < p.k; u++)
+                if (rep[qcol[u]] < 0) rep[qcol[u]] = u;
+            // Every matched pattern this query draws on, with the maps phi(p^E, q^E)
+            Pat pe = p;
+            pe.vi = false;
+            for (const Term &t : out.terms[i]) {
+                const Pat &q = out.matched[t.matched];
+                Pat qe = q;
+                qe.vi = false;
+                std::vector<Perm> fs = (q.vi || q.is_clique()) && !p.vi ? embeddings(pe, qe)
+                                                                         : embeddings(p, q);
+                for (int c = 0; c < nqc; c++) {
+                    auto &dst = out.mni_sources[i][c];
+                    for (const Perm &f : fs) {
+                        std::pair<int, int> src{t.matched, out.matched_orbit[t.matched][f[rep[c]]]};
+                        if (std::find(dst.begin(), dst.end(), src) == dst.end()) dst.push_back(src);
+                    }
+                }
+            }
+        }
+    }
+}
+
+namespace {
+
+// Cost-based selection (Section 4.1, "pattern morphing optimizer").  A
+// count is "known" as a signed combination of matched patterns.  For a
+// vertex-induced count there are two ways: match p^V, or match p^E and
+// subtract c(p, q) * (known vertex-induced count) for every non-isomorphic
+// superpattern q (Corollary 3.1, applied recursively).  For an edge-induced
+// count: match p^E, or add c(p, q) * (known vertex-induced count) over all
+// superpatterns q, p included (Theorem 3.1).  MNI has no subtraction
+// (Section 3.2.3), so its vertex-induced domains are always matched
+// directly.  Each choice minimises the summed cost of the patterns it adds
+// to those already selected (patterns shared between queries cost once).
+struct CostSelector {
+    pm_op op;
+    const std::function<double(const Pat &)> &cost;
+    std::map<Key, double> cost_memo;
+    std::set<Key> selected;                                  // patterns committed so far
+    std::map<Key, Pat> pats;
+    std::map<Key, std::map<Key, int64_t>> known_v;           // memo: combination per pattern class
+
+    double c(const Pat &q) {
+        const Key k = canonical(q);
+        auto it = cost_memo.find(k);
+        if (it != cost_memo.end()) return it->second;
+        const double v = cost(q);
+        cost_memo[k] = v;
+        return v;
+    }
+    static void add(std::map<Key, int64_t> &acc, const std::map<Key, int64_t> &x, int64_t f) {
+        for (auto &kv : x) acc[kv.first] += f * kv.second;
+    }
+    // cost of the patterns of a combination that are not selected yet
+    double marginal(const std::map<Key, int64_t> &combo) {
+        double t = 0;
+        for (auto &kv : combo)
+            if (kv.second != 0 && !selected.count(kv.first)) t += c(pats[kv.first]);
+        return t;
+    }
+    std::map<Key, int64_t> single(const Pat &q) {
+        Pat n = canonical_form(q);
+        const Key k = canonical(n);
+        pats[k] = n;
+        return {{k, 1}};
+    }
+    std::map<Key, int64_t> vertex_induced(const Pat &p) {
+        Pat pv = p;
+        pv.vi = !p.is_clique();
+        const Key key = canonical(pv);
+        auto it = known_v.find(key);
+        if (it != known_v.end()) return it->second;
+        std::map<Key, int64_t> direct = single(pv);
+        std::map<Key, int64_t> best = direct;
+        if (!p.is_clique() && op == PM_OP_COUNT) {
+            Pat pe = p;
+            pe.vi = false;
+            std::map<Key, int64_t> via = single(pe);
+            for (const Super &s : cached_superpatterns(pe)) {
+                if (canonical(s.q) == key) continue;          // p itself
+                add(via, vertex_induced(s.q), -s.coef);
+            }
+            if (marginal(via) < marginal(direct)) best = via;
+        }
+        known_v[key] = best;
+        return best;
+    }
+    std::map<Key, int64_t> edge_induced(const Pat &p) {
+        Pat pe = p;
+        pe.vi = false;
+        std::map<Key, int64_t> direct = single(pe);
+        if (p.is_clique()) return direct;
+        std::map<Key, int64_t> via;
+        for (const Super &s : cached_superpatterns(pe)) add(via, vertex_induced(s.q), s.coef);
+        return marginal(via) < marginal(direct) ? via : direct;
+    }
+    void commit(const std::map<Key, int64_t> &combo) {
+        for (auto &kv : combo)
+            if (kv.second != 0) selected.insert(kv.first);
+    }
+};
+
+}  // namespace
+
 pm_status morph_select(const std::vector<Pat> &queries, pm_op op, pm_morph_mode mode,
-                       MorphPlan &out, std::string *why) {
+                       MorphPlan &out, std::string *why,
+                       const std::function<double(const Pat &)> *cost) {
     if (mode == PM_MORPH_COST) {
-        if (why) *why = "cost-based morph selection is not implemented";
-        return PM_EUNSUPPORTED;
+        if (!cost) {
+            if (why) *why = "cost-based morph selection needs a graph to measure costs on";
+            return PM_EINVAL;
+        }
+        CostSelector sel{op, *cost};
+        MatchedSet ms;
+        out.queries = queries;
+        out.terms.assign(queries.size(), {});
+        for (size_t i = 0; i < queries.size(); i++) {
+            Pat p = queries[i];
+            if (p.is_clique()) p.vi = false;
+            std::map<Key, int64_t> combo = p.vi ? sel.vertex_induced(p) : sel.edge_induced(p);
+            sel.commit(combo);
+            for (auto &kv : combo)
+                if (kv.second != 0) out.terms[i].push_back({ms.add(sel.pats[kv.first]), kv.second});
+        }
+        out.matched = ms.pats;
+        out.matched_columns.assign(out.matched.size(), 0);
+        out.matched_orbit.assign(out.matched.size(), {});
+        for (size_t j = 0; j < out.matched.size(); j++)
+            out.matched_orbit[j] = columns_of(out.matched[j], &out.matched_columns[j]);
+        if (op == PM_OP_SUPPORT) fill_mni_sources(out);
+        return PM_OK;
     }
     MatchedSet ms;
     out.queries = queries;
@@ -128,36 +270,7 @@ pm_status morph_select(const std::vector<Pat> &queries, pm_op op, pm_morph_mode 
     for (size_t j = 0; j < out.matched.size(); j++)
         out.matched_orbit[j] = columns_of(out.matched[j], &out.matched_columns[j]);
 
-    if (op == PM_OP_SUPPORT) {
-        out.mni_sources.assign(queries.size(), {});
-        for (size_t i = 0; i < queries.size(); i++) {
-            Pat p = queries[i];
-            if (p.is_clique()) p.vi = false;
-            int nqc = 0;
-            std::vector<int> qcol = columns_of(p, &nqc);
-            out.mni_sources[i].assign(nqc, {});
-            std::vector<int> rep(nqc, -1);
-            for (int u = 0; u < p.k; u++)
-                if (rep[qcol[u]] < 0) rep[qcol[u]] = u;
-            // Every matched pattern this query draws on, with the maps phi(p^E, q^E)
-            Pat pe = p;
-            pe.vi = false;
-            for (const Term &t : out.terms[i]) {
-                const Pat &q = out.matched[t.matched];
-                Pat qe = q;
-                qe.vi = false;
-                std::vector<Perm> fs = (q.vi || q.is_clique()) && !p.vi ? embeddings(pe, qe)
-                                                                         : embeddings(p, q);
-                for (int c = 0; c < nqc; c++) {
-                    auto &dst = out.mni_sources[i][c];
-                    for (const Perm &f : fs) {
-                        std::pair<int, int> src{t.matched, out.matched_orbit[t.matched][f[rep[c]]]};
-                        if (std::find(dst.begin(), dst.end(), src) == dst.end()) dst.push_back(src);
-                    }
-                }
-            }
-        }
-    }
+    if (op == PM_OP_SUPPORT) fill_mni_sources(out);
     return PM_OK;
 }
 

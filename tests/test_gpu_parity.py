@@ -51,7 +51,7 @@ def test_motifs_small_rmat_against_oracle(scale, ef, seed, kmax):
     for k in range(3, kmax + 1):
         want_v = oracle.motif_counts_direct(og, k)
         want_e = [oracle.count(og, algebra.Pattern.from_mask(k, m)) for m in algebra.connected_classes(k)]
-        for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+        for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE, pm.MORPH_COST):
             for family in (pm.PLANS_AUTO, pm.PLANS_ROOTED, pm.PLANS_FREE):
                 pv = pm.Plan(g, motif_queries(k), mode=mode)
                 pv.select(family)
@@ -191,7 +191,7 @@ def test_mni_support_against_oracle():
     qs = oracle.labeled_edge_patterns(3, [0, 1, 2])[::2] + oracle.labeled_edge_patterns(2, [0, 1, 2])
     cq = [pm.make_pattern(p.k, p.mask, pm.EDGE_INDUCED, p.labels) for p in qs]
     want = [oracle.support_direct(og, p) for p in qs]
-    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE, pm.MORPH_COST):
         for family in (pm.PLANS_ROOTED, pm.PLANS_FREE):
             plan = pm.Plan(g, cq, op=pm.OP_SUPPORT, mode=mode)
             plan.select(family)
@@ -210,7 +210,7 @@ def test_fsm_against_oracle():
     g = load(n, s, d, labels)
     threshold = 40
     want_last, want_levels = oracle.fsm(og, 3, threshold)
-    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE, pm.MORPH_COST):
         pats, sup, freq = pm.fsm(g, 3, threshold, mode=mode)
         got = {}
         for (k, mask, lab), sp, fr in zip(pats, sup, freq):
@@ -241,6 +241,23 @@ def test_batched_random_patterns_captured_graph():
         plan.capture()
         assert plan.count() == want
         assert plan.count() == want
+
+
+def test_cost_mode_mixed_sets_and_labels():
+    """Cost-based selection may mix direct and morphed patterns per query;
+    whatever it picks, the counts are the oracle's (labeled, 4 and 5 vertices)."""
+    n = 512
+    s, d = rmat_edges(9, 8, seed=116)
+    labels = zipf_labels(n, 2, seed=117)
+    og = oracle.prepare_graph(n, s, d, labels)
+    g = load(n, s, d, labels)
+    qs = oracle.labeled_edge_patterns(3, [0, 1])[::2]
+    for vi in (False, True):
+        cq = [pm.make_pattern(p.k, p.mask, int(vi), p.labels) for p in qs]
+        want = [oracle.count(og, p.with_induced(vi)) for p in qs]
+        assert pm.Plan(g, cq, mode=pm.MORPH_COST).count() == want
+    with pytest.raises(pm.PMError):
+        pm.Plan(None, [pm.make_pattern(3, 0b011)], mode=pm.MORPH_COST)
 
 
 def test_autotune_choices_are_cached_per_graph():
