@@ -297,7 +297,7 @@ class Plan:
         rec = np.dtype([("k", "<i4"), ("n_enum", "<i4"), ("tail", "<i4"), ("closed", "<i4"),
                         ("counter", "<i4"), ("dom_base", "<i4"), ("n_columns", "<i4"),
                         ("split", "<i4"), ("task_space", "<i4"), ("kind", "<i4"),
-                        ("pad", "<i4", (2,)),
+                        ("pair", "<i4"), ("pad", "<i4"),
                         ("lv", level, (8,))])
         out = np.zeros(self.n_plans if family == PLANS_ROOTED else self.n_matched, dtype=rec)
         _check(_lib.pm_plan_export(self._h, family, _ptr(out), out.nbytes), "pm_plan_export")

@@ -712,7 +712,7 @@ pm_status pm_plan(const pm_graph *g, const pm_pattern *queries, int32_t nq, pm_o
         p->rooted.insert(p->rooted.end(), v.begin(), v.end());
         p->rooted_begin.push_back(int(p->rooted.size()));
         p->free_plans.push_back(compile_free_plan(p->morph.matched[j], int(j), p->dom_base[j],
-                                                  p->morph.matched_orbit[j]));
+                                                  p->morph.matched_orbit[j], op == PM_OP_COUNT));
     }
     p->choice.assign(nm, -1);
     if (op == PM_OP_SUPPORT) {

@@ -69,7 +69,7 @@ std::vector<DevPlan> compile_plans(const Pat &p, int counter, int dom_base,
                                    const std::vector<int> &column_of_vertex, bool counting);
 // The free matching plan of one pattern (whole automorphism group broken).
 DevPlan compile_free_plan(const Pat &p, int counter, int dom_base,
-                          const std::vector<int> &column_of_vertex);
+                          const std::vector<int> &column_of_vertex, bool counting);
 
 // Device memory through the configured allocator.
 void *dev_alloc(size_t bytes, int device);

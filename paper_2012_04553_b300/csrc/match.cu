@@ -251,10 +251,11 @@ __device__ __forceinline__ uint64_t operand_bytes(const DevGraph &g, const DevLe
     return bytes;
 }
 
-// Slices of buffer L's prefixes for level L+1, and their scan.
+// Slices of buffer L's prefixes for the level with constraints `nl` (the
+// next level, or a pair's merged level), and their scan.
 template <bool STATS>
-__device__ __forceinline__ void setup_level(const DevGraph &g, const DevPlan &P, LevelBuf *B, int L,
-                                            int lane, uint64_t &stat) {
+__device__ __forceinline__ void setup_level_with(const DevGraph &g, const DevLevel &nl, LevelBuf *B,
+                                                 int L, int lane, uint64_t &stat) {
     LevelBuf &b = B[L];
     const int cnt = b.cnt;
     int32_t lens[2] = {0, 0};
@@ -263,11 +264,11 @@ __device__ __forceinline__ void setup_level(const DevGraph &g, const DevPlan &P,
         const int p = lane + 32 * h;
         if (p < cnt) {
             const Bound m = tuple_of(B, L, p);
-            const Slice s = make_slice(g, P.lv[L + 1], m);
+            const Slice s = make_slice(g, nl, m);
             b.base[p] = s.base;
             b.src[p] = uint8_t(s.src);
             lens[h] = s.len;
-            stat += operand_bytes<STATS>(g, P.lv[L + 1], s, m);
+            stat += operand_bytes<STATS>(g, nl, s, m);
         }
     }
     store_scan(b, lane, lens[0], lens[1]);
@@ -277,6 +278,12 @@ __device__ __forceinline__ void setup_level(const DevGraph &g, const DevPlan &P,
         b.total = cnt > 0 ? b.scan[cnt - 1] : 0;
     }
     __syncwarp();
+}
+
+template <bool STATS>
+__device__ __forceinline__ void setup_level(const DevGraph &g, const DevPlan &P, LevelBuf *B, int L,
+                                            int lane, uint64_t &stat) {
+    setup_level_with<STATS>(g, P.lv[L + 1], B, L, lane, stat);
 }
 
 // Prefix that owns flattened candidate index e of a buffer.
@@ -328,6 +335,33 @@ __device__ bool final_stage(const DevGraph &g, const DevPlan &P, LevelBuf *B, Wa
         return true;
     }
     const DevLevel &lv = P.lv[P.n_enum];
+    if (!DOMAINS && P.pair) {
+        // |A| * |B| per prefix (once per chunk), minus collisions A n B (scanned)
+        if (t_begin == 0) {
+            const DevLevel &lb = P.lv[P.n_enum + 1];
+            for (int p = lane; p < cnt; p += 32) {
+                const Bound m = tuple_of(B, L, p);
+                acc += u128(uint64_t(closed_count(g, lv, m))) * u128(uint64_t(closed_count(g, lb, m)));
+                if (STATS) stat += 48 + 8ull * (__popc(lv.neq) + __popc(lb.neq));
+            }
+        }
+        const DevLevel &lm = P.lv[P.k];
+        setup_level_with<STATS>(g, lm, B, L, lane, stat);
+        const int32_t total = min(b.total, t_end);
+        for (int32_t t0 = t_begin; t0 < total; t0 += 32) {
+            if (deadline_hit(deadline, status, lane, tick)) return false;
+            const int32_t e = t0 + lane;
+            if (e < total) {
+                const int p = prefix_of(b, e);
+                const int32_t off = e - (p ? b.scan[p - 1] : 0);
+                const int32_t x = __ldg(g.col + b.base[p] + off);
+                const Bound m = tuple_of(B, L, p);
+                if (admissible(g, lm, b.src[p], m, x)) acc -= 1;
+            }
+        }
+        __syncwarp();
+        return true;
+    }
     if (!DOMAINS && P.closed) {
         for (int p = lane; p < cnt; p += 32) {
             const Bound m = tuple_of(B, L, p);
@@ -475,13 +509,17 @@ __device__ bool process_chunk(const KernelArgs &A, LevelBuf *B, WarpTail &T, uns
     bool alive = true;
     // second-level ranges may be split when the final stage adds up partial
     // counts (n_enum > 2) or counts a single scanned level one by one
-    const bool splittable = P.n_enum > 2 || (!DOMAINS && !P.closed && P.tail == 1);
+    const bool splittable =
+        P.n_enum > 2 || (!DOMAINS && ((!P.closed && P.tail == 1) || P.pair));
     if (!splittable) {
         alive = final_stage<DOMAINS, STATS>(g, P, B, T, 1, 0, INT_MAX, lane, acc, stat, A.bitsets,
                                            A.words, deadline, status, tick);
     } else {
         uint64_t resetup = 0;
-        setup_level<STATS>(g, P, B, 1, lane, may_defer ? stat : resetup);
+        // the split range is over the second level's candidates, or, for a
+        // pair final right after the task, over the collisions it scans
+        const DevLevel &first = (P.n_enum == 2 && P.pair && !DOMAINS) ? P.lv[P.k] : P.lv[2];
+        setup_level_with<STATS>(g, first, B, 1, lane, may_defer ? stat : resetup);
         const int32_t T1 = B[1].total;
         int32_t t_end_eff = min(t_end, T1);
         if (may_defer && T1 > P.split) {

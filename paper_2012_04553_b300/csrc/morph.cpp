@@ -319,7 +319,7 @@ bool same_common(const DevLevel &a, const DevLevel &b, uint8_t tail_bits) {
 // below the root.
 static DevPlan build_plan(const Pat &p, const std::vector<int> &order, std::vector<Perm> H,
                           bool rooted, int counter, int dom_base,
-                          const std::vector<int> &column_of_vertex) {
+                          const std::vector<int> &column_of_vertex, bool counting) {
     int n_columns = 0;
     for (int c : column_of_vertex) n_columns = std::max(n_columns, c + 1);
     std::vector<int> level_of(p.k);
@@ -387,6 +387,31 @@ static DevPlan build_plan(const Pat &p, const std::vector<int> &order, std::vect
     plan.n_enum = p.k - tail;
     const DevLevel &f = plan.lv[plan.n_enum < p.k ? plan.n_enum : p.k - 1];
     plan.closed = tail > 0 && __builtin_popcount(f.isect) == 1 && f.diff == 0 && f.label < 0;
+    // Independent pair of closed leaves at the end (counting plans only).
+    if (counting && tail == 1 && p.k >= 4 && p.k < PLAN_KMAX) {
+        const int L1 = p.k - 2, L2 = p.k - 1;
+        const DevLevel &a = plan.lv[L1], &b = plan.lv[L2];
+        const uint8_t bit1 = uint8_t(1u << L1);
+        auto closed_level = [](const DevLevel &x) {
+            return __builtin_popcount(x.isect) == 1 && x.diff == 0 && x.label < 0;
+        };
+        if (closed_level(a) && closed_level(b) && !((b.isect | b.diff | b.lt | b.gt) & bit1)) {
+            DevLevel B = b;
+            B.neq &= uint8_t(~bit1);
+            DevLevel M{};
+            M.isect = a.isect | B.isect;
+            M.lt = a.lt | B.lt;
+            M.gt = a.gt | B.gt;
+            M.neq = uint8_t((a.neq | B.neq) & ~(a.isect | B.isect | M.lt | M.gt));
+            M.label = -1;
+            plan.lv[L2] = B;
+            plan.lv[p.k] = M;
+            plan.pair = 1;
+            plan.tail = 2;
+            plan.n_enum = p.k - 2;
+            plan.closed = 1;
+        }
+    }
     // second-level candidates per chunk before the rest is deferred: deeper
     // plans do more work per candidate, so they split finer
     plan.split = plan.n_enum <= 2 ? 4096 : std::max(32, 1024 >> (2 * (plan.n_enum - 3)));
@@ -416,7 +441,7 @@ std::vector<DevPlan> compile_plans(const Pat &p, int counter, int dom_base,
         for (const Perm &s : aut)
             if (s[root] == root) H.push_back(s);
         plans.push_back(build_plan(p, matching_order(p, root), H, true, counter, dom_base,
-                                   column_of_vertex));
+                                   column_of_vertex, counting));
     }
     // the 4-cycle's single rooted plan is counted by the wedge kernel (its
     // levels still describe the same occurrences: root, two lower neighbours
@@ -426,13 +451,13 @@ std::vector<DevPlan> compile_plans(const Pat &p, int counter, int dom_base,
 }
 
 DevPlan compile_free_plan(const Pat &p, int counter, int dom_base,
-                          const std::vector<int> &column_of_vertex) {
+                          const std::vector<int> &column_of_vertex, bool counting) {
     // root at a vertex of highest pattern degree (most intersections early)
     int root = 0;
     for (int u = 1; u < p.k; u++)
         if (__builtin_popcount(p.adj[u]) > __builtin_popcount(p.adj[root])) root = u;
     return build_plan(p, matching_order(p, root), automorphisms(p), false, counter, dom_base,
-                      column_of_vertex);
+                      column_of_vertex, counting);
 }
 
 }  // namespace pm

@@ -22,6 +22,12 @@
 //   x < m_j (j in lt), x > m_j (j in gt)   (root bound, symmetry breaking)
 //   x != m_j (j in neq)                    (injectivity not implied above)
 //   label(x) == label                      (labeled patterns)
+// Pair finals: when the last two vertices u, v are independent leaves (each
+// a single closed adjacency range, no edge, anti-edge or ordering between
+// them, v only required to differ from u), the prefix contributes
+// |A| * |B| - |A n B| (choices of u and v minus collisions u = v), where
+// lv[n_enum] and lv[n_enum + 1] give A and B and lv[k] holds the merged
+// constraints of A n B (counted by a scan); n_enum = k - 2, tail = 2.
 // Levels 0 (root) and 1 (a lower-ranked neighbour of the root) come from the
 // task, an oriented edge.  Levels 2..n_enum-1 are enumerated.  The last `tail`
 // levels share one candidate set C and are totally ordered among themselves,
@@ -73,7 +79,8 @@ struct DevPlan {
     int32_t split;        // second-level candidates a task chunk keeps before deferring the rest
     int32_t task_space;   // TaskSpace
     int32_t kind;         // PlanKind
-    int32_t pad[2];
+    int32_t pair;         // 1: the last two levels are an independent pair (see below)
+    int32_t pad;
     DevLevel lv[PLAN_KMAX];
 };
 

@@ -46,7 +46,13 @@ def run_plans(plans, n_matched, adj, labels, roots=None):
             out = [x for x in c if lo < x < hi and (d["label"] < 0 or labels[x] == d["label"])]
             return sorted(out)
 
+        pair = int(P["pair"]) if "pair" in P.dtype.names else 0
+
         def dfs(L, m):
+            if L == n_enum and pair:
+                A = candidates(L, m)
+                B = candidates(L + 1, m + [None])   # level L+1 has no constraint on level L
+                return len(A) * len(B) - len(set(A) & set(B))
             if L == n_enum:
                 if tail == 0:
                     return 1
