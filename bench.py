@@ -42,10 +42,15 @@ def parse():
     ap.add_argument("--motifs", choices=["4", "45"], default="4")
     ap.add_argument("--direct-deadline", type=float, default=30.0)
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline leg")
-    ap.add_argument("--workload", choices=["mc", "fsm", "batch", "serve"], default="mc",
+    ap.add_argument("--workload", choices=["mc", "fsm", "batch", "serve", "pattern"], default="mc",
                     help="mc: the timed motif-counting line (default); fsm / batch / serve: "
                          "one measurement line of the other workloads")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--pattern", default="4:63:0",
+                    help="pattern workload: k:edge_mask:induced (induced 1 = vertex-induced)")
+    ap.add_argument("--scale", type=int, default=18, help="R-MAT scale of the pattern workload")
+    ap.add_argument("--seed", type=int, default=7, help="R-MAT seed of the pattern workload")
+    ap.add_argument("--family", choices=["auto", "rooted", "free"], default="auto")
     return ap.parse_args()
 
 
@@ -399,6 +404,22 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_pattern(args):
+    """One pattern on R-MAT (scale, ef 16, seed), matched as given: device
+    time of the matching kernels (profiling target)."""
+    import torch
+    import paper_2012_04553_b300 as pm
+    k, mask, ind = (int(x) for x in args.pattern.split(":"))
+    src, dst = cached_rmat(args.scale, 16, args.seed)
+    g = pm.Graph(1 << args.scale, src, dst)
+    plan = pm.Plan(g, [pm.make_pattern(k, mask, ind)], mode=pm.MORPH_NONE)
+    plan.select({"auto": pm.PLANS_AUTO, "rooted": pm.PLANS_ROOTED, "free": pm.PLANS_FREE}[args.family])
+    counts = plan.count()
+    print(json.dumps({"metric": "single-pattern count, kernel time", "value": plan.last_kernel_ms(),
+                      "unit": "ms", "count": str(counts[0]), "pattern": args.pattern,
+                      "scale": args.scale, "seed": args.seed, "family": args.family}), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
@@ -407,7 +428,8 @@ def main():
         return
     if args.workload != "mc":
         if rank == 0:
-            {"fsm": run_fsm, "batch": run_batch, "serve": run_serve}[args.workload](args)
+            {"fsm": run_fsm, "batch": run_batch, "serve": run_serve,
+             "pattern": run_pattern}[args.workload](args)
         return
     import torch
     import paper_2012_04553_b300 as pm
