@@ -118,7 +118,11 @@ pm_status pm_set_allocator(pm_alloc_fn alloc, pm_free_fn release, void *ctx);
  * labels: n bytes or NULL (unlabeled).  The graph is renumbered by
  * (degree, id) ascending, stored as CSR with sorted rows (int64 row offsets,
  * int32 column ids, uint8 labels) on `device`, uploaded on `stream`, and the
- * call returns after the upload completes.  Errors: PM_EINVAL (null pointer,
+ * call returns after the upload completes.  Vertices of degree >= the
+ * environment variable PM_HUB_MIN_DEGREE (default 1024) also get an n-bit
+ * adjacency bitmap (highest degrees first, at most 256 MiB in total) that
+ * turns membership tests in their lists into single bit reads.
+ * Errors: PM_EINVAL (null pointer,
  * n < 1 or n > 2^31-1, an id outside [0, n)), PM_ENOMEM, PM_ECUDA. */
 pm_status pm_load_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_t *dst,
                         const uint8_t *labels, int device, void *stream, pm_graph **out);

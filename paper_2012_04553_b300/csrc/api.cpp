@@ -658,6 +658,8 @@ void pm_free_graph(pm_graph *g) {
     dev_free(g->d_col, sizeof(int32_t) * std::max<int64_t>(2 * g->m, 1), g->device);
     for (int sp = 0; sp < 3; sp++) dev_free(g->d_off[sp], b_rp, g->device);
     dev_free(g->d_labels, g->n, g->device);
+    dev_free(g->d_hub, sizeof(int32_t) * g->n, g->device);
+    dev_free(g->d_bits, sizeof(uint32_t) * size_t(g->n_hubs) * size_t(g->hub_words), g->device);
     delete g;
 }
 

@@ -4,6 +4,7 @@
 // over the host's cores.
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <thread>
 #include <vector>
@@ -155,6 +156,53 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
             return PM_ENOMEM;
         }
         g->bytes = 4 * b_rp + b_col + (labels ? n : 0);
+        // 7. adjacency bitmaps for the highest-degree vertices: every vertex of
+        //    degree >= PM_HUB_MIN_DEGREE (environment, default 1024), highest
+        //    first, within 256 MiB of bitmaps
+        {
+            int64_t min_degree = 1024;
+            if (const char *env = std::getenv("PM_HUB_MIN_DEGREE")) min_degree = std::max(1L, std::atol(env));
+            const int64_t words = (n + 31) / 32;
+            const int64_t cap = std::max<int64_t>(0, (int64_t(256) << 20) / (4 * words));
+            int64_t nh = 0;
+            for (int64_t r = n - 1; r >= 0 && nh < cap; r--) {
+                if (rowptr[r + 1] - rowptr[r] < min_degree) break;   // ids ascend by degree
+                nh++;
+            }
+            if (nh > 0) {
+                std::vector<int32_t> hub(n, -1);
+                std::vector<uint32_t> bits(size_t(nh) * size_t(words), 0u);
+                for (int64_t i = 0; i < nh; i++) {
+                    const int64_t r = n - 1 - i;
+                    hub[r] = int32_t(i);
+                    uint32_t *w = bits.data() + size_t(i) * size_t(words);
+                    for (int64_t e = rowptr[r]; e < rowptr[r + 1]; e++)
+                        w[col[e] >> 5] |= 1u << (col[e] & 31);
+                }
+                g->d_hub = (int32_t *)dev_alloc(sizeof(int32_t) * n, device);
+                g->d_bits = (uint32_t *)dev_alloc(sizeof(uint32_t) * bits.size(), device);
+                if (!g->d_hub || !g->d_bits) {
+                    set_error("pm_load_graph: device allocation failed (hub bitmaps)");
+                    pm_free_graph(g);
+                    cudaSetDevice(prev);
+                    return PM_ENOMEM;
+                }
+                g->n_hubs = nh;
+                g->hub_words = words;
+                g->bytes += sizeof(int32_t) * n + sizeof(uint32_t) * bits.size();
+                cudaError_t eh = cudaMemcpyAsync(g->d_hub, hub.data(), sizeof(int32_t) * n,
+                                                 cudaMemcpyHostToDevice, s);
+                if (!eh) eh = cudaMemcpyAsync(g->d_bits, bits.data(), sizeof(uint32_t) * bits.size(),
+                                              cudaMemcpyHostToDevice, s);
+                if (!eh) eh = cudaStreamSynchronize(s);   // host vectors die here
+                if (eh) {
+                    set_error(std::string("pm_load_graph: hub upload: ") + cudaGetErrorString(eh));
+                    pm_free_graph(g);
+                    cudaSetDevice(prev);
+                    return PM_ECUDA;
+                }
+            }
+        }
         cudaError_t e1 = cudaMemcpyAsync(g->d_rowptr, rowptr.data(), b_rp, cudaMemcpyHostToDevice, s);
         cudaError_t e2 = nnz ? cudaMemcpyAsync(g->d_col, col.data(), sizeof(int32_t) * nnz,
                                                cudaMemcpyHostToDevice, s) : cudaSuccess;

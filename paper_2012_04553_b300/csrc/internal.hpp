@@ -24,6 +24,9 @@ struct pm_graph {
     int32_t *d_col = nullptr;
     uint8_t *d_labels = nullptr;
     int64_t *d_off[3] = {nullptr, nullptr, nullptr};  // task offsets per TaskSpace, all roots
+    int32_t *d_hub = nullptr;        // hub bitmap index per vertex (-1: none)
+    uint32_t *d_bits = nullptr;      // hub adjacency bitmaps
+    int64_t n_hubs = 0, hub_words = 0;
     int64_t ntasks[3] = {0, 0, 0};
     size_t bytes = 0;
     // Autotuner cache: canonical pattern key -> chosen plan family
@@ -32,7 +35,8 @@ struct pm_graph {
     mutable std::map<pm::Key, int> tuned;
     mutable std::map<pm::Key, double> tuned_ms;   // sampled time of the chosen family
     pm::DevGraph dev() const {
-        return pm::DevGraph{n, 2 * m, d_rowptr, d_col, d_labels};
+        return pm::DevGraph{n, 2 * m, d_rowptr, d_col, d_labels,
+                            n_hubs ? d_hub : nullptr, d_bits, hub_words};
     }
 };
 

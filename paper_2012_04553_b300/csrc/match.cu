@@ -63,6 +63,10 @@ __device__ __forceinline__ int32_t lower_bound_dev(const int32_t *__restrict__ a
 }
 
 __device__ __forceinline__ bool contains(const DevGraph &g, int32_t v, int32_t x) {
+    if (g.hub) {
+        const int32_t h = __ldg(g.hub + v);
+        if (h >= 0) return (__ldg(g.bits + int64_t(h) * g.words + (x >> 5)) >> (x & 31)) & 1u;
+    }
     const int64_t b = __ldg(g.rowptr + v);
     const int32_t len = int32_t(__ldg(g.rowptr + v + 1) - b);
     const int32_t *a = g.col + b;

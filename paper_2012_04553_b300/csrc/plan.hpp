@@ -92,6 +92,12 @@ struct DevGraph {
     const int64_t *rowptr;     // n + 1
     const int32_t *col;        // nnz
     const uint8_t *labels;     // n, or nullptr
+    // Adjacency bitmaps of the highest-degree vertices: hub[v] >= 0 is the
+    // index of v's bitmap (n bits, `words` 32-bit words each) in `bits`, so a
+    // membership test in N(v) is one bit read instead of a binary search.
+    const int32_t *hub;        // n, or nullptr (no bitmaps)
+    const uint32_t *bits;
+    int64_t words;
 };
 
 // Task spaces: oriented edges (root, v) grouped by root, for each TaskSpace.

@@ -61,6 +61,23 @@ def test_motifs_small_rmat_against_oracle(scale, ef, seed, kmax):
                 assert pe.count() == want_e, (k, mode, family)
 
 
+def test_hub_bitmaps_against_oracle(monkeypatch):
+    """Membership tests through hub adjacency bitmaps (every vertex of degree
+    >= 16 gets one here) give the oracle's counts, rooted and free plans."""
+    monkeypatch.setenv("PM_HUB_MIN_DEGREE", "16")
+    n = 512
+    s, d = rmat_edges(9, 8, seed=118)
+    og = oracle.prepare_graph(n, s, d)
+    g = load(n, s, d)
+    for k in (3, 4):
+        want_v = oracle.motif_counts_direct(og, k)
+        for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+            for family in (pm.PLANS_ROOTED, pm.PLANS_FREE):
+                plan = pm.Plan(g, motif_queries(k), mode=mode)
+                plan.select(family)
+                assert plan.count() == want_v, (k, mode, family)
+
+
 def test_six_vertex_patterns_against_oracle():
     s, d = rmat_edges(7, 5, seed=104)
     og = oracle.prepare_graph(128, s, d)
