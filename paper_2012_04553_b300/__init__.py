@@ -23,6 +23,7 @@ OP_COUNT, OP_SUPPORT = 0, 1
 MORPH_NONE, MORPH_NAIVE, MORPH_COST = 0, 1, 2
 MAX_K = 8
 PLANS_AUTO, PLANS_ROOTED, PLANS_FREE = -1, 0, 1
+LAUNCH_PER_PATTERN, LAUNCH_SINGLE = 0, 1
 
 
 class PMError(RuntimeError):
@@ -89,6 +90,7 @@ def _load():
         "pm_support": [vp, vp, dbl, ctypes.c_uint64, vp, vp],
         "pm_plan_export": [vp, i32, vp, i64],
         "pm_plan_select": [vp, i32],
+        "pm_plan_set_launch": [vp, i32],
         "pm_plan_autotune": [vp, vp, vp],
         "pm_count_c4_noalloc": [vp, vp, i64, vp, vp],
         "pm_plan_capture": [vp, vp, dbl],
@@ -128,7 +130,7 @@ ABI_SYMBOLS = [
     "pm_plan_export", "pm_count_instrumented", "pm_plan_last_kernel_ms", "pm_plan_select",
     "pm_plan_autotune", "pm_count_c4_noalloc", "pm_fsm", "pm_plan_capture",
     "pm_server_create", "pm_server_submit", "pm_server_wait", "pm_server_get_stats",
-    "pm_server_destroy",
+    "pm_server_destroy", "pm_plan_set_launch",
 ]
 
 
@@ -306,6 +308,10 @@ class Plan:
     def select(self, family):
         """Force a plan family for count()/support() (PLANS_AUTO = autotuned)."""
         _check(_lib.pm_plan_select(self._h, family), "pm_plan_select")
+
+    def set_launch(self, mode):
+        """LAUNCH_PER_PATTERN (default) or LAUNCH_SINGLE (one persistent launch)."""
+        _check(_lib.pm_plan_set_launch(self._h, mode), "pm_plan_set_launch")
 
     def capture(self, stream=None, timeout_s=0.0):
         """Record this plan's pm_count as a CUDA graph; count() then replays it."""

@@ -90,6 +90,7 @@ struct pm_query_plan {
     std::vector<DevPlan> free_plans;
     std::vector<int> choice;        // per matched pattern: 0 rooted, 1 free, -1 undecided
     int forced = -1;                // pm_plan_select: -1 = autotuned per pattern
+    int launch_mode = PM_LAUNCH_PER_PATTERN;
     PlanTable active;               // pm_count / pm_support
     PlanTable rooted_table;         // pm_count_roots
     uint64_t *d_counters = nullptr;
@@ -302,10 +303,12 @@ pm_status ensure_device(pm_query_plan *p) {
     p->bytes_counters = sizeof(uint64_t) * 2 * std::max<size_t>(nm, 1);
     p->d_counters = (uint64_t *)dev_alloc(p->bytes_counters, g->device);
     p->d_ctl = (Control *)dev_alloc(sizeof(Control), g->device);
-    // deferral list: one entry per first-pass chunk at most (capped)
+    // deferral list: room for every first-pass chunk of the largest table,
+    // up to 2^26 entries (768 MiB); beyond that, oversized chunks run unsplit
     const int64_t per_plan = (std::max(g->ntasks[2], int64_t(1)) + 31) / 32;
     const int64_t nplans = int64_t(std::max(p->rooted.size(), p->free_plans.size()));
-    p->defer_cap = uint32_t(std::min<int64_t>(std::max<int64_t>(per_plan * nplans, 1024), 1 << 22));
+    p->defer_cap = uint32_t(std::min<int64_t>(std::max<int64_t>(per_plan * nplans, 1024),
+                                              int64_t(1) << 26));
     p->d_defer = (Deferred *)dev_alloc(sizeof(Deferred) * p->defer_cap, g->device);
     p->d_piece_off = (uint32_t *)dev_alloc(sizeof(uint32_t) * p->defer_cap, g->device);
     if (!p->d_counters || !p->d_ctl || !p->d_defer || !p->d_piece_off) {
@@ -391,7 +394,25 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
     L.stats = stats;
     int n_setops = 0;
     while (n_setops < L.nplans && t.plans[n_setops].kind == PLAN_SETOPS) n_setops++;
-    if (n_setops > 0 && L.n_echunks > 0) {
+    if (n_setops > 0 && L.n_echunks > 0 && p->launch_mode == PM_LAUNCH_PER_PATTERN) {
+        // one launch sequence per matched pattern (plans of a pattern are adjacent)
+        int b = 0;
+        while (b < n_setops) {
+            int e = b + 1;
+            while (e < n_setops && t.plans[e].counter == t.plans[b].counter) e++;
+            MatchLaunch G = L;
+            G.plans = t.d + b;
+            G.nplans = e - b;
+            std::vector<DevPlan> sub(t.plans.begin() + b, t.plans.begin() + e);
+            G.n_echunks = echunks_for(sub, tasks);
+            G.max_enum = 2;
+            for (const DevPlan &dp : sub) G.max_enum = std::max(G.max_enum, int(dp.n_enum));
+            if (b > 0 && launch_rearm(p->d_ctl, s)) return PM_ECUDA;
+            const int rc = domains ? launch_domains(G, s) : launch_count(G, s);
+            if (rc) return PM_ECUDA;
+            b = e;
+        }
+    } else if (n_setops > 0 && L.n_echunks > 0) {
         L.nplans = n_setops;
         const int rc = domains ? launch_domains(L, s) : launch_count(L, s);
         if (rc) return PM_ECUDA;
@@ -766,6 +787,16 @@ pm_status pm_plan_export(const pm_query_plan *p, int32_t family, void *out, int6
         return PM_EINVAL;
     }
     std::memcpy(out, v.data(), size_t(need));
+    return PM_OK;
+}
+
+pm_status pm_plan_set_launch(pm_query_plan *p, int32_t mode) {
+    if (!p || (mode != PM_LAUNCH_PER_PATTERN && mode != PM_LAUNCH_SINGLE)) return PM_EINVAL;
+    if (p->graph_exec) {
+        set_error("pm_plan_set_launch: the plan was already captured");
+        return PM_EINVAL;
+    }
+    p->launch_mode = mode;
     return PM_OK;
 }
 

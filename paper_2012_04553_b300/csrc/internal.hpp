@@ -84,6 +84,8 @@ void set_error(const std::string &msg);
 // Kernel launchers (match.cu).
 // Resets the control block and arms the deadline (budget_ns = 0: none).
 int launch_arm(Control *d_ctl, uint64_t budget_ns, void *stream);
+// Resets the work counters, keeping the status and deadline.
+int launch_rearm(Control *d_ctl, void *stream);
 // One matching launch (both passes).  max_enum: largest n_enum over the
 // plans (sizes the per-warp level buffers); stats (nullable): instrumented
 // run adding the algorithmic bytes read.

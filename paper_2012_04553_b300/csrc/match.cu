@@ -530,7 +530,7 @@ __device__ bool process_chunk(const KernelArgs &A, LevelBuf *B, WarpTail &T, uns
             if (lane == 0) {
                 const uint32_t slot = atomicAdd(&A.ctl->n_deferred, 1u);
                 if (slot < A.defer_cap) {
-                    A.defer[slot].chunk = c;
+                    A.defer[slot].chunk = uint32_t(c);
                     A.defer[slot].total = uint32_t(T1);
                     t_end_eff = P.split;
                 }
@@ -812,6 +812,20 @@ int launch_wedge_pairs(const DevGraph &g, const DevTasks &tasks, int counter, ui
         return -1;
     }
     return 0;
+}
+
+// Resets the work counters between launches that share one armed deadline.
+__global__ void rearm_kernel(Control *ctl) {
+    ctl->work = 0;
+    ctl->work2 = 0;
+    ctl->work3 = 0;
+    ctl->n_deferred = 0;
+    ctl->n_pieces = 0;
+}
+
+int launch_rearm(Control *d_ctl, void *stream) {
+    rearm_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(d_ctl);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 __global__ void arm_kernel(Control *ctl, uint64_t budget_ns) {

@@ -130,9 +130,8 @@ struct Control {
 // A chunk whose second-level candidate range [split, total) awaits the
 // second pass.
 struct Deferred {
-    unsigned long long chunk;
+    uint32_t chunk;
     uint32_t total;
-    uint32_t pad;
 };
 
 }  // namespace pm

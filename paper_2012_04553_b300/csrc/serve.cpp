@@ -61,12 +61,12 @@ namespace {
 
 double seconds(Clock::duration d) { return std::chrono::duration<double>(d).count(); }
 
-// Device memory a batch may use: plan buffers and the deferral list
-// (bounded by 80 MiB) plus the 4-cycle wedge counters (one n-word array per
-// SM) when the batch could need them.
+// Device memory a batch may use: plan buffers, the deferral list (at most
+// 2^26 entries of 12 bytes) and the 4-cycle wedge counters (one n-word array
+// per SM).
 int64_t batch_estimate(const pm_graph *g) {
     const int sms = pm::device_sm_count(g->device);
-    return (int64_t(80) << 20) + int64_t(4) * g->n * std::max(sms, 1);
+    return (int64_t(16) << 20) + (int64_t(12) << 26) + int64_t(4) * g->n * std::max(sms, 1);
 }
 
 void worker_loop(pm_server *s, int graph) {

@@ -252,12 +252,14 @@ def test_batched_random_patterns_captured_graph():
     qs = [pm.make_pattern(k, m, ind) for k, m, ind in pats]
     want = [oracle.count(og, algebra.Pattern.from_mask(k, m, None, bool(ind))) for k, m, ind in pats]
     for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
-        plan = pm.Plan(g, qs, mode=mode)
-        direct = plan.count()
-        assert direct == want
-        plan.capture()
-        assert plan.count() == want
-        assert plan.count() == want
+        for launch in (pm.LAUNCH_PER_PATTERN, pm.LAUNCH_SINGLE):
+            plan = pm.Plan(g, qs, mode=mode)
+            plan.set_launch(launch)
+            direct = plan.count()
+            assert direct == want
+            plan.capture()
+            assert plan.count() == want
+            assert plan.count() == want
 
 
 def test_cost_mode_mixed_sets_and_labels():
