@@ -45,7 +45,9 @@ def parse():
     ap.add_argument("--workload", choices=["mc", "fsm", "batch", "serve", "pattern"], default="mc",
                     help="mc: the timed motif-counting line (default); fsm / batch / serve: "
                          "one measurement line of the other workloads")
-    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--batch-scale", type=int, default=SCALE)
+    ap.add_argument("--serve-kmax", type=int, default=6, help="largest pattern size in serving requests")
     ap.add_argument("--pattern", default="4:63:0",
                     help="pattern workload: k:edge_mask:induced (induced 1 = vertex-induced)")
     ap.add_argument("--scale", type=int, default=18, help="R-MAT scale of the pattern workload")
@@ -317,8 +319,9 @@ def run_batch(args):
     import torch
     import paper_2012_04553_b300 as pm
     from pm_inputs import random_patterns
-    n = 1 << SCALE
-    src, dst = cached_rmat(SCALE, EDGE_FACTOR, SEED)
+    scale = args.batch_scale
+    n = 1 << scale
+    src, dst = cached_rmat(scale, EDGE_FACTOR, SEED)
     g = pm.Graph(n, src, dst)
     pats = random_patterns(512, seed=5)
     qs = [pm.make_pattern(k, m, ind) for k, m, ind in pats]
@@ -337,15 +340,15 @@ def run_batch(args):
     except pm.PMTimeout:
         counts, status = None, "deadline (300 s) expired"
     wall = time.time() - t0
-    line = {"metric": "batched 512-pattern counting wall time, R-MAT scale 20", "value": wall,
+    line = {"metric": f"batched 512-pattern counting wall time, R-MAT scale {scale}", "value": wall,
             "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "int64",
             "data": "synthetic", "status": status, "n_matched": plan.n_matched,
             "plan_s": t_plan, "autotune_and_capture_s": t_tune,
             "patterns_per_s": (512 / wall) if counts else None,
             "config": {"workload": "512 random connected patterns of 3-6 vertices (uniform over sizes, "
                                    "alternating vertex-/edge-induced, seed 5), naive morph, one plan, "
-                                   "single persistent launch, captured CUDA graph, R-MAT scale 20 ef 16 "
-                                   "seed 2"}}
+                                   f"single persistent launch, captured CUDA graph, R-MAT scale {scale} "
+                                   "ef 16 seed 2"}}
     print(json.dumps(line), flush=True)
 
 
@@ -366,12 +369,13 @@ def run_serve(args):
     nreq = len(arrivals)
     sizes = uniform_ints(6, 40, nreq, 1, 65)
     which = uniform_ints(6, 41, nreq, 0, 3)
-    pool = random_patterns(int(sizes.sum()), seed=64)
+    pool = random_patterns(int(sizes.sum()), kmax=args.serve_kmax, seed=64)
     nv = sum(k for k, _, _ in pool)
     label_draw = zipf_labels(nv, 8, s=1.2, seed=66)            # one label per query vertex
     coin = uniform01(65, 0, np.arange(nv, dtype=np.uint64))    # labeled with probability 1/2
     srv = pm.Server(graphs, workers_per_graph=2, max_batch_patterns=512,
-                    hbm_budget_bytes=100 << 30, batch_timeout_s=2.0)
+                    hbm_budget_bytes=100 << 30, batch_timeout_s=0.5, batch_total_s=4.0,
+                    family=pm.PLANS_QUICK)
     ids, at, vat, t0 = [], 0, 0, time.time()
     for i in range(nreq):
         wait = arrivals[i] - (time.time() - t0)
@@ -402,10 +406,12 @@ def run_serve(args):
             "patterns_per_s_completed": ok_pat / wall, "requests": nreq,
             "status_counts": {str(k): v for k, v in statuses.items()}, "server": stats,
             "n_gpus": 1, "data": "synthetic",
-            "config": {"workload": f"Poisson 200 req/s for {args.serve_seconds:.0f} s, 1-64 random 3-6 vertex "
+            "config": {"workload": f"Poisson 200 req/s for {args.serve_seconds:.0f} s, 1-64 random "
+                                   f"3-{args.serve_kmax} vertex "
                                    "patterns per request, R-MAT scale 16/20/22 ef 16 (scale 22 with 8 "
                                    "Zipf(1.2) labels, half the query vertices labeled), naive morph, "
-                                   "2 workers per graph, 2 s batch deadline"}}
+                                   "quick plan family (no autotuning), 2 workers per graph, 0.5 s "
+                                   "deadline per matched pattern, 4 s per batch"}}
     print(json.dumps(line), flush=True)
 
 

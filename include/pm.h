@@ -159,6 +159,9 @@ void pm_free_plan(pm_query_plan *p);
 #define PM_PLANS_AUTO (-1)
 #define PM_PLANS_ROOTED 0
 #define PM_PLANS_FREE 1
+/* No timing: free plans, except the rooted 4-cycle plan that runs the
+ * wedge kernel (for latency-bound callers such as the serving loop). */
+#define PM_PLANS_QUICK 2
 pm_status pm_plan_select(pm_query_plan *p, int32_t family);
 /* How a plan's set-operation plans are launched.  PM_LAUNCH_PER_PATTERN
  * (default): one launch sequence (both matching passes and the piece scan)
@@ -203,6 +206,15 @@ pm_status pm_morph(const pm_query_plan *p, const uint64_t *matched, uint64_t *re
  * deadline and the call returns PM_ETIMEOUT. */
 pm_status pm_count(pm_query_plan *p, void *stream, double timeout_s, uint64_t *counts,
                    uint64_t *matched);
+
+/* pm_count with a deadline per matched pattern: the matched patterns run
+ * one after another (per-pattern launches), each with timeout_per_pattern_s,
+ * capped by timeout_total_s from the start of the call (<= 0: no limit);
+ * a query whose alternative set uses a pattern whose deadline expired gets
+ * status PM_ETIMEOUT and count 0, the others PM_OK and their exact counts.
+ * status: n_queries entries.  Returns PM_OK unless the call itself fails. */
+pm_status pm_count_each(pm_query_plan *p, void *stream, double timeout_per_pattern_s,
+                        double timeout_total_s, uint64_t *counts, int32_t *status);
 
 /* As pm_count, restricted to occurrences whose highest-ranked vertex —
  * rank ordering vertices by (degree, caller id) — is one of the nroots
@@ -280,8 +292,11 @@ pm_status pm_count_c4_noalloc(const int64_t *rowptr, const int32_t *col, int64_t
  * CUDA streams.  A free worker takes the requests queued for its graph (up
  * to max_batch_patterns patterns) as one batch: one pm_plan over all their
  * queries (morph selection with `mode` deduplicates the matched patterns the
- * requests share) and one pm_count with batch_timeout_s; each request then
- * receives its own slice of the counts.  Requests arriving while batches run
+ * requests share) and one pm_count_each with batch_timeout_s as the deadline
+ * of each matched pattern and batch_total_s for the batch; each request then
+ * receives its own slice of the
+ * counts, and fails with PM_ETIMEOUT only if one of its queries needed a
+ * pattern whose deadline expired.  Requests arriving while batches run
  * join the next batch as soon as a worker is free and the batch's device
  * memory estimate fits hbm_budget_bytes beside the batches in flight;
  * batches on different workers overlap on the device.  Latency is measured
@@ -291,9 +306,10 @@ typedef struct {
     int32_t workers_per_graph;
     int32_t max_batch_patterns;
     int64_t hbm_budget_bytes;
-    double batch_timeout_s;     /* <= 0: no deadline */
+    double batch_timeout_s;     /* deadline of each matched pattern of a batch (<= 0: none) */
+    double batch_total_s;       /* deadline of the whole batch (<= 0: none) */
     int32_t mode;               /* pm_morph_mode */
-    int32_t pad;
+    int32_t family;             /* plan family for every batch (pm_plan_select) */
 } pm_server_config;
 typedef struct {
     int64_t requests_submitted, requests_done, batches, patterns_done;

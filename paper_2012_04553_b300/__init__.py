@@ -22,7 +22,7 @@ EDGE_INDUCED, VERTEX_INDUCED = 0, 1
 OP_COUNT, OP_SUPPORT = 0, 1
 MORPH_NONE, MORPH_NAIVE, MORPH_COST = 0, 1, 2
 MAX_K = 8
-PLANS_AUTO, PLANS_ROOTED, PLANS_FREE = -1, 0, 1
+PLANS_AUTO, PLANS_ROOTED, PLANS_FREE, PLANS_QUICK = -1, 0, 1, 2
 LAUNCH_PER_PATTERN, LAUNCH_SINGLE = 0, 1
 
 
@@ -58,7 +58,7 @@ class c_plan_info(ctypes.Structure):
 class c_server_config(ctypes.Structure):
     _fields_ = [("workers_per_graph", ctypes.c_int32), ("max_batch_patterns", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_int64), ("batch_timeout_s", ctypes.c_double),
-                ("mode", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("batch_total_s", ctypes.c_double), ("mode", ctypes.c_int32), ("family", ctypes.c_int32)]
 
 
 class c_server_stats(ctypes.Structure):
@@ -91,6 +91,7 @@ def _load():
         "pm_plan_export": [vp, i32, vp, i64],
         "pm_plan_select": [vp, i32],
         "pm_plan_set_launch": [vp, i32],
+        "pm_count_each": [vp, vp, dbl, dbl, vp, vp],
         "pm_plan_autotune": [vp, vp, vp],
         "pm_count_c4_noalloc": [vp, vp, i64, vp, vp],
         "pm_plan_capture": [vp, vp, dbl],
@@ -130,7 +131,7 @@ ABI_SYMBOLS = [
     "pm_plan_export", "pm_count_instrumented", "pm_plan_last_kernel_ms", "pm_plan_select",
     "pm_plan_autotune", "pm_count_c4_noalloc", "pm_fsm", "pm_plan_capture",
     "pm_server_create", "pm_server_submit", "pm_server_wait", "pm_server_get_stats",
-    "pm_server_destroy", "pm_plan_set_launch",
+    "pm_server_destroy", "pm_plan_set_launch", "pm_count_each",
 ]
 
 
@@ -344,6 +345,14 @@ class Plan:
         _check(_lib.pm_plan_last_kernel_ms(self._h, ctypes.byref(v)), "pm_plan_last_kernel_ms")
         return float(v.value)
 
+    def count_each(self, timeout_per_pattern_s=0.0, timeout_total_s=0.0, stream=None):
+        """(counts, statuses): a deadline per matched pattern, a status per query."""
+        out = np.zeros(2 * self.n_queries, dtype=np.uint64)
+        st = np.zeros(self.n_queries, dtype=np.int32)
+        _check(_lib.pm_count_each(self._h, _stream_handle(stream), float(timeout_per_pattern_s),
+                                  float(timeout_total_s), _ptr(out), _ptr(st)), "pm_count_each")
+        return _words_to_ints(out), [int(x) for x in st]
+
     def count_instrumented(self, stream=None):
         """(counts, algorithmic bytes read by the matching) from an instrumented run."""
         out = np.zeros(2 * self.n_queries, dtype=np.uint64)
@@ -383,11 +392,12 @@ class Server:
     """pm_server: continuous batching of count requests over loaded graphs."""
 
     def __init__(self, graphs, workers_per_graph=2, max_batch_patterns=256,
-                 hbm_budget_bytes=64 << 30, batch_timeout_s=0.0, mode=MORPH_NAIVE):
+                 hbm_budget_bytes=64 << 30, batch_timeout_s=0.0, batch_total_s=0.0,
+                 mode=MORPH_NAIVE, family=PLANS_AUTO):
         self.graphs = list(graphs)
         arr = (ctypes.c_void_p * len(self.graphs))(*[g.handle for g in self.graphs])
         cfg = c_server_config(workers_per_graph, max_batch_patterns, int(hbm_budget_bytes),
-                              float(batch_timeout_s), mode, 0)
+                              float(batch_timeout_s), float(batch_total_s), mode, family)
         h = ctypes.c_void_p()
         _check(_lib.pm_server_create(arr, len(self.graphs), ctypes.byref(cfg), ctypes.byref(h)),
                "pm_server_create")

@@ -110,6 +110,7 @@ struct pm_query_plan {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // bracket the last matching launch
     bool timed = false;
     unsigned long long *d_stats = nullptr;
+    uint8_t *d_timed_out = nullptr;          // pm_count_each: expired matched patterns
     uint32_t *d_wedge = nullptr;             // wedge-kernel counters: blocks x n, kept zero
     int wedge_nblocks = 0;
     size_t bytes_counters = 0, bytes_bitsets = 0, bytes_cols = 0, bytes_wedge = 0;
@@ -213,6 +214,8 @@ void free_plan_device(pm_query_plan *p) {
     dev_free(p->d_col_src, p->bytes_cols, dev);
     dev_free(p->d_popc, p->bytes_cols, dev);
     dev_free(p->d_stats, 256, dev);
+    dev_free(p->d_timed_out, std::max<size_t>(p->morph.matched.size(), 1), dev);
+    p->d_timed_out = nullptr;
     dev_free(p->d_wedge, p->bytes_wedge, dev);
     p->d_wedge = nullptr;
     p->bytes_wedge = 0;
@@ -372,9 +375,12 @@ pm_status ensure_wedge(pm_query_plan *p, cudaStream_t s) {
 }
 
 // Launch both matching passes for one plan table on the given tasks.
+// gate_budget_ns > 0 (with gate_flags): every matched pattern gets its own
+// deadline and its expiry is flagged per pattern (pm_count_each).
 pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tasks,
                        int sample_stride, bool domains, unsigned long long *stats,
-                       cudaStream_t s) {
+                       cudaStream_t s, uint64_t gate_budget_ns = 0,
+                       uint8_t *gate_flags = nullptr) {
     const pm_graph *g = p->g;
     MatchLaunch L{};
     L.g = g->dev();
@@ -407,7 +413,13 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
             G.n_echunks = echunks_for(sub, tasks);
             G.max_enum = 2;
             for (const DevPlan &dp : sub) G.max_enum = std::max(G.max_enum, int(dp.n_enum));
-            if (b > 0 && launch_rearm(p->d_ctl, s)) return PM_ECUDA;
+            if (gate_flags) {
+                if (launch_pattern_gate(p->d_ctl, gate_flags, b > 0 ? t.plans[b - 1].counter : -1,
+                                        gate_budget_ns, s))
+                    return PM_ECUDA;
+            } else if (b > 0 && launch_rearm(p->d_ctl, s)) {
+                return PM_ECUDA;
+            }
             const int rc = domains ? launch_domains(G, s) : launch_count(G, s);
             if (rc) return PM_ECUDA;
             b = e;
@@ -417,6 +429,7 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
         const int rc = domains ? launch_domains(L, s) : launch_count(L, s);
         if (rc) return PM_ECUDA;
     }
+    int last = n_setops > 0 ? t.plans[n_setops - 1].counter : -1;
     for (size_t i = size_t(n_setops); i < t.plans.size(); i++) {
         if (domains) {
             set_error("wedge-pair plans count only");
@@ -424,10 +437,15 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
         }
         pm_status st = ensure_wedge(p, s);
         if (st != PM_OK) return st;
+        if (gate_flags && launch_pattern_gate(p->d_ctl, gate_flags, last, gate_budget_ns, s))
+            return PM_ECUDA;
         if (launch_wedge_pairs(L.g, tasks, t.plans[i].counter, p->d_counters, p->d_wedge,
                                p->wedge_nblocks, sample_stride, p->d_ctl, s))
             return PM_ECUDA;
+        last = t.plans[i].counter;
     }
+    if (gate_flags && last >= 0 && launch_pattern_gate(p->d_ctl, gate_flags, last, 0, s))
+        return PM_ECUDA;
     return PM_OK;
 }
 
@@ -504,7 +522,14 @@ pm_status autotune(pm_query_plan *p, cudaStream_t s) {
 pm_status prepare_active(pm_query_plan *p, cudaStream_t s) {
     const size_t nm = p->morph.matched.size();
     std::vector<int> want(nm);
-    if (p->forced >= 0) {
+    if (p->forced == PM_PLANS_QUICK) {
+        // no timing: the rooted family where it runs the wedge kernel, else free
+        for (size_t j = 0; j < nm; j++) {
+            const bool wedge = p->rooted_begin[j + 1] - p->rooted_begin[j] == 1 &&
+                               p->rooted[p->rooted_begin[j]].kind == PLAN_WEDGE_PAIRS;
+            want[j] = wedge ? PM_PLANS_ROOTED : PM_PLANS_FREE;
+        }
+    } else if (p->forced >= 0) {
         std::fill(want.begin(), want.end(), p->forced);
     } else {
         pm_status st = autotune(p, s);
@@ -631,9 +656,81 @@ pm_status run_count(pm_query_plan *p, void *stream, double timeout_s, const int3
     return pm_morph(p, raw.data(), counts);
 }
 
+// pm_count with a deadline per matched pattern and a status per query.
+pm_status run_count_each(pm_query_plan *p, void *stream, double timeout_s, double total_s,
+                         uint64_t *counts, int32_t *status) {
+    if (!p || !counts || !status) {
+        set_error("pm_count_each: null argument");
+        return PM_EINVAL;
+    }
+    if (p->op != PM_OP_COUNT || !p->g) {
+        set_error("pm_count_each: needs a counting plan made on a graph");
+        return PM_EINVAL;
+    }
+    const pm_graph *g = p->g;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return PM_ECUDA;
+    pm_status st = ensure_device(p);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (st == PM_OK) st = prepare_active(p, s);
+    if (st != PM_OK) return st;
+    const size_t nm = p->morph.matched.size();
+    if (!p->d_timed_out) {
+        p->d_timed_out = (uint8_t *)dev_alloc(std::max<size_t>(nm, 1), g->device);
+        if (!p->d_timed_out) return PM_ENOMEM;
+    }
+    const int saved_mode = p->launch_mode;
+    p->launch_mode = PM_LAUNCH_PER_PATTERN;
+    cudaError_t e = cudaMemsetAsync(p->d_counters, 0, p->bytes_counters, s);
+    if (!e) e = cudaMemsetAsync(p->d_timed_out, 0, std::max<size_t>(nm, 1), s);
+    if (e) {
+        p->launch_mode = saved_mode;
+        return cuda_fail("pm_count_each: memset", e);
+    }
+    const uint64_t budget = timeout_s > 0 ? uint64_t(timeout_s * 1e9) : 0;
+    if (launch_arm(p->d_ctl, total_s > 0 ? uint64_t(total_s * 1e9) : 0, s)) {
+        p->launch_mode = saved_mode;
+        return PM_ECUDA;
+    }
+    cudaEventRecord(p->ev0, s);
+    st = launch_table(p, p->active, all_tasks(g), 1, false, nullptr, s, budget,
+                      p->d_timed_out);
+    p->launch_mode = saved_mode;
+    if (st != PM_OK) return st;
+    cudaEventRecord(p->ev1, s);
+    p->timed = true;
+    std::vector<uint64_t> raw(2 * nm);
+    std::vector<uint8_t> flags(std::max<size_t>(nm, 1));
+    e = cudaMemcpyAsync(raw.data(), p->d_counters, sizeof(uint64_t) * 2 * nm,
+                        cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(flags.data(), p->d_timed_out, nm, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail("pm_count_each: kernel or readback", e);
+    bool any = false;
+    for (size_t j = 0; j < nm; j++) any |= flags[j] != 0;
+    if (any) {
+        rezero_wedge(p, s);
+        cudaStreamSynchronize(s);
+    }
+    st = pm_morph(p, raw.data(), counts);
+    if (st != PM_OK) return st;
+    for (size_t i = 0; i < p->morph.terms.size(); i++) {
+        status[i] = PM_OK;
+        for (const Term &t : p->morph.terms[i])
+            if (flags[t.matched]) status[i] = PM_ETIMEOUT;
+        if (status[i] != PM_OK) counts[2 * i] = counts[2 * i + 1] = 0;
+    }
+    return PM_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+pm_status pm_count_each(pm_query_plan *p, void *stream, double timeout_per_pattern_s,
+                        double timeout_total_s, uint64_t *counts, int32_t *status) {
+    return run_count_each(p, stream, timeout_per_pattern_s, timeout_total_s, counts, status);
+}
 
 pm_status pm_set_allocator(pm_alloc_fn alloc, pm_free_fn release, void *ctx) {
     if ((alloc == nullptr) != (release == nullptr)) {
@@ -801,7 +898,7 @@ pm_status pm_plan_set_launch(pm_query_plan *p, int32_t mode) {
 }
 
 pm_status pm_plan_select(pm_query_plan *p, int32_t family) {
-    if (!p || family < PM_PLANS_AUTO || family > PM_PLANS_FREE) return PM_EINVAL;
+    if (!p || family < PM_PLANS_AUTO || family > PM_PLANS_QUICK) return PM_EINVAL;
     p->forced = family;
     return PM_OK;
 }

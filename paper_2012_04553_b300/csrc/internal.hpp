@@ -86,6 +86,10 @@ void set_error(const std::string &msg);
 int launch_arm(Control *d_ctl, uint64_t budget_ns, void *stream);
 // Resets the work counters, keeping the status and deadline.
 int launch_rearm(Control *d_ctl, void *stream);
+// Per-pattern deadlines: flag pattern prev_counter (>= 0) if its deadline
+// expired, then reset the status and counters and arm budget_ns.
+int launch_pattern_gate(Control *d_ctl, uint8_t *d_timed_out, int prev_counter,
+                        uint64_t budget_ns, void *stream);
 // One matching launch (both passes).  max_enum: largest n_enum over the
 // plans (sizes the per-warp level buffers); stats (nullable): instrumented
 // run adding the algorithmic bytes read.

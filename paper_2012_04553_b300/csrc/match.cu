@@ -814,6 +814,30 @@ int launch_wedge_pairs(const DevGraph &g, const DevTasks &tasks, int counter, ui
     return 0;
 }
 
+// Between the launches of two matched patterns when each pattern has its own
+// deadline: records whether the previous pattern's deadline expired, then
+// clears the status, resets the work counters and arms the next deadline.
+__global__ void pattern_gate_kernel(Control *ctl, uint8_t *timed_out, int prev_counter,
+                                    uint64_t budget_ns) {
+    if (prev_counter >= 0 && ctl->status == 1) timed_out[prev_counter] = 1;
+    ctl->status = 0;
+    ctl->work = 0;
+    ctl->work2 = 0;
+    ctl->work3 = 0;
+    ctl->n_deferred = 0;
+    ctl->n_pieces = 0;
+    const unsigned long long own = budget_ns ? global_ns() + budget_ns : 0;
+    const unsigned long long cap = ctl->call_deadline;
+    ctl->deadline = (own && cap) ? min(own, cap) : (own ? own : cap);
+}
+
+int launch_pattern_gate(Control *d_ctl, uint8_t *d_timed_out, int prev_counter,
+                        uint64_t budget_ns, void *stream) {
+    pattern_gate_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(d_ctl, d_timed_out, prev_counter,
+                                                           budget_ns);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 // Resets the work counters between launches that share one armed deadline.
 __global__ void rearm_kernel(Control *ctl) {
     ctl->work = 0;
@@ -836,6 +860,7 @@ __global__ void arm_kernel(Control *ctl, uint64_t budget_ns) {
     ctl->n_deferred = 0;
     ctl->n_pieces = 0;
     ctl->deadline = budget_ns ? global_ns() + budget_ns : 0;
+    ctl->call_deadline = ctl->deadline;
 }
 
 int launch_arm(Control *d_ctl, uint64_t budget_ns, void *stream) {

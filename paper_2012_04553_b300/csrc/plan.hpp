@@ -125,6 +125,7 @@ struct Control {
     unsigned int n_deferred;      // chunks appended to the deferred list
     unsigned int n_pieces;        // pieces of the deferred chunks (after the scan)
     unsigned long long work3;     // root counter of the wedge kernel
+    unsigned long long call_deadline;  // pm_count_each: caps every pattern's deadline (0 = none)
 };
 
 // A chunk whose second-level candidate range [split, total) awaits the

@@ -10,7 +10,9 @@
 // different workers) run concurrently on the device.  A batch is one pm_plan
 // over the concatenated queries: morph selection deduplicates the matched
 // (morphed) patterns shared by the batch's requests, and every request reads
-// its own slice of the batch's counts.  Admission reserves an estimate of the
+// its own slice of the batch's counts.  Each matched pattern of a batch has
+// its own deadline (pm_count_each), so a pattern that runs out of time fails
+// only the requests whose queries need it.  Admission reserves an estimate of the
 // batch's device memory against `hbm_budget_bytes`; a batch waits until the
 // estimate fits.  Latency is measured from submission to completion.
 #include <algorithm>
@@ -107,6 +109,7 @@ void worker_loop(pm_server *s, int graph) {
             }
         }
         std::vector<uint64_t> counts(2 * all.size(), 0);
+        std::vector<int32_t> qstatus(all.size(), PM_OK);
         pm_query_plan *plan = nullptr;
         pm_status st = pm_plan(g, all.data(), int32_t(all.size()), PM_OP_COUNT,
                                pm_morph_mode(s->cfg.mode), &plan);
@@ -115,7 +118,11 @@ void worker_loop(pm_server *s, int graph) {
             pm_plan_info info;
             pm_plan_get_info(plan, &info);
             matched = info.n_matched;
-            st = pm_count(plan, stream, s->cfg.batch_timeout_s, counts.data(), nullptr);
+            pm_plan_select(plan, s->cfg.family);
+            // a deadline per matched pattern: a heavy pattern fails only the
+            // requests that need it
+            st = pm_count_each(plan, stream, s->cfg.batch_timeout_s, s->cfg.batch_total_s,
+                               counts.data(), qstatus.data());
             pm_free_plan(plan);
         }
         {
@@ -124,13 +131,16 @@ void worker_loop(pm_server *s, int graph) {
             for (size_t b = 0; b < batch.size(); b++) {
                 Request &r = s->reqs[batch[b]];
                 r.status = st;
+                if (st == PM_OK)
+                    for (size_t qi = 0; qi < r.queries.size(); qi++)
+                        if (qstatus[first[b] + qi] != PM_OK) r.status = pm_status(qstatus[first[b] + qi]);
                 r.counts.assign(counts.begin() + 2 * first[b],
                                 counts.begin() + 2 * (first[b] + r.queries.size()));
                 r.finished = now;
                 r.done = true;
                 s->stats.matched_alone += r.matched_alone;
-                if (st == PM_ETIMEOUT) s->stats.timeouts++;
-                else if (st != PM_OK) s->stats.failures++;
+                if (r.status == PM_ETIMEOUT) s->stats.timeouts++;
+                else if (r.status != PM_OK) s->stats.failures++;
             }
             s->stats.batches++;
             s->stats.requests_done += int64_t(batch.size());

@@ -279,6 +279,24 @@ def test_cost_mode_mixed_sets_and_labels():
         pm.Plan(None, [pm.make_pattern(3, 0b011)], mode=pm.MORPH_COST)
 
 
+def test_count_each_fails_only_queries_of_expired_patterns():
+    """A deadline per matched pattern: the vertex-induced 5-star (leaf-wise
+    differences on hubs, seconds of work here) runs out of its 0.5 s while the
+    triangle and wedge queries of the same plan complete exactly."""
+    s, d = rmat_edges(14, 16, seed=119)
+    g = load(1 << 14, s, d)
+    light = [pm.make_pattern(3, 0b111), pm.make_pattern(3, 0b011)]     # triangle, wedge
+    heavy = [pm.make_pattern(5, 0b1111, pm.VERTEX_INDUCED)]              # 5-vertex star
+    want = pm.Plan(g, light, mode=pm.MORPH_NONE).count()
+    plan = pm.Plan(g, light + heavy, mode=pm.MORPH_NONE)
+    plan.select(pm.PLANS_ROOTED)
+    counts, status = plan.count_each(timeout_per_pattern_s=0.5, timeout_total_s=30.0)
+    assert status == [pm.PM_OK, pm.PM_OK, pm.PM_ETIMEOUT]
+    assert counts == want + [0]
+    light_only = pm.Plan(g, light, mode=pm.MORPH_NONE)
+    assert light_only.count_each(timeout_per_pattern_s=0.0) == (want, [pm.PM_OK, pm.PM_OK])
+
+
 def test_autotune_choices_are_cached_per_graph():
     s, d = rmat_edges(11, 8, seed=111)
     g = load(2048, s, d)
