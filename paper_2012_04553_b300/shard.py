@@ -1,0 +1,82 @@
+"""Root-range sharding of a count over several processes (one GPU each).
+
+Every occurrence of a pattern has exactly one highest-ranked vertex, rank
+ordering vertices by (degree, caller id), so the per-root counts of
+pm_count_roots over a partition of the vertex set add up to the whole count.
+Each process holds a replica of the data graph, counts the matched
+(morphed) patterns over its own roots, the partial counts are summed exactly
+across processes, and the morph transform (Theorem 3.1 / Corollary 3.1) is
+applied once to the sum.  The transform is linear over the integers mod
+2^128, so summing matched counts and then morphing equals morphing each
+partial and summing.
+
+The only exchange is one sum of n_matched 128-bit integers, carried out as
+16-bit limbs in int64 so that it is exact for any realistic world size.
+"""
+import numpy as np
+
+LIMB_BITS = 16
+LIMBS = 128 // LIMB_BITS
+
+
+def root_shard(new_id, rank, world):
+    """Caller vertex ids whose occurrences process `rank` of `world` counts.
+
+    new_id[v] is the degree-ordered id of caller vertex v (as returned by
+    Graph.vertex_order).  Work per root grows with its degree, so vertices are
+    dealt out from the highest rank down in a snake order (0,1,..,w-1,w-1,..,0,
+    ...), which keeps the hubs spread evenly over the processes.  The shards
+    of rank 0..world-1 partition range(len(new_id))."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("need 0 <= rank < world")
+    new_id = np.asarray(new_id)
+    by_rank = np.empty(len(new_id), dtype=np.int64)
+    by_rank[new_id] = np.arange(len(new_id))     # caller id at each degree-ordered id
+    desc = by_rank[::-1]
+    pos = np.arange(len(desc)) % (2 * world)
+    owner = np.where(pos < world, pos, 2 * world - 1 - pos)
+    return np.sort(desc[owner == rank]).astype(np.int32)
+
+
+def to_limbs(values):
+    """128-bit integers (Python ints, taken mod 2^128) as int64 limbs, least
+    significant first: shape (len(values), LIMBS)."""
+    out = np.zeros((len(values), LIMBS), dtype=np.int64)
+    mask = (1 << LIMB_BITS) - 1
+    for i, v in enumerate(values):
+        v %= 1 << 128
+        for j in range(LIMBS):
+            out[i, j] = (v >> (LIMB_BITS * j)) & mask
+    return out
+
+
+def from_limbs(limbs):
+    """Inverse of to_limbs after limb-wise sums: carries propagate through
+    Python integers, the result is reduced mod 2^128."""
+    out = []
+    for row in np.asarray(limbs):
+        v = 0
+        for j in range(LIMBS - 1, -1, -1):
+            v = (v << LIMB_BITS) + int(row[j])
+        out.append(v % (1 << 128))
+    return out
+
+
+def allreduce_counts(values, group=None):
+    """Exact sum mod 2^128 of per-process lists of 128-bit counts over a
+    torch.distributed process group (any backend that sums int64)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.from_numpy(to_limbs(values))
+    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return from_limbs(t.numpy())
+
+
+def count_sharded(plan, graph, rank, world, stream=None, timeout_s=0.0, group=None):
+    """Requested counts of `plan` with the roots split over `world` processes:
+    this process counts its shard with pm_count_roots, the matched counts
+    are summed across processes, and every process morphs the sum."""
+    roots = root_shard(graph.vertex_order(), rank, world)
+    _, matched = plan.count_roots(roots, stream=stream, timeout_s=timeout_s, with_matched=True)
+    total = allreduce_counts(matched, group) if world > 1 else matched
+    return plan.morph(total)

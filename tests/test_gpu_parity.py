@@ -173,6 +173,23 @@ def test_root_subsets_partition_and_match_oracle():
     assert plan.count_roots(np.zeros(0, np.int32)) == [0] * 6
 
 
+def test_snake_shards_sum_to_whole_count():
+    # the shards a multi-process run would count, summed here in one process
+    from paper_2012_04553_b300 import shard
+    n = 2048
+    s, d = rmat_edges(11, 8, seed=108)
+    og = oracle.prepare_graph(n, s, d)
+    g = load(n, s, d)
+    plan = pm.Plan(g, motif_queries(4), mode=pm.MORPH_NAIVE)
+    want = oracle.motif_counts_direct(og, 4)
+    for world in (2, 3):
+        matched = [plan.count_roots(shard.root_shard(g.vertex_order(), r, world), with_matched=True)[1]
+                   for r in range(world)]
+        total = [sum(x) % (1 << 128) for x in zip(*matched)]
+        assert plan.morph(total) == want
+    assert shard.count_sharded(plan, g, 0, 1) == want
+
+
 def sampled_roots(deg, seed, count, max_degree):
     """Uniformly drawn vertices whose degree is at most max_degree (the oracle
     enumerates every automorphic copy, about degree^(k-1) maps per root)."""
