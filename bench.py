@@ -8,7 +8,7 @@ device time per step.  The same query set is also run without morphing
 (matched as given) under a deadline, for the morphed-vs-direct comparison.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--motifs 4|45] [--direct-deadline S]
+                    [--direct-deadline S] [--workload mc|mc5|fsm|batch|serve|pattern]
 
 N > 1 (torchrun) runs independent replicas, one graph per GPU; the line
 reports the whole-job rate (sum over ranks / max time over ranks).
@@ -39,12 +39,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--motifs", choices=["4", "45"], default="4")
     ap.add_argument("--direct-deadline", type=float, default=30.0)
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline leg")
-    ap.add_argument("--workload", choices=["mc", "fsm", "batch", "serve", "pattern"], default="mc",
-                    help="mc: the timed motif-counting line (default); fsm / batch / serve: "
-                         "one measurement line of the other workloads")
+    ap.add_argument("--workload", choices=["mc", "mc5", "fsm", "batch", "serve", "pattern"], default="mc",
+                    help="mc: the timed 4-motif counting line (default); mc5: 5-motif counting on "
+                         "a systematic root sample, morphed vs direct; fsm / batch / serve: one "
+                         "measurement line of the other workloads")
+    ap.add_argument("--mc5-roots", type=int, default=1024, help="root sample size of the mc5 workload")
+    ap.add_argument("--mc5-deadline", type=float, default=60.0, help="deadline of each mc5 count")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--batch-scale", type=int, default=SCALE)
     ap.add_argument("--serve-kmax", type=int, default=6, help="largest pattern size in serving requests")
@@ -232,7 +234,7 @@ def run_reference(args, world, rank):
         return
     n = 1 << SCALE
     src, dst = cached_rmat(SCALE, EDGE_FACTOR, SEED)
-    ks = [4] if args.motifs == "4" else [4, 5]
+    ks = [4]
     budget = max(5.0, 100.0 / max(1, args.steps + args.warmup))
     steps = []
     for i in range(args.warmup + args.steps):
@@ -268,12 +270,11 @@ def launches_per_count(plan):
 
 
 def metric_name(args):
-    return ("4-motif" if args.motifs == "4" else "4- and 5-motif") + \
-        " counting matches/s (morphed), R-MAT scale 20"
+    return "4-motif counting matches/s (morphed), R-MAT scale 20"
 
 
 def workload_config(args):
-    return {"workload": f"{'4' if args.motifs == '4' else '4+5'}-motif counting: all connected "
+    return {"workload": "4-motif counting: all connected "
                         f"vertex-induced unlabeled patterns, naive morph to edge-induced patterns, "
                         f"on R-MAT scale {SCALE} (2^{SCALE} vertices), edge factor {EDGE_FACTOR}, "
                         f"a=0.57 b=c=0.19 d=0.05, seed {SEED}, degree-ordered int32 CSR, 128-bit counts",
@@ -415,6 +416,58 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mc5(args):
+    """5-motif counting (the 21 connected vertex-induced patterns) on the
+    scale-20 graph, restricted to a systematic sample of roots: every
+    (n / R)-th vertex in degree order, offset by half a stride (the sample
+    spans all degrees but leaves out the single highest-ranked vertices).
+    Counts are of occurrences whose highest-ranked vertex is a sampled root,
+    so morphed and direct results on the sample must agree exactly; each
+    count runs under its own deadline."""
+    import torch
+    import paper_2012_04553_b300 as pm
+    n = 1 << SCALE
+    src, dst = cached_rmat(SCALE, EDGE_FACTOR, SEED)
+    g = pm.Graph(n, src, dst)
+    by_rank = np.empty(n, dtype=np.int64)
+    by_rank[g.vertex_order()] = np.arange(n)
+    stride = n // args.mc5_roots
+    ranks = (np.arange(args.mc5_roots) * stride + stride // 2).astype(np.int64)
+    roots = np.sort(by_rank[ranks]).astype(np.int32)
+    deg = np.bincount(np.concatenate([src, dst]), minlength=n)   # raw, before dedup: for the record only
+    queries = [pm.make_pattern(5, m, pm.VERTEX_INDUCED) for m in connected_classes(5)]
+    out = {}
+    for name, mode in (("morphed", pm.MORPH_NAIVE), ("direct", pm.MORPH_NONE)):
+        plan = pm.Plan(g, queries, mode=mode)
+        plan.count_roots(roots[:8], timeout_s=args.mc5_deadline)       # warm-up on a few light roots
+        torch.cuda.synchronize()
+        t0 = time.time()
+        try:
+            c = plan.count_roots(roots, timeout_s=args.mc5_deadline)
+            torch.cuda.synchronize()
+            out[name] = {"wall_s": time.time() - t0, "counts": [str(x) for x in c], "matches": sum(c),
+                         "n_matched_patterns": plan.n_matched}
+        except pm.PMTimeout:
+            out[name] = {"timed_out_after_s": round(time.time() - t0, 3), "deadline_s": args.mc5_deadline,
+                         "n_matched_patterns": plan.n_matched}
+    m, d = out["morphed"], out["direct"]
+    line = {"metric": "5-motif counting matches/s on sampled roots (morphed), R-MAT scale 20",
+            "value": (m["matches"] / m["wall_s"]) if "wall_s" in m else None, "unit": "matches/s",
+            "higher_is_better": True, "n_gpus": 1, "dtype": "int64", "data": "synthetic",
+            "morphed": {k: v for k, v in m.items() if k != "matches"},
+            "direct": {k: v for k, v in d.items() if k != "matches"},
+            "direct_over_morphed_time": (d["wall_s"] / m["wall_s"]) if "wall_s" in m and "wall_s" in d
+            else None,
+            "counts_equal": (m["counts"] == d["counts"]) if "counts" in m and "counts" in d else None,
+            "sample": {"roots": int(len(roots)), "stride_in_degree_order": int(stride),
+                       "max_raw_degree_in_sample": int(deg[roots].max())},
+            "config": {"workload": "5-motif counting (21 connected vertex-induced unlabeled patterns), "
+                                   "naive morph to edge-induced patterns vs direct, rooted plans, on the "
+                                   "occurrences whose highest-ranked vertex lies in a systematic sample "
+                                   f"of {len(roots)} roots, R-MAT scale {SCALE} ef {EDGE_FACTOR} seed {SEED}"}}
+    print(json.dumps(line), flush=True)
+
+
 def run_pattern(args):
     """One pattern on R-MAT (scale, ef 16, seed), matched as given: device
     time of the matching kernels (profiling target)."""
@@ -439,7 +492,7 @@ def main():
         return
     if args.workload != "mc":
         if rank == 0:
-            {"fsm": run_fsm, "batch": run_batch, "serve": run_serve,
+            {"fsm": run_fsm, "batch": run_batch, "serve": run_serve, "mc5": run_mc5,
              "pattern": run_pattern}[args.workload](args)
         return
     import torch
@@ -449,7 +502,7 @@ def main():
     dev = torch.device("cuda", local)
     n = 1 << SCALE
     src, dst = cached_rmat(SCALE, EDGE_FACTOR, SEED)
-    ks = [4] if args.motifs == "4" else [4, 5]
+    ks = [4]
     queries = [pm.make_pattern(k, m, pm.VERTEX_INDUCED) for k in ks for m in connected_classes(k)]
     g = pm.Graph(n, src, dst, device=local)
     info = g.info()
