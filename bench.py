@@ -259,14 +259,14 @@ def launches_per_count(plan):
     """Library kernels one pm_count launches (per-pattern launch mode): the
     arming kernel; per matched pattern run by set operations, the two
     matching passes and the piece scan (plus a counter reset before every
-    pattern but the first); one wedge kernel for a 4-cycle run with its
-    rooted plan."""
+    pattern but the first); one wedge or clique kernel for a 4-cycle or a
+    clique run with its rooted plan."""
     import paper_2012_04553_b300 as pm
     fam = plan.autotune()            # the cached per-pattern decisions
     rooted = plan.export_plans(pm.PLANS_ROOTED)
-    wedge = sum(1 for r in rooted if r["kind"] == 1 and fam[int(r["counter"])] == pm.PLANS_ROOTED)
-    setops = plan.n_matched - wedge
-    return 1 + 3 * setops + max(0, setops - 1) + wedge
+    special = sum(1 for r in rooted if r["kind"] != 0 and fam[int(r["counter"])] == pm.PLANS_ROOTED)
+    setops = plan.n_matched - special
+    return 1 + 3 * setops + max(0, setops - 1) + special
 
 
 def metric_name(args):

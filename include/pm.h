@@ -183,7 +183,7 @@ pm_status pm_plan_autotune(pm_query_plan *p, void *stream, int32_t *families);
 /* Copy the compiled plans of one family (PM_PLANS_ROOTED: n_kernels_plans
  * records; PM_PLANS_FREE: n_matched records) into out (cap bytes).  A record
  * is 112 bytes: int32 k, n_enum, tail, closed, counter, dom_base, n_columns,
- * split, task_space, kind (0 set operations, 1 wedge pairs), pair (1: the
+ * split, task_space, kind (0 set operations, 1 wedge pairs, 2 clique), pair (1: the
  * last two levels are an independent pair counted as |A||B| - |A n B|, with
  * the merged constraints of A n B in level k), int32 pad;
  * then 8 levels of uint8 isect, diff, lt,

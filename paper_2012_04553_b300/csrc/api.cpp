@@ -113,7 +113,10 @@ struct pm_query_plan {
     uint8_t *d_timed_out = nullptr;          // pm_count_each: expired matched patterns
     uint32_t *d_wedge = nullptr;             // wedge-kernel counters: blocks x n, kept zero
     int wedge_nblocks = 0;
-    size_t bytes_counters = 0, bytes_bitsets = 0, bytes_cols = 0, bytes_wedge = 0;
+    int32_t *d_spill = nullptr;              // clique-kernel spill sets (per warp)
+    int64_t spill_len = 0;
+    size_t bytes_counters = 0, bytes_bitsets = 0, bytes_cols = 0, bytes_wedge = 0, bytes_spill = 0;
+    bool spill_ready = false;
     bool device_ready = false;
     // CUDA graph of a whole pm_count (pm_plan_capture): replayed by pm_count
     cudaGraphExec_t graph_exec = nullptr;
@@ -219,6 +222,10 @@ void free_plan_device(pm_query_plan *p) {
     dev_free(p->d_wedge, p->bytes_wedge, dev);
     p->d_wedge = nullptr;
     p->bytes_wedge = 0;
+    dev_free(p->d_spill, p->bytes_spill, dev);
+    p->d_spill = nullptr;
+    p->bytes_spill = 0;
+    p->spill_ready = false;
     dev_free(p->d_defer, sizeof(Deferred) * std::max<uint32_t>(p->defer_cap, 1), dev);
     dev_free(p->d_piece_off, sizeof(uint32_t) * std::max<uint32_t>(p->defer_cap, 1), dev);
     p->d_counters = nullptr;
@@ -374,6 +381,25 @@ pm_status ensure_wedge(pm_query_plan *p, cudaStream_t s) {
     return e ? cuda_fail("wedge counters", e) : PM_OK;
 }
 
+// Spill sets of the clique kernel, sized by the graph's largest degree
+// (none when every set fits the kernel's shared buffers).
+pm_status ensure_clique(pm_query_plan *p) {
+    if (p->spill_ready) return PM_OK;
+    const pm_graph *g = p->g;
+    p->spill_len = clique_spill_len(g->max_degree);
+    if (p->spill_len > 0) {
+        p->bytes_spill = sizeof(int32_t) * 2 * size_t(p->spill_len) * size_t(clique_warps(g->device));
+        p->d_spill = (int32_t *)dev_alloc(p->bytes_spill, g->device);
+        if (!p->d_spill) {
+            p->bytes_spill = 0;
+            set_error("device allocation failed (clique spill sets)");
+            return PM_ENOMEM;
+        }
+    }
+    p->spill_ready = true;
+    return PM_OK;
+}
+
 // Launch both matching passes for one plan table on the given tasks.
 // gate_budget_ns > 0 (with gate_flags): every matched pattern gets its own
 // deadline and its expiry is flagged per pattern (pm_count_each).
@@ -431,18 +457,24 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
     }
     int last = n_setops > 0 ? t.plans[n_setops - 1].counter : -1;
     for (size_t i = size_t(n_setops); i < t.plans.size(); i++) {
+        const DevPlan &dp = t.plans[i];
         if (domains) {
-            set_error("wedge-pair plans count only");
+            set_error("wedge-pair and clique plans count only");
             return PM_EINVAL;
         }
-        pm_status st = ensure_wedge(p, s);
+        pm_status st = dp.kind == PLAN_WEDGE_PAIRS ? ensure_wedge(p, s) : ensure_clique(p);
         if (st != PM_OK) return st;
         if (gate_flags && launch_pattern_gate(p->d_ctl, gate_flags, last, gate_budget_ns, s))
             return PM_ECUDA;
-        if (launch_wedge_pairs(L.g, tasks, t.plans[i].counter, p->d_counters, p->d_wedge,
-                               p->wedge_nblocks, sample_stride, p->d_ctl, s))
+        if (dp.kind == PLAN_WEDGE_PAIRS) {
+            if (launch_wedge_pairs(L.g, tasks, dp.counter, p->d_counters, p->d_wedge,
+                                   p->wedge_nblocks, sample_stride, p->d_ctl, s))
+                return PM_ECUDA;
+        } else if (launch_clique(L.g, tasks, dp.k, dp.counter, p->d_counters, p->d_spill,
+                                 p->spill_len, sample_stride, p->d_ctl, stats, s)) {
             return PM_ECUDA;
-        last = t.plans[i].counter;
+        }
+        last = dp.counter;
     }
     if (gate_flags && last >= 0 && launch_pattern_gate(p->d_ctl, gate_flags, last, 0, s))
         return PM_ECUDA;
@@ -523,11 +555,12 @@ pm_status prepare_active(pm_query_plan *p, cudaStream_t s) {
     const size_t nm = p->morph.matched.size();
     std::vector<int> want(nm);
     if (p->forced == PM_PLANS_QUICK) {
-        // no timing: the rooted family where it runs the wedge kernel, else free
+        // no timing: the rooted family where it runs the wedge or clique
+        // kernel, else free
         for (size_t j = 0; j < nm; j++) {
-            const bool wedge = p->rooted_begin[j + 1] - p->rooted_begin[j] == 1 &&
-                               p->rooted[p->rooted_begin[j]].kind == PLAN_WEDGE_PAIRS;
-            want[j] = wedge ? PM_PLANS_ROOTED : PM_PLANS_FREE;
+            const bool special = p->rooted_begin[j + 1] - p->rooted_begin[j] == 1 &&
+                                 p->rooted[p->rooted_begin[j]].kind != PLAN_SETOPS;
+            want[j] = special ? PM_PLANS_ROOTED : PM_PLANS_FREE;
         }
     } else if (p->forced >= 0) {
         std::fill(want.begin(), want.end(), p->forced);
@@ -1000,10 +1033,17 @@ pm_status pm_plan_capture(pm_query_plan *p, void *stream, double timeout_s) {
     pm_status st = ensure_device(p);
     if (st == PM_OK) st = prepare_active(p, user);
     if (st != PM_OK) return st;
-    bool needs_wedge = false;
-    for (const DevPlan &dp : p->active.plans) needs_wedge |= dp.kind == PLAN_WEDGE_PAIRS;
+    bool needs_wedge = false, needs_clique = false;
+    for (const DevPlan &dp : p->active.plans) {
+        needs_wedge |= dp.kind == PLAN_WEDGE_PAIRS;
+        needs_clique |= dp.kind == PLAN_CLIQUE;
+    }
     if (needs_wedge) {
         st = ensure_wedge(p, user);
+        if (st != PM_OK) return st;
+    }
+    if (needs_clique) {
+        st = ensure_clique(p);
         if (st != PM_OK) return st;
     }
     const size_t nm = p->morph.matched.size();

@@ -118,6 +118,16 @@ int wedge_blocks(int device);
 int launch_wedge_pairs(const DevGraph &g, const DevTasks &tasks, int counter, uint64_t *counters,
                        uint32_t *scratch, int blocks, int sample_stride, Control *ctl,
                        void *stream);
+// Clique kernel (clique.cu) for one PLAN_CLIQUE plan (k = 4 or 5) over the
+// lower task space of `tasks`.  spill: clique_warps(device) * 2 * spill_len
+// int32 entries, where spill_len = clique_spill_len(max degree); nullptr is
+// allowed only when that length is 0.  stats (nullable): add the algorithmic
+// bytes read.
+int64_t clique_warps(int device);
+int64_t clique_spill_len(int64_t max_degree);
+int launch_clique(const DevGraph &g, const DevTasks &tasks, int k, int counter,
+                  uint64_t *counters, int32_t *spill, int64_t spill_len, int sample_stride,
+                  Control *ctl, unsigned long long *stats, void *stream);
 int launch_mni_reduce(const uint32_t *d_bitsets, int64_t words_per_bitset, const int32_t *d_src_off,
                       const int32_t *d_src, int n_columns, unsigned long long *d_popc,
                       void *stream);

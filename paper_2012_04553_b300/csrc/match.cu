@@ -34,45 +34,13 @@
 #include <climits>
 #include <cstdio>
 
+#include "devgraph.cuh"
 #include "internal.hpp"
 
 namespace pm {
 
-typedef unsigned __int128 u128;
-
-constexpr unsigned FULL = 0xffffffffu;
 constexpr int CAP = 64;       // prefixes per level buffer
 constexpr int WARPS = 4;      // warps per block
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// First index in a[0, len) whose value is >= key.
-__device__ __forceinline__ int32_t lower_bound_dev(const int32_t *__restrict__ a, int32_t len,
-                                                   int32_t key) {
-    int32_t lo = 0, hi = len;
-    while (lo < hi) {
-        const int32_t mid = int32_t((uint32_t(lo) + uint32_t(hi)) >> 1);
-        if (__ldg(a + mid) < key) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ bool contains(const DevGraph &g, int32_t v, int32_t x) {
-    if (g.hub) {
-        const int32_t h = __ldg(g.hub + v);
-        if (h >= 0) return (__ldg(g.bits + int64_t(h) * g.words + (x >> 5)) >> (x & 31)) & 1u;
-    }
-    const int64_t b = __ldg(g.rowptr + v);
-    const int32_t len = int32_t(__ldg(g.rowptr + v + 1) - b);
-    const int32_t *a = g.col + b;
-    const int32_t p = lower_bound_dev(a, len, x);
-    return p < len && __ldg(a + p) == x;
-}
 
 // Bound vertices of levels 0..L in registers; every access uses a
 // compile-time index (unrolled loops) so the array never leaves registers.
@@ -432,14 +400,6 @@ __device__ __forceinline__ u128 shfl_xor_u128(u128 v, int mask) {
     const uint64_t lo = __shfl_xor_sync(FULL, uint64_t(v), mask);
     const uint64_t hi = __shfl_xor_sync(FULL, uint64_t(v >> 64), mask);
     return (u128(hi) << 64) | lo;
-}
-
-__device__ __forceinline__ void add_u128(uint64_t *counter, u128 v) {
-    const unsigned long long lo = (unsigned long long)(uint64_t)v;
-    unsigned long long hi = (unsigned long long)(uint64_t)(v >> 64);
-    const unsigned long long old = atomicAdd((unsigned long long *)counter, lo);
-    if (old + lo < old) hi += 1;
-    if (hi) atomicAdd((unsigned long long *)counter + 1, hi);
 }
 
 struct KernelArgs {

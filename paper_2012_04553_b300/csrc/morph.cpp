@@ -447,6 +447,9 @@ std::vector<DevPlan> compile_plans(const Pat &p, int counter, int dom_base,
     // levels still describe the same occurrences: root, two lower neighbours
     // and the opposite vertex)
     if (counting && is_plain_c4(p) && plans.size() == 1) plans[0].kind = PLAN_WEDGE_PAIRS;
+    // the unlabeled 4- and 5-clique's single rooted plan runs in the clique kernel
+    if (counting && (p.k == 4 || p.k == 5) && p.is_clique() && !p.labeled() && plans.size() == 1)
+        plans[0].kind = PLAN_CLIQUE;
     return plans;
 }
 

@@ -65,8 +65,13 @@ enum TaskSpace : int32_t {
 // root a and each opposite vertex c < a, the occurrences with a as highest-
 // ranked vertex are C(w, 2) with w = |N(a) n N(c) n [0, a)|; counting the
 // 2-paths a-b-c into per-c counters and adding each counter's old value
-// gives that sum, since C(w, 2) = 0 + 1 + ... + (w - 1).
-enum PlanKind : int32_t { PLAN_SETOPS = 0, PLAN_WEDGE_PAIRS = 1 };
+// gives that sum, since C(w, 2) = 0 + 1 + ... + (w - 1).  The rooted plan of
+// the unlabeled 4- or 5-clique runs in a clique kernel: for the root a and
+// each lower neighbour b, the occurrences with a highest-ranked and b second
+// are the (k-2)-cliques inside S = N(a) n N(b) n [0, b), counted on S once
+// it is materialised.  In both cases the plan's levels still describe the
+// same occurrences.
+enum PlanKind : int32_t { PLAN_SETOPS = 0, PLAN_WEDGE_PAIRS = 1, PLAN_CLIQUE = 2 };
 
 struct DevPlan {
     int32_t k;

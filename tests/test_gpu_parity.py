@@ -78,6 +78,56 @@ def test_hub_bitmaps_against_oracle(monkeypatch):
                 assert plan.count() == want_v, (k, mode, family)
 
 
+def two_hub_graph():
+    """R-MAT scale 11 (ef 8, seed 119) plus a dense 40-vertex block and two
+    adjacent hubs joined to 1,400 common vertices: the hubs' task has more
+    common lower neighbours than the clique kernel's shared buffers hold, so
+    its sets spill to global memory."""
+    n = 2048
+    s, d = rmat_edges(11, 8, seed=119)
+    a, b = 2046, 2047
+    extra_s, extra_d = [a], [b]
+    for v in range(1400):
+        extra_s += [a, b]
+        extra_d += [v, v]
+    dense = uniform_ints(120, 1, 40 * 40, 0, 2)
+    for i in range(40):
+        for j in range(i + 1, 40):
+            if dense[i * 40 + j]:
+                extra_s.append(500 + i)
+                extra_d.append(500 + j)
+    s = np.concatenate([s, np.array(extra_s, dtype=s.dtype)])
+    d = np.concatenate([d, np.array(extra_d, dtype=d.dtype)])
+    return n, s, d
+
+
+def test_clique_kernel_against_oracle():
+    """4- and 5-cliques through the clique kernel (rooted family) and the
+    set-operation kernel (free family), whole graph and a root subset, with
+    the spill path exercised by two hubs of degree > 1,024."""
+    n, s, d = two_hub_graph()
+    og = oracle.prepare_graph(n, s, d)
+    g = load(n, s, d)
+    assert g.info()["max_degree"] > 1024
+    qs = [pm.make_pattern(4, 63), pm.make_pattern(5, 1023), pm.make_pattern(5, 1023, pm.VERTEX_INDUCED)]
+    want = [oracle.count(og, algebra.Pattern.from_mask(4, 63)),
+            oracle.count(og, algebra.Pattern.from_mask(5, 1023)),
+            oracle.count(og, algebra.Pattern.from_mask(5, 1023, None, True))]
+    assert want[0] > 0 and want[1] > 0
+    for family in (pm.PLANS_ROOTED, pm.PLANS_FREE, pm.PLANS_AUTO):
+        plan = pm.Plan(g, qs, mode=pm.MORPH_NONE)
+        plan.select(family)
+        assert plan.count() == want, family
+    plan = pm.Plan(g, qs, mode=pm.MORPH_NONE)
+    assert [r["kind"] for r in plan.export_plans(pm.PLANS_ROOTED)] == [2, 2]
+    plan.select(pm.PLANS_ROOTED)
+    counts, alg = plan.count_instrumented()
+    assert counts == want and alg > 0
+    roots = np.concatenate([np.arange(0, n, 7), [2046, 2047]]).astype(np.int32)
+    assert plan.count_roots(roots) == [oracle.count(og, algebra.Pattern.from_mask(k, m), roots=roots)
+                                       for k, m in ((4, 63), (5, 1023), (5, 1023))]
+
+
 def test_six_vertex_patterns_against_oracle():
     s, d = rmat_edges(7, 5, seed=104)
     og = oracle.prepare_graph(128, s, d)

@@ -157,3 +157,21 @@ def test_morph_is_modulo_2_128():
     big = [(1 << 127) + 12345] * plan.n_matched
     out = plan.morph(big)
     assert all(0 <= x < (1 << 128) for x in out)
+
+
+def test_special_plan_kinds():
+    # counting: the 4-cycle's rooted plan runs the wedge kernel, the 4- and
+    # 5-clique's the clique kernel; MNI support keeps set-operation plans
+    qs = [pm.make_pattern(4, 30), pm.make_pattern(4, 63), pm.make_pattern(5, 1023),
+          pm.make_pattern(6, (1 << 15) - 1), pm.make_pattern(4, 31)]
+    plan = pm.Plan(None, qs, mode=pm.MORPH_NONE)
+    matched = plan.matched_patterns()
+    kinds = {}
+    for r in plan.export_plans(pm.PLANS_ROOTED):
+        k, m = matched[int(r["counter"])][:2]
+        kinds.setdefault((k, m), set()).add(int(r["kind"]))
+    kinds = {key: v.pop() if len(v) == 1 else v for key, v in kinds.items()}
+    assert kinds == {(4, 30): 1, (4, 63): 2, (5, 1023): 2, (6, (1 << 15) - 1): 0, (4, 31): 0}
+    assert all(int(r["kind"]) == 0 for r in plan.export_plans(pm.PLANS_FREE))
+    sup = pm.Plan(None, qs[:3], op=pm.OP_SUPPORT, mode=pm.MORPH_NONE)
+    assert all(int(r["kind"]) == 0 for r in sup.export_plans(pm.PLANS_ROOTED))
