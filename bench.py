@@ -255,7 +255,7 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def launches_per_count(plan):
+def launches_per_count(plan, n):
     """Library kernels one pm_count launches (per-pattern launch mode): the
     arming kernel; per matched pattern run by set operations, the two
     matching passes and the piece scan (plus a counter reset before every
@@ -264,9 +264,13 @@ def launches_per_count(plan):
     import paper_2012_04553_b300 as pm
     fam = plan.autotune()            # the cached per-pattern decisions
     rooted = plan.export_plans(pm.PLANS_ROOTED)
-    special = sum(1 for r in rooted if r["kind"] != 0 and fam[int(r["counter"])] == pm.PLANS_ROOTED)
-    setops = plan.n_matched - special
-    return 1 + 3 * setops + max(0, setops - 1) + special
+    chosen = [int(r["kind"]) for r in rooted if r["kind"] != 0 and fam[int(r["counter"])] == pm.PLANS_ROOTED]
+    # the wedge plan launches a heavy-root kernel (top H ranks) and, when
+    # n > H, a light-root kernel
+    heavy = int(os.environ.get("PM_WEDGE_HEAVY", "16384"))
+    wedge = int(heavy > 0) + int(n > heavy)
+    setops = plan.n_matched - len(chosen)
+    return 1 + 3 * setops + max(0, setops - 1) + sum(wedge if k == 1 else 1 for k in chosen)
 
 
 def metric_name(args):
@@ -590,7 +594,7 @@ def main():
                      "algorithmic_bytes_per_launch": alg_bytes},
         "e2e": {"value": total_matches / e2e_s, "unit": "matches/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "wall_s": e2e_s},
-        "gpu_launches": args.steps * launches_per_count(plan0),
+        "gpu_launches": args.steps * launches_per_count(plan0, n),
         "clocks": clocks,
         "graph": {"n": info["n"], "m": info["m"], "max_degree": info["max_degree"]},
     }

@@ -2,6 +2,7 @@
 // the plan-family autotuner, launches and the host half of the morph
 // transform.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstddef>
 #include <cstring>
@@ -113,6 +114,10 @@ struct pm_query_plan {
     uint8_t *d_timed_out = nullptr;          // pm_count_each: expired matched patterns
     uint32_t *d_wedge = nullptr;             // wedge-kernel counters: blocks x n, kept zero
     int wedge_nblocks = 0;
+    uint2 *d_lists = nullptr;                // heavy-root wedge kernel: entry lists
+    int64_t list_cap = 0, heavy_from = 0;
+    size_t bytes_lists = 0;
+    bool wedge_ready = false;
     int32_t *d_spill = nullptr;              // clique-kernel spill sets (per warp)
     int64_t spill_len = 0;
     size_t bytes_counters = 0, bytes_bitsets = 0, bytes_cols = 0, bytes_wedge = 0, bytes_spill = 0;
@@ -222,6 +227,10 @@ void free_plan_device(pm_query_plan *p) {
     dev_free(p->d_wedge, p->bytes_wedge, dev);
     p->d_wedge = nullptr;
     p->bytes_wedge = 0;
+    dev_free(p->d_lists, p->bytes_lists, dev);
+    p->d_lists = nullptr;
+    p->bytes_lists = 0;
+    p->wedge_ready = false;
     dev_free(p->d_spill, p->bytes_spill, dev);
     p->d_spill = nullptr;
     p->bytes_spill = 0;
@@ -365,20 +374,43 @@ int64_t echunks_for(const std::vector<DevPlan> &plans, const DevTasks &t) {
     return (most + 31) / 32;
 }
 
-// Counters of the wedge kernel (zeroed once; the kernel leaves them zero).
+// Scratch of the wedge kernels: entry lists of the heavy-root kernel (two
+// per block, largest degree each) and, when some roots are light, the light
+// kernel's dense per-block counters (zeroed once; the kernel leaves them
+// zero).  Roots of rank >= n - H are heavy, H = PM_WEDGE_HEAVY (default
+// 16384; rows are addressed with 32-bit cursors, so a graph with 2^32 or
+// more adjacency entries has no heavy roots).
 pm_status ensure_wedge(pm_query_plan *p, cudaStream_t s) {
-    if (p->d_wedge) return PM_OK;
+    if (p->wedge_ready) return PM_OK;
     const pm_graph *g = p->g;
     p->wedge_nblocks = wedge_blocks(g->device);
-    p->bytes_wedge = sizeof(uint32_t) * size_t(g->n) * size_t(p->wedge_nblocks);
-    p->d_wedge = (uint32_t *)dev_alloc(p->bytes_wedge, g->device);
-    if (!p->d_wedge) {
-        p->bytes_wedge = 0;
-        set_error("device allocation failed (wedge counters)");
-        return PM_ENOMEM;
+    int64_t heavy = 16384;
+    if (const char *env = std::getenv("PM_WEDGE_HEAVY")) heavy = std::max<int64_t>(0, std::atoll(env));
+    if (2 * g->m >= (int64_t(1) << 32)) heavy = 0;
+    p->heavy_from = std::max<int64_t>(0, g->n - heavy);
+    p->list_cap = std::max<int64_t>(1, g->max_degree);
+    if (p->heavy_from < g->n) {
+        p->bytes_lists = sizeof(uint2) * 2 * size_t(p->list_cap) * size_t(p->wedge_nblocks);
+        p->d_lists = (uint2 *)dev_alloc(p->bytes_lists, g->device);
+        if (!p->d_lists) {
+            p->bytes_lists = 0;
+            set_error("device allocation failed (wedge entry lists)");
+            return PM_ENOMEM;
+        }
     }
-    cudaError_t e = cudaMemsetAsync(p->d_wedge, 0, p->bytes_wedge, s);
-    return e ? cuda_fail("wedge counters", e) : PM_OK;
+    if (p->heavy_from > 0) {
+        p->bytes_wedge = sizeof(uint32_t) * size_t(g->n) * size_t(p->wedge_nblocks);
+        p->d_wedge = (uint32_t *)dev_alloc(p->bytes_wedge, g->device);
+        if (!p->d_wedge) {
+            p->bytes_wedge = 0;
+            set_error("device allocation failed (wedge counters)");
+            return PM_ENOMEM;
+        }
+        cudaError_t e = cudaMemsetAsync(p->d_wedge, 0, p->bytes_wedge, s);
+        if (e) return cuda_fail("wedge counters", e);
+    }
+    p->wedge_ready = true;
+    return PM_OK;
 }
 
 // Spill sets of the clique kernel, sized by the graph's largest degree
@@ -467,8 +499,9 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
         if (gate_flags && launch_pattern_gate(p->d_ctl, gate_flags, last, gate_budget_ns, s))
             return PM_ECUDA;
         if (dp.kind == PLAN_WEDGE_PAIRS) {
-            if (launch_wedge_pairs(L.g, tasks, dp.counter, p->d_counters, p->d_wedge,
-                                   p->wedge_nblocks, sample_stride, p->d_ctl, s))
+            if (launch_wedge_pairs(L.g, tasks, p->heavy_from, dp.counter, p->d_counters, p->d_wedge,
+                                   p->d_lists, p->list_cap, p->wedge_nblocks, sample_stride,
+                                   p->d_ctl, s))
                 return PM_ECUDA;
         } else if (launch_clique(L.g, tasks, dp.k, dp.counter, p->d_counters, p->d_spill,
                                  p->spill_len, sample_stride, p->d_ctl, stats, s)) {
@@ -757,6 +790,35 @@ pm_status run_count_each(pm_query_plan *p, void *stream, double timeout_s, doubl
 }
 
 }  // namespace
+
+// Validates a query set and returns the size of its alternative set under
+// `mode` (morph selection only, no plan compilation): the serving loop's
+// per-request count of matched patterns, for its deduplication statistic.
+namespace pm {
+pm_status matched_set_size(const pm_graph *g, const pm_pattern *queries, int32_t nq,
+                           pm_morph_mode mode, int32_t *n_matched) {
+    if (!queries || nq < 1 || !n_matched) {
+        set_error("matched_set_size: null argument or empty query set");
+        return PM_EINVAL;
+    }
+    std::vector<Pat> pats(nq);
+    for (int32_t i = 0; i < nq; i++) {
+        pm_status st = to_pat(queries[i], g ? g->labeled : true, &pats[i]);
+        if (st != PM_OK) return st;
+    }
+    MorphPlan mp;
+    std::string why;
+    // cost-based selection needs device timings; the naive set stands in
+    const pm_morph_mode m = mode == PM_MORPH_COST ? PM_MORPH_NAIVE : mode;
+    pm_status st = morph_select(pats, PM_OP_COUNT, m, mp, &why, nullptr);
+    if (st != PM_OK) {
+        set_error("matched_set_size: " + why);
+        return st;
+    }
+    *n_matched = int32_t(mp.matched.size());
+    return PM_OK;
+}
+}  // namespace pm
 
 extern "C" {
 

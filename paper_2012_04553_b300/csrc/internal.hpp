@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <vector_types.h>
+
 #include "../../include/pm.h"
 #include "pattern.hpp"
 #include "plan.hpp"
@@ -67,6 +69,10 @@ pm_status morph_select(const std::vector<Pat> &queries, pm_op op, pm_morph_mode 
                        MorphPlan &out, std::string *why,
                        const std::function<double(const Pat &)> *cost = nullptr);
 
+// Size of the alternative set of a query set (morph selection only).
+pm_status matched_set_size(const pm_graph *g, const pm_pattern *queries, int32_t nq,
+                           pm_morph_mode mode, int32_t *n_matched);
+
 // Rooted matching plans of one pattern (one per automorphism orbit).
 // counting: the plans serve pm_count (a 4-cycle may then use the wedge kernel).
 std::vector<DevPlan> compile_plans(const Pat &p, int counter, int dom_base,
@@ -112,12 +118,15 @@ struct MatchLaunch {
 };
 int launch_count(const MatchLaunch &L, void *stream);
 int launch_domains(const MatchLaunch &L, void *stream);
-// Wedge-pair kernel for one PLAN_WEDGE_PAIRS plan over the lower task space
-// of `tasks`; scratch: blocks * n uint32 counters, zero on entry and exit.
+// Wedge-pair kernels for one PLAN_WEDGE_PAIRS plan over the lower task space
+// of `tasks`: roots a >= heavy_from by the shared-memory heavy-root kernel
+// (lists: blocks * 2 * list_cap (cursor, end) pairs, list_cap >= the largest
+// degree), the others with dense counters in scratch (blocks * n uint32,
+// zero on entry and exit; unused when heavy_from == 0).
 int wedge_blocks(int device);
-int launch_wedge_pairs(const DevGraph &g, const DevTasks &tasks, int counter, uint64_t *counters,
-                       uint32_t *scratch, int blocks, int sample_stride, Control *ctl,
-                       void *stream);
+int launch_wedge_pairs(const DevGraph &g, const DevTasks &tasks, int64_t heavy_from, int counter,
+                       uint64_t *counters, uint32_t *scratch, uint2 *lists, int64_t list_cap,
+                       int blocks, int sample_stride, Control *ctl, void *stream);
 // Clique kernel (clique.cu) for one PLAN_CLIQUE plan (k = 4 or 5) over the
 // lower task space of `tasks`.  spill: clique_warps(device) * 2 * spill_len
 // int32 entries, where spill_len = clique_spill_len(max degree); nullptr is

@@ -694,16 +694,31 @@ int device_sm_count(int device) {
     return sms;
 }
 
-// Wedge-pair counting for the edge-induced 4-cycle (see PlanKind): one block
-// per root a, highest-ranked first; warps take lower neighbours b of a, lanes
-// the neighbours c < a of b; atomicAdd on the block's dense per-c counters
-// returns the old value, whose running sum is sum_c C(w_c, 2); a second walk
-// over the same 2-paths resets the touched counters to zero.
+// Wedge-pair counting for the edge-induced 4-cycle (see PlanKind).  For the
+// root a and every 2-path a-b-c with b, c < a, an atomicAdd on a per-c
+// counter returns the old value, whose running sum is sum_c C(w_c, 2).
+// Roots split by rank: the 2-paths concentrate on the highest-ranked roots
+// (on R-MAT scale 20 the top 16,384 of 2^20 roots carry 99 % of them).
+//
+// Heavy roots (a >= heavy_from): one block per root keeps the counters in
+// shared memory for a window [w0, w0 + W) of c at a time.  Every lower
+// neighbour b with neighbours below a is an entry (cursor, end) into b's
+// row; a window consumes, warp by warp, each entry's run of c inside the
+// window (a prefix of what is left, rows being sorted), keeps unfinished
+// entries for the next window and starts that window at their smallest c,
+// so empty stretches of ids cost nothing and no counter touches DRAM.
+//
+// Light roots (a < heavy_from): one block per root with dense per-c
+// counters in global memory (blocks x n); warps take lower neighbours b,
+// lanes the neighbours c < a of b, and a second walk over the same 2-paths
+// resets the touched counters to zero.
 constexpr int WEDGE_THREADS = 512;
+constexpr int WH_THREADS = 1024;
+constexpr int WH_W = 53248;          // counters per window (208 KiB of shared memory)
 
 __global__ void __launch_bounds__(WEDGE_THREADS)
-wedge_pairs_kernel(DevGraph g, DevTasks tasks, int counter, uint64_t *counters, uint32_t *scratch,
-                   int sample_stride, Control *ctl) {
+wedge_pairs_kernel(DevGraph g, DevTasks tasks, int64_t heavy_from, int counter, uint64_t *counters,
+                   uint32_t *scratch, int sample_stride, Control *ctl) {
     __shared__ unsigned long long s_root;
     __shared__ int s_stop;
     __shared__ unsigned long long s_acc[WEDGE_THREADS / 32];
@@ -729,6 +744,7 @@ wedge_pairs_kernel(DevGraph g, DevTasks tasks, int counter, uint64_t *counters, 
         __syncthreads();
         if (done) break;
         const int32_t a = tasks.roots ? __ldg(tasks.roots + r) : int32_t(g.n - 1 - r);
+        if (a >= heavy_from) continue;                 // counted by the heavy-root kernel
         const int32_t lo = int32_t(__ldg(tasks.off[0] + r + 1) - __ldg(tasks.off[0] + r));
         const int64_t abase = __ldg(g.rowptr + a);
         for (int pass = 0; pass < 2; pass++) {
@@ -757,15 +773,131 @@ wedge_pairs_kernel(DevGraph g, DevTasks tasks, int counter, uint64_t *counters, 
     }
 }
 
+// lists: per block two entry lists of list_cap (cursor, end) pairs, list_cap
+// >= the largest degree.
+__global__ void __launch_bounds__(WH_THREADS, 1)
+wedge_heavy_kernel(DevGraph g, DevTasks tasks, int64_t heavy_from, int counter,
+                   uint64_t *counters, uint2 *lists, int64_t list_cap, int sample_stride,
+                   Control *ctl) {
+    extern __shared__ uint32_t wh_cnt[];
+    __shared__ unsigned long long s_root;
+    __shared__ int s_stop;
+    __shared__ int s_n[2];
+    __shared__ int s_minc[2];
+    __shared__ unsigned long long s_acc[WH_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    uint2 *L[2] = {lists + size_t(blockIdx.x) * 2 * size_t(list_cap),
+                   lists + size_t(blockIdx.x) * 2 * size_t(list_cap) + list_cap};
+    const uint64_t deadline = *(volatile unsigned long long *)&ctl->deadline;
+    const int64_t stride = sample_stride > 1 ? sample_stride : 1;
+    const int64_t nr = (tasks.nroots + stride - 1) / stride;
+    unsigned long long acc = 0;
+    for (;;) {
+        if (tid == 0) {
+            s_root = atomicAdd(&ctl->work2, 1ull);
+            int stop = *(volatile int *)&ctl->status;
+            if (!stop && deadline && global_ns() > deadline) {
+                atomicExch(&ctl->status, 1);
+                stop = 1;
+            }
+            s_stop = stop;
+            s_n[0] = 0;
+            s_minc[0] = INT_MAX;
+        }
+        __syncthreads();
+        const int64_t r = int64_t(s_root) * stride;
+        const bool done = s_root >= (unsigned long long)nr || s_stop;
+        if (done) break;
+        // with the implicit root list the heavy roots are the first ones
+        if (!tasks.roots && g.n - 1 - r < heavy_from) break;
+        const int32_t a = tasks.roots ? __ldg(tasks.roots + r) : int32_t(g.n - 1 - r);
+        if (a < heavy_from) {
+            __syncthreads();
+            continue;
+        }
+        const int32_t lo = int32_t(__ldg(tasks.off[0] + r + 1) - __ldg(tasks.off[0] + r));
+        const int64_t abase = __ldg(g.rowptr + a);
+        for (int i = tid; i < lo; i += blockDim.x) {
+            const int32_t b = __ldg(g.col + abase + i);
+            const int64_t bb = __ldg(g.rowptr + b);
+            const int32_t bl = lower_bound_dev(g.col + bb, int32_t(__ldg(g.rowptr + b + 1) - bb), a);
+            if (bl > 0) {
+                const int slot = atomicAdd(&s_n[0], 1);
+                L[0][slot] = make_uint2(uint32_t(bb), uint32_t(bb + bl));
+                atomicMin(&s_minc[0], __ldg(g.col + bb));
+            }
+        }
+        __syncthreads();
+        int cur = 0;
+        int nact = s_n[0];
+        int64_t w0 = s_minc[0];
+        while (nact > 0) {
+            for (int j = tid; j < WH_W; j += blockDim.x) wh_cnt[j] = 0;
+            if (tid == 0) {
+                s_n[cur ^ 1] = 0;
+                s_minc[cur ^ 1] = INT_MAX;
+                int stop = *(volatile int *)&ctl->status;
+                if (!stop && deadline && global_ns() > deadline) {
+                    atomicExch(&ctl->status, 1);
+                    stop = 1;
+                }
+                s_stop = stop;
+            }
+            __syncthreads();
+            if (s_stop) break;
+            const int64_t w1 = w0 + WH_W;
+            for (int e = warp; e < nact; e += nwarps) {
+                const uint2 en = L[cur][e];
+                uint32_t p = en.x;
+                for (;;) {
+                    const uint32_t idx = p + uint32_t(lane);
+                    const int32_t c = idx < en.y ? __ldg(g.col + idx) : INT_MAX;
+                    const bool in = c < w1;              // the run inside the window is a prefix
+                    if (in) acc += atomicAdd(&wh_cnt[c - w0], 1u);
+                    const int k = __popc(__ballot_sync(FULL, in));
+                    p += uint32_t(k);
+                    if (k < 32 || p >= en.y) break;
+                }
+                if (lane == 0 && p < en.y) {
+                    const int slot = atomicAdd(&s_n[cur ^ 1], 1);
+                    L[cur ^ 1][slot] = make_uint2(p, en.y);
+                    atomicMin(&s_minc[cur ^ 1], __ldg(g.col + p));
+                }
+            }
+            __syncthreads();
+            nact = s_n[cur ^ 1];
+            w0 = s_minc[cur ^ 1];
+            cur ^= 1;
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL, acc, off);
+    if (lane == 0) s_acc[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        u128 total = 0;
+        for (int w = 0; w < nwarps; w++) total += s_acc[w];
+        if (total) add_u128(counters + 2 * int64_t(counter), total);
+    }
+}
+
 int wedge_blocks(int device) { return device_sm_count(device); }
 
-int launch_wedge_pairs(const DevGraph &g, const DevTasks &tasks, int counter, uint64_t *counters,
-                       uint32_t *scratch, int blocks, int sample_stride, Control *ctl,
-                       void *stream) {
+int launch_wedge_pairs(const DevGraph &g, const DevTasks &tasks, int64_t heavy_from, int counter,
+                       uint64_t *counters, uint32_t *scratch, uint2 *lists, int64_t list_cap,
+                       int blocks, int sample_stride, Control *ctl, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
+    const size_t smem = sizeof(uint32_t) * WH_W;
+    cudaFuncSetAttribute(wedge_heavy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaMemsetAsync(&ctl->work2, 0, sizeof(unsigned long long), s);
     cudaMemsetAsync(&ctl->work3, 0, sizeof(unsigned long long), s);
-    wedge_pairs_kernel<<<blocks, WEDGE_THREADS, 0, s>>>(g, tasks, counter, counters, scratch,
-                                                       sample_stride, ctl);
+    if (heavy_from < g.n)
+        wedge_heavy_kernel<<<blocks, WH_THREADS, smem, s>>>(g, tasks, heavy_from, counter, counters,
+                                                            lists, list_cap, sample_stride, ctl);
+    if (heavy_from > 0)
+        wedge_pairs_kernel<<<blocks, WEDGE_THREADS, 0, s>>>(g, tasks, heavy_from, counter, counters,
+                                                           scratch, sample_stride, ctl);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) {
         set_error(std::string("wedge kernel launch: ") + cudaGetErrorString(err));

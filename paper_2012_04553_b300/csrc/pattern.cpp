@@ -1,7 +1,7 @@
 // Pattern algebra (see pattern.hpp).  Automorphisms and embeddings are found
 // by backtracking over vertex images with adjacency, label and degree
-// pruning; canonical forms take the least (labels, edge mask) over all k!
-// relabelings (k <= 8).
+// pruning; canonical forms take the least (labels, edge mask) over the
+// relabelings that order vertices by an isomorphism invariant (k <= 8).
 #include "pattern.hpp"
 
 #include <algorithm>
@@ -76,21 +76,52 @@ static uint64_t pack_labels(const Pat &p) {
     return x;
 }
 
+// Vertex invariant for canonical labelling: label, then degree (higher
+// first), then the multiset of neighbour degrees.  Isomorphisms preserve it,
+// so taking the least (labels, mask) only over the relabelings that number
+// vertices in ascending invariant order (every order of equal-invariant
+// vertices tried) is still a class function, and it tries far fewer than k!
+// relabelings unless the pattern is vertex-transitive.
+static uint64_t vertex_invariant(const Pat &p, int v, const int *deg) {
+    uint64_t code = 0;
+    for (int u = 0; u < p.k; u++)
+        if (p.adjacent(v, u)) code += uint64_t(1) << (3 * (deg[u] - 1));
+    return (uint64_t(uint8_t(p.lab[v] + 1)) << 48) | (uint64_t(7 - deg[v]) << 40) | code;
+}
+
 Pat canonical_form(const Pat &p) {
-    Perm perm{};
-    std::iota(perm.begin(), perm.begin() + p.k, 0);
+    const int k = p.k;
+    int deg[KMAX];
+    uint64_t inv[KMAX];
+    int order[KMAX];
+    for (int v = 0; v < k; v++) deg[v] = __builtin_popcount(p.adj[v]);
+    for (int v = 0; v < k; v++) {
+        inv[v] = vertex_invariant(p, v, deg);
+        order[v] = v;
+    }
+    std::sort(order, order + k, [&](int a, int b) { return inv[a] != inv[b] ? inv[a] < inv[b] : a < b; });
+    int gb[KMAX + 1], ng = 0;      // group boundaries in `order`
+    for (int i = 0; i < k; i++)
+        if (i == 0 || inv[order[i]] != inv[order[i - 1]]) gb[ng++] = i;
+    gb[ng] = k;
     Pat best;
     bool have = false;
     uint64_t best_l = 0;
     uint32_t best_m = 0;
-    do {
+    for (;;) {
+        Perm perm{};
+        for (int i = 0; i < k; i++) perm[order[i]] = uint8_t(i);
         Pat q = relabel(p, perm);
-        uint64_t l = pack_labels(q);
-        uint32_t m = q.mask();
+        const uint64_t l = pack_labels(q);
+        const uint32_t m = q.mask();
         if (!have || l < best_l || (l == best_l && m < best_m)) {
             best = q; best_l = l; best_m = m; have = true;
         }
-    } while (std::next_permutation(perm.begin(), perm.begin() + p.k));
+        // next combination of within-group orders (odometer, last group fastest)
+        int g = ng - 1;
+        while (g >= 0 && !std::next_permutation(order + gb[g], order + gb[g + 1])) g--;
+        if (g < 0) break;
+    }
     if (best.is_clique()) best.vi = false;
     return best;
 }

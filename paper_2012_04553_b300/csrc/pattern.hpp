@@ -38,8 +38,10 @@ struct Pat {
     static Pat from_mask(int k, uint32_t mask, const int8_t *lab, bool vi);
 };
 
-// Canonical key (k, induced flag, labels and edge mask minimised over all
-// relabelings).  Cliques are keyed as edge-induced since both forms coincide.
+// Canonical key (k, induced flag, labels and edge mask minimised over the
+// relabelings that number vertices in ascending order of an isomorphism
+// invariant: a class function).  Cliques are keyed as edge-induced since
+// both forms coincide.
 struct Key {
     uint64_t a = 0, b = 0;
     bool operator<(const Key &o) const { return a != o.a ? a < o.a : b < o.b; }

@@ -185,13 +185,11 @@ pm_status pm_server_submit(pm_server *s, int32_t graph, const pm_pattern *querie
         return PM_EINVAL;
     }
     // reject malformed patterns now rather than failing the whole batch later
-    pm_query_plan *probe = nullptr;
-    pm_status st = pm_plan(s->graphs[graph], queries, nq, PM_OP_COUNT, pm_morph_mode(s->cfg.mode),
-                           &probe);
+    // validation and the request's own alternative-set size (no plan compilation)
+    int32_t matched_alone = 0;
+    pm_status st = pm::matched_set_size(s->graphs[graph], queries, nq, pm_morph_mode(s->cfg.mode),
+                                        &matched_alone);
     if (st != PM_OK) return st;
-    pm_plan_info info;
-    pm_plan_get_info(probe, &info);
-    pm_free_plan(probe);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         const uint64_t rid = s->next_id++;
@@ -199,7 +197,7 @@ pm_status pm_server_submit(pm_server *s, int32_t graph, const pm_pattern *querie
         r.graph = graph;
         r.queries.assign(queries, queries + nq);
         r.submitted = Clock::now();
-        r.matched_alone = info.n_matched;
+        r.matched_alone = matched_alone;
         s->pending[graph].push_back(rid);
         s->stats.requests_submitted++;
         *id = rid;

@@ -128,6 +128,27 @@ def test_clique_kernel_against_oracle():
                                        for k, m in ((4, 63), (5, 1023), (5, 1023))]
 
 
+@pytest.mark.parametrize("heavy", ["0", "64", "100000"])
+def test_wedge_heavy_and_light_roots(monkeypatch, heavy):
+    """Edge-induced 4-cycles through the wedge kernels with every root light
+    (dense global counters), the top 64 roots heavy (shared-memory windows),
+    and every root heavy; whole graph and a root subset."""
+    monkeypatch.setenv("PM_WEDGE_HEAVY", heavy)
+    n, s, d = two_hub_graph()
+    og = oracle.prepare_graph(n, s, d)
+    g = load(n, s, d)
+    c4 = algebra.Pattern.from_mask(4, 30)
+    plan = pm.Plan(g, [pm.make_pattern(4, 30)], mode=pm.MORPH_NONE)
+    plan.select(pm.PLANS_ROOTED)
+    assert plan.export_plans(pm.PLANS_ROOTED)[0]["kind"] == 1
+    assert plan.count() == [oracle.count(og, c4)]
+    assert plan.count() == [oracle.count(og, c4)]          # scratch left clean
+    roots = np.concatenate([np.arange(1, n, 5), [2046, 2047]]).astype(np.int32)
+    assert plan.count_roots(roots) == [oracle.count(og, c4, roots=roots)]
+    want4 = oracle.motif_counts_direct(og, 4)
+    assert pm.Plan(g, motif_queries(4), mode=pm.MORPH_NAIVE).count() == want4
+
+
 def test_six_vertex_patterns_against_oracle():
     s, d = rmat_edges(7, 5, seed=104)
     og = oracle.prepare_graph(128, s, d)
