@@ -786,8 +786,8 @@ wedge_heavy_kernel(DevGraph g, DevTasks tasks, int64_t heavy_from, int counter,
     __shared__ int s_minc[2];
     __shared__ unsigned long long s_acc[WH_THREADS / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    uint2 *L[2] = {lists + size_t(blockIdx.x) * 2 * size_t(list_cap),
-                   lists + size_t(blockIdx.x) * 2 * size_t(list_cap) + list_cap};
+    uint2 *const L0 = lists + size_t(blockIdx.x) * 2 * size_t(list_cap);
+    uint2 *const L1 = L0 + list_cap;
     const uint64_t deadline = *(volatile unsigned long long *)&ctl->deadline;
     const int64_t stride = sample_stride > 1 ? sample_stride : 1;
     const int64_t nr = (tasks.nroots + stride - 1) / stride;
@@ -823,7 +823,7 @@ wedge_heavy_kernel(DevGraph g, DevTasks tasks, int64_t heavy_from, int counter,
             const int32_t bl = lower_bound_dev(g.col + bb, int32_t(__ldg(g.rowptr + b + 1) - bb), a);
             if (bl > 0) {
                 const int slot = atomicAdd(&s_n[0], 1);
-                L[0][slot] = make_uint2(uint32_t(bb), uint32_t(bb + bl));
+                L0[slot] = make_uint2(uint32_t(bb), uint32_t(bb + bl));
                 atomicMin(&s_minc[0], __ldg(g.col + bb));
             }
         }
@@ -847,7 +847,7 @@ wedge_heavy_kernel(DevGraph g, DevTasks tasks, int64_t heavy_from, int counter,
             if (s_stop) break;
             const int64_t w1 = w0 + WH_W;
             for (int e = warp; e < nact; e += nwarps) {
-                const uint2 en = L[cur][e];
+                const uint2 en = (cur ? L1 : L0)[e];
                 uint32_t p = en.x;
                 for (;;) {
                     const uint32_t idx = p + uint32_t(lane);
@@ -860,7 +860,7 @@ wedge_heavy_kernel(DevGraph g, DevTasks tasks, int64_t heavy_from, int counter,
                 }
                 if (lane == 0 && p < en.y) {
                     const int slot = atomicAdd(&s_n[cur ^ 1], 1);
-                    L[cur ^ 1][slot] = make_uint2(p, en.y);
+                    (cur ? L0 : L1)[slot] = make_uint2(p, en.y);
                     atomicMin(&s_minc[cur ^ 1], __ldg(g.col + p));
                 }
             }
