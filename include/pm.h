@@ -155,7 +155,10 @@ void pm_free_plan(pm_query_plan *p);
  * plan of a pattern counts every occurrence once from its cheapest vertex,
  * breaking the whole automorphism group.  pm_count and pm_support use, per
  * matched pattern, the family the autotuner found faster on the plan's graph
- * (PM_PLANS_AUTO), unless pm_plan_select forces one. */
+ * (PM_PLANS_AUTO), unless pm_plan_select forces one.  The rooted plan of an
+ * unlabeled 4- or 5-clique runs in the clique kernel, which the autotuner
+ * does not yet choose (its hub-to-hub tasks are not load-balanced); it runs
+ * when the rooted family is selected and in pm_count_roots. */
 #define PM_PLANS_AUTO (-1)
 #define PM_PLANS_ROOTED 0
 #define PM_PLANS_FREE 1
