@@ -175,3 +175,46 @@ def test_special_plan_kinds():
     assert all(int(r["kind"]) == 0 for r in plan.export_plans(pm.PLANS_FREE))
     sup = pm.Plan(None, qs[:3], op=pm.OP_SUPPORT, mode=pm.MORPH_NONE)
     assert all(int(r["kind"]) == 0 for r in sup.export_plans(pm.PLANS_ROOTED))
+
+
+def _permuted(k, mask, labels, perm):
+    """The pattern with vertex v renamed perm[v] (mask over pairs a < b)."""
+    pairs = [(a, b) for a in range(k) for b in range(a + 1, k)]
+    index = {p: i for i, p in enumerate(pairs)}
+    out = 0
+    for i, (a, b) in enumerate(pairs):
+        if mask >> i & 1:
+            x, y = sorted((perm[a], perm[b]))
+            out |= 1 << index[(x, y)]
+    lab = [-1] * k
+    for v in range(k):
+        lab[perm[v]] = labels[v]
+    return out, lab
+
+
+def test_canonical_labelling_is_a_class_function():
+    # the library's canonical form (least labels/mask over the relabelings
+    # ordered by a vertex invariant) must name isomorphism classes exactly:
+    # all connected graphs on k <= 6 vertices give 2 / 6 / 21 / 112 classes
+    # (OEIS A001349), and random labeled patterns keep their class under
+    # random relabelings and split into exactly the oracle's classes
+    for k, want in ((3, 2), (4, 6), (5, 21), (6, 112)):
+        qs = [pm.make_pattern(k, m) for m in range(1 << (k * (k - 1) // 2))
+              if algebra.Pattern.from_mask(k, m).connected()]
+        assert pm.Plan(None, qs, mode=pm.MORPH_NONE).n_matched == want
+    rng = np.random.default_rng(17)
+    from pm_inputs import random_patterns
+    pool = random_patterns(300, kmin=3, kmax=7, seed=18)
+    lib_q, keys = [], set()
+    for k, m, ind in pool:
+        labels = [int(x) for x in rng.integers(-1, 2, size=k)]
+        perm = [int(x) for x in rng.permutation(k)]
+        m2, l2 = _permuted(k, m, labels, perm)
+        a = pm.make_pattern(k, m, ind, labels)
+        b = pm.make_pattern(k, m2, ind, l2)
+        assert pm.Plan(None, [a, b], mode=pm.MORPH_NONE).n_matched == 1
+        lib_q.append(a)
+        op = algebra.Pattern.from_mask(k, m, labels, bool(ind))
+        # a clique's vertex- and edge-induced forms are one pattern
+        keys.add(algebra.canonical(op.with_induced(False) if op.is_clique else op))
+    assert pm.Plan(None, lib_q, mode=pm.MORPH_NONE).n_matched == len(keys)
