@@ -158,7 +158,11 @@ void pm_free_plan(pm_query_plan *p);
  * (PM_PLANS_AUTO), unless pm_plan_select forces one.  The rooted plan of an
  * unlabeled 4- or 5-clique runs in the clique kernel, which the autotuner
  * does not yet choose (its hub-to-hub tasks are not load-balanced); it runs
- * when the rooted family is selected and in pm_count_roots. */
+ * when the rooted family is selected and in pm_count_roots.  The rooted plan
+ * of the edge-induced 4-cycle runs in the wedge kernels: roots among the
+ * H highest-ranked vertices (environment variable PM_WEDGE_HEAVY, read when
+ * a plan first runs the 4-cycle; default 16384) keep their pair counters in
+ * shared memory, the others in per-block global counters. */
 #define PM_PLANS_AUTO (-1)
 #define PM_PLANS_ROOTED 0
 #define PM_PLANS_FREE 1
