@@ -23,6 +23,7 @@
 // the host allocates whenever the largest degree exceeds the buffer.
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 
 #include "devgraph.cuh"
 #include "internal.hpp"
@@ -43,6 +44,7 @@ struct CliqueArgs {
     int32_t *spill;              // 2 * spill_len entries per warp, or nullptr
     int64_t spill_len;
     unsigned long long *stats;
+    int32_t balanced;            // 1: strided chunks, weighted sides, per-task deadline checks
 };
 
 // First index in s[0, len) whose value is >= key; s is written by this
@@ -62,15 +64,27 @@ __device__ __forceinline__ bool has_bitmap(const DevGraph &g, int32_t v) {
 }
 
 // Walking side for x against the members S[0, i): the row range of N(x)
-// inside [S[0], x).  Returns its length and start (index into col).
+// inside [S[0], x).  Returns its length and start (index into col); deg
+// receives |N(x)|.
 __device__ __forceinline__ int32_t walk_range(const DevGraph &g, int32_t x, int32_t s0,
-                                              int64_t &start) {
+                                              int64_t &start, int32_t &deg) {
     const int64_t rb = __ldg(g.rowptr + x);
     const int32_t d = int32_t(__ldg(g.rowptr + x + 1) - rb);
     const int32_t plo = lower_bound_dev(g.col + rb, d, s0);
     const int32_t phi = plo + lower_bound_dev(g.col + rb + plo, d - plo, x);
     start = rb + plo;
+    deg = d;
     return phi - plo;
+}
+
+__device__ __forceinline__ uint32_t bit_length(uint32_t v) { return 32u - uint32_t(__clz(v | 1u)); }
+
+// Walk instead of test?  Plain: the shorter side.  Weighted (balanced
+// mode): each side's item count times the depth of its binary searches --
+// a test searches N(x) (degree d), a walk searches the i members.
+__device__ __forceinline__ bool prefer_walk(int32_t len, int32_t i, int32_t d, bool weighted) {
+    if (!weighted) return len < i;
+    return uint64_t(len) * bit_length(uint32_t(i)) < uint64_t(i) * bit_length(uint32_t(d));
 }
 
 // Testing is chosen when x has a bitmap or few earlier members; otherwise
@@ -81,7 +95,7 @@ constexpr int32_t CQ_TEST_ALWAYS = 24;
 // sum over i of |S[0, i) n N(S[i])|.
 template <bool STATS>
 __device__ uint64_t edges_within(const DevGraph &g, const int32_t *S, int32_t s, int lane,
-                                 uint64_t &stat) {
+                                 uint64_t &stat, bool weighted) {
     uint64_t hits = 0;
     if (s < 2) return 0;
     const int32_t s0 = S[0];
@@ -93,8 +107,9 @@ __device__ uint64_t edges_within(const DevGraph &g, const int32_t *S, int32_t s,
             x = S[i];
             cost = i;
             if (i > CQ_TEST_ALWAYS && !has_bitmap(g, x)) {
-                const int32_t len = walk_range(g, x, s0, start);
-                if (len < i) {
+                int32_t d = 0;
+                const int32_t len = walk_range(g, x, s0, start, d);
+                if (prefer_walk(len, i, d, weighted)) {
                     walk = 1;
                     cost = len;
                 }
@@ -144,12 +159,13 @@ __device__ uint64_t edges_within(const DevGraph &g, const int32_t *S, int32_t s,
 // D = S[0, i) n N(x) in ascending order; returns |D| (warp-uniform).
 template <bool STATS>
 __device__ int32_t restrict_set(const DevGraph &g, const int32_t *S, int32_t i, int32_t x,
-                                int32_t *D, int lane, uint64_t &stat) {
+                                int32_t *D, int lane, uint64_t &stat, bool weighted) {
     int32_t len = i, walk = 0;
     int64_t start = 0;
     if (i > CQ_TEST_ALWAYS && !has_bitmap(g, x)) {
-        const int32_t w = walk_range(g, x, S[0], start);
-        if (w < i) {
+        int32_t d = 0;
+        const int32_t w = walk_range(g, x, S[0], start, d);
+        if (prefer_walk(w, i, d, weighted)) {
             walk = 1;
             len = w;
         }
@@ -221,8 +237,14 @@ clique_kernel(CliqueArgs A) {
         if (lane == 0) w = atomicAdd(&ctl->work3, 1ull);
         w = __shfl_sync(FULL, w, 0);
         if (w >= n_sampled || cq_stop(ctl, deadline, lane)) break;
-        // this lane's task of the chunk: root by binary search over the offsets
-        const int64_t e = int64_t(w * stride) * 32 + lane;
+        // this lane's task of the chunk: root by binary search over the offsets.
+        // Plain mode: chunk c holds tasks 32c .. 32c + 31 (one root's
+        // neighbours side by side); balanced mode: tasks c + j * n_chunks, so
+        // the tasks between one hub and its hub neighbours, adjacent in the
+        // hub's row, go to different chunks.  Either way every task is in
+        // exactly one chunk, and the tasks past the end are a suffix of lanes.
+        const int64_t c = int64_t(w * stride);
+        const int64_t e = A.balanced ? c + int64_t(lane) * int64_t(n_chunks) : c * 32 + lane;
         // (lower-neighbour tasks index a's row from its start, so the index of b
         // in N(a) is |N(a) n [0, b)|)
         int32_t a = -1, b = -1, ia = 0;
@@ -242,6 +264,10 @@ clique_kernel(CliqueArgs A) {
             const int32_t rb = __shfl_sync(FULL, b, q);
             const int32_t la = __shfl_sync(FULL, ia, q);
             if (ra < 0) break;                       // tasks past the end are at the tail
+            if (A.balanced && q > 0 && cq_stop(ctl, deadline, lane)) {
+                alive = false;
+                break;
+            }
             const int64_t rowa = __ldg(g.rowptr + ra);
             const int64_t rowb = __ldg(g.rowptr + rb);
             int32_t lb = 0;
@@ -269,7 +295,7 @@ clique_kernel(CliqueArgs A) {
             }
             __syncwarp();
             if (A.k == 4) {
-                hits += edges_within<STATS>(g, S, s, lane, stat);
+                hits += edges_within<STATS>(g, S, s, lane, stat, A.balanced != 0);
                 continue;
             }
             for (int32_t i = 2; i < s; i++) {
@@ -278,8 +304,8 @@ clique_kernel(CliqueArgs A) {
                     break;
                 }
                 int32_t *D = i <= CQ_CAP ? sD : pD;
-                const int32_t c2 = restrict_set<STATS>(g, S, i, S[i], D, lane, stat);
-                if (c2 >= 2) hits += edges_within<STATS>(g, D, c2, lane, stat);
+                const int32_t c2 = restrict_set<STATS>(g, S, i, S[i], D, lane, stat, A.balanced != 0);
+                if (c2 >= 2) hits += edges_within<STATS>(g, D, c2, lane, stat, A.balanced != 0);
                 __syncwarp();
             }
         }
@@ -341,6 +367,10 @@ int launch_clique(const DevGraph &g, const DevTasks &tasks, int k, int counter,
     A.spill = spill;
     A.spill_len = spill_len;
     A.stats = stats;
+    // balanced scheduling is opt-in until it has been timed against the
+    // plain one (PM_CLIQUE_BALANCED=1)
+    const char *bal = std::getenv("PM_CLIQUE_BALANCED");
+    A.balanced = (bal && bal[0] == '1') ? 1 : 0;
     cudaMemsetAsync(&ctl->work3, 0, sizeof(unsigned long long), s);
     if (stats) {
         const int blocks = clique_blocks_for<true>(device, k);
