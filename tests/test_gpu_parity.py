@@ -102,10 +102,13 @@ def two_hub_graph():
     return n, s, d
 
 
-def test_clique_kernel_against_oracle():
-    """4- and 5-cliques through the clique kernel (rooted family) and the
-    set-operation kernel (free family), whole graph and a root subset, with
-    the spill path exercised by two hubs of degree > 1,024."""
+@pytest.mark.parametrize("balanced", ["0", "1"])
+def test_clique_kernel_against_oracle(monkeypatch, balanced):
+    """4- and 5-cliques through the clique kernel (rooted family; plain and
+    balanced scheduling) and the set-operation kernel (free family), whole
+    graph and a root subset, with the spill path exercised by two hubs of
+    degree > 1,024."""
+    monkeypatch.setenv("PM_CLIQUE_BALANCED", balanced)
     n, s, d = two_hub_graph()
     og = oracle.prepare_graph(n, s, d)
     g = load(n, s, d)
