@@ -158,7 +158,10 @@ void pm_free_plan(pm_query_plan *p);
  * (PM_PLANS_AUTO), unless pm_plan_select forces one.  The rooted plan of an
  * unlabeled 4- or 5-clique runs in the clique kernel, which the autotuner
  * does not yet choose (its hub-to-hub tasks are not load-balanced); it runs
- * when the rooted family is selected and in pm_count_roots.  The rooted plan
+ * when the rooted family is selected and in pm_count_roots (environment
+ * variable PM_CLIQUE_BALANCED=1, read at each launch, spreads a root's
+ * tasks over chunks and weighs intersection sides by search depth; exact
+ * either way).  The rooted plan
  * of the edge-induced 4-cycle runs in the wedge kernels: roots among the
  * H highest-ranked vertices (environment variable PM_WEDGE_HEAVY, read when
  * a plan first runs the 4-cycle; default 16384) keep their pair counters in
@@ -231,7 +234,7 @@ pm_status pm_count_roots(pm_query_plan *p, void *stream, double timeout_s, const
                          int64_t nroots, uint64_t *counts, uint64_t *matched);
 
 /* Record the whole of pm_count for this plan (counter reset, arming, both
- * matching passes and the piece scan, the wedge kernel, the copy of the raw
+ * matching passes and the piece scan, the wedge or clique kernels, the copy of the raw
  * counts into pinned host memory) as one CUDA graph; later pm_count calls on
  * the plan replay it with one cudaGraphLaunch on their stream.  Autotuning
  * and all buffer set-up happen here, before capture.  timeout_s (<= 0: none)
