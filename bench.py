@@ -189,56 +189,91 @@ def barrier(world):
         dist.barrier()
 
 
-def traffic_record():
-    """DRAM bytes per launch of the matching kernel from the committed ncu
-    summary, valid only while the kernel source is unchanged."""
-    path = os.path.join(ROOT, "profiles", "match_kernel_traffic.json")
-    src = os.path.join(ROOT, "paper_2012_04553_b300", "csrc", "match.cu")
+def traffic_record(kernel):
+    """DRAM bytes per launch of `kernel` on this workload from the committed
+    ncu summary (profiles/traffic.json), valid only while the kernel's source
+    file is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
-    rec = json.load(open(path))
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if rec.get("match_cu_sha256") != sha:
+    rec = json.load(open(path)).get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2012_04553_b300", "csrc", rec["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
         return None
     return rec
 
 
-def cpu_oracle_sample(n, src, dst, ks, budget_s=15.0, seed=11, max_degree=200):
+def cpu_oracle_sample(n, src, dst, ks, budget_s=12.0, seed=11, per_root_s=1.0, sample=4096,
+                      all_core=True):
     """The oracle as it stands (direct vertex-induced counting) on a bounded
-    sample: roots drawn uniformly among the vertices of degree <= max_degree
-    (a root's occurrences are those whose highest-ranked vertex it is; the
-    oracle's cost per root grows like degree^(k-1), so hubs are left out to
-    keep the sample bounded), 16 at a time until budget_s; returns matches/s
-    over the roots processed."""
+    sample of the same workload: roots drawn uniformly over all n vertices
+    (every degree; a root's occurrences are those whose highest-ranked vertex
+    it is), each counted single-threaded under a per-root wall-clock budget
+    until budget_s is spent; roots whose budget runs out are recorded (with
+    their degree) and left out.  The completed roots are then counted again
+    in one call on all host cores.  Returns the all-core matches/s, the
+    single-thread matches/s, the roots and the per-root occurrence sums."""
     import oracle
     og = oracle.prepare_graph(n, src, dst)
-    cand = np.nonzero(og.degree <= max_degree)[0]
-    order = cand[uniform_ints(seed, 9, len(cand), 0, len(cand))]
-    matches, done, t0 = 0, 0, time.time()
-    while time.time() - t0 < budget_s and done < len(order):
-        roots = np.unique(order[done:done + 16]).astype(np.int32)
-        for k in ks:
-            matches += sum(oracle.motif_counts_direct(og, k, roots=roots))
-        done += 16
-    dt = time.time() - t0
-    return {"value": matches / dt, "unit": "matches/s", "cores": oracle.max_threads(),
-            "kind": "oracle",
-            "sample": f"{done} roots drawn uniformly among vertices of degree <= {max_degree} of the "
-                      f"same graph (occurrences whose highest-ranked vertex is a sampled root), "
-                      f"{'+'.join(str(k) for k in ks)}-motifs direct, {dt:.1f}s"}
+    order = uniform_ints(seed, 9, sample, 0, n)
+    _, first = np.unique(order, return_index=True)
+    order = order[np.sort(first)]
+    done, timed_out, matches, t_single, t0 = [], [], 0, 0.0, time.time()
+    for r in order:
+        if time.time() - t0 > budget_s:
+            break
+        oracle.set_budget(per_root_s)
+        t1 = time.time()
+        try:
+            c = sum(sum(oracle.motif_counts_direct(og, k, roots=np.array([r], np.int32), threads=1))
+                    for k in ks)
+        except oracle.OracleTimeout:
+            timed_out.append(int(og.degree[r]))
+            continue
+        finally:
+            oracle.set_budget(0)
+        t_single += time.time() - t1
+        done.append(int(r))
+        matches += c
+    roots = np.array(sorted(done), dtype=np.int32)
+    out = {"unit": "matches/s", "kind": "oracle", "roots": roots, "matches": matches,
+           "single_thread": {"value": matches / t_single if t_single > 0 else 0.0, "cores": 1,
+                             "seconds": round(t_single, 3)}}
+    value, cores = out["single_thread"]["value"], 1
+    if all_core and len(roots):
+        t1 = time.time()
+        c_all = sum(sum(oracle.motif_counts_direct(og, k, roots=roots)) for k in ks)
+        t_all = time.time() - t1
+        assert c_all == matches
+        value, cores = matches / t_all, oracle.max_threads()
+        out["all_core"] = {"value": value, "cores": cores, "seconds": round(t_all, 3)}
+    deg_done = og.degree[roots] if len(roots) else np.zeros(1, np.int64)
+    out.update({"value": value, "cores": cores,
+                "sample": f"{len(order[:len(done) + len(timed_out)])} roots drawn uniformly over all "
+                          f"{n} vertices of the same graph (occurrences whose highest-ranked vertex is a "
+                          f"sampled root), {'+'.join(str(k) for k in ks)}-motifs direct; "
+                          f"{len(done)} completed (max degree {int(deg_done.max())}), "
+                          f"{len(timed_out)} exceeded the {per_root_s:g} s per-root budget "
+                          f"(degrees {sorted(timed_out)[-8:]}); single-thread pass "
+                          f"{t_single:.1f} s, then the completed roots on all cores",
+                "roots_timed_out_degrees": sorted(timed_out)})
+    return out
 
 
 def run_reference(args, world, rank):
-    """Reference arm: the CPU oracle on the same workload, bounded samples."""
+    """Reference arm: the CPU oracle on the same workload, bounded samples
+    (a fresh uniform root sample per step, all host cores)."""
     if rank != 0:
         return
     n = 1 << SCALE
     src, dst = cached_rmat(SCALE, EDGE_FACTOR, SEED)
     ks = [4]
-    budget = max(5.0, 100.0 / max(1, args.steps + args.warmup))
+    budget = max(3.0, 90.0 / max(1, args.steps + args.warmup))
     steps = []
     for i in range(args.warmup + args.steps):
-        r = cpu_oracle_sample(n, src, dst, ks, budget_s=budget, seed=11 + i)
+        r = cpu_oracle_sample(n, src, dst, ks, budget_s=budget, seed=11 + i, per_root_s=0.5)
         if i >= args.warmup:
             steps.append(r)
     value = float(np.mean([r["value"] for r in steps]))
@@ -528,7 +563,7 @@ def main():
     barrier(world)
     torch.cuda.synchronize()
     sampler.start()
-    times, kernel_ms, counts = [], [], None
+    times, kernel_ms, per_pattern_ms, counts = [], [], [], None
     for _ in range(args.steps):
         flush.fill_(1)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -538,6 +573,7 @@ def main():
         torch.cuda.synchronize()
         times.append(ev0.elapsed_time(ev1))
         kernel_ms.append(plan.last_kernel_ms())
+        per_pattern_ms.append(plan.pattern_ms())
     torch.cuda.synchronize()
     barrier(world)
     clocks = sampler.stop()
@@ -547,20 +583,30 @@ def main():
     total_matches = allreduce_sum(matches, world)
     value = total_matches / (ms_step / 1000.0)
 
-    # end to end through the public API from pinned host buffers
+    # end to end through the public API from pinned host buffers: graph load
+    # (host preparation + upload), planning with autotuning on the fresh
+    # graph, the count, the result read back
     src_t = torch.from_numpy(src).pin_memory()
     dst_t = torch.from_numpy(dst).pin_memory()
-    e2e_times = []
+    e2e_times, phases = [], []
     for _ in range(max(1, min(args.steps, 2))):
         torch.cuda.synchronize()
         t0 = time.time()
         g2 = pm.Graph(n, src_t.numpy(), dst_t.numpy(), device=local, stream=stream)
-        c2 = pm.Plan(g2, queries, mode=pm.MORPH_NAIVE).count(stream=stream)
+        t1 = time.time()
+        p2 = pm.Plan(g2, queries, mode=pm.MORPH_NAIVE)
+        p2.autotune(stream=stream)
+        t2 = time.time()
+        c2 = p2.count(stream=stream)
         torch.cuda.synchronize()
-        e2e_times.append(time.time() - t0)
+        t3 = time.time()
+        e2e_times.append(t3 - t0)
+        phases.append((t1 - t0, t2 - t1, t3 - t2))
+        p2.free()
         g2.free()
         assert c2 == counts
     e2e_s = allreduce_max(float(np.mean(e2e_times)), world)
+    ph = np.mean(np.array(phases), axis=0)
     h2d = 8 * (n + 1) * 2 + 4 * 2 * info["m"] + 96 * plan0.n_plans
     d2h = 16 * plan0.n_matched + 24
 
@@ -576,9 +622,8 @@ def main():
         direct = {"timed_out_after_s": round(time.time() - t0, 3), "deadline_s": args.direct_deadline}
 
     peak, peak_kind = read_peaks()
-    kms = float(np.mean(kernel_ms))
-    achieved = alg_bytes / (kms / 1000.0) / 1e9 if kms > 0 else 0.0
-    trec = traffic_record()
+    roof = dominant_roofline(pm, g, plan0, per_pattern_ms, alg_bytes, float(np.mean(kernel_ms)),
+                             peak, peak_kind, stream)
     line = {
         "metric": metric_name(args), "value": value, "unit": "matches/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -587,21 +632,74 @@ def main():
         "counts": [str(c) for c in counts],
         "morphed_wall_s": ms_step / 1000.0,
         "direct": direct,
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 5), "peak_source": peak_kind,
-                     "traffic": trec["dram_bytes_per_launch"] if trec else None,
-                     "kernel": "match_kernel", "kernel_ms": round(kms, 3),
-                     "algorithmic_bytes_per_launch": alg_bytes},
+        "roofline": roof,
         "e2e": {"value": total_matches / e2e_s, "unit": "matches/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "wall_s": e2e_s},
+                "d2h_bytes_per_step": d2h, "wall_s": e2e_s,
+                "phases_s": {"load_and_upload": round(float(ph[0]), 3),
+                             "plan_and_autotune": round(float(ph[1]), 3),
+                             "count_and_readback": round(float(ph[2]), 3)}},
         "gpu_launches": args.steps * launches_per_count(plan0, n),
         "clocks": clocks,
         "graph": {"n": info["n"], "m": info["m"], "max_degree": info["max_degree"]},
     }
     if rank == 0 and world == 1 and not args.no_baseline:
-        line["cpu_baseline"] = cpu_oracle_sample(n, src, dst, ks)
+        base = cpu_oracle_sample(n, src, dst, ks)
+        roots = base.pop("roots")
+        sample_matches = base.pop("matches")
+        if len(roots):
+            # the library's exact count on the same roots; the whole-graph
+            # oracle time is extrapolated by the sample's share of occurrences
+            gpu_sample = sum(pm.Plan(g, queries, mode=pm.MORPH_NAIVE).count_roots(roots, stream=stream))
+            base["sample_counts_equal_library"] = gpu_sample == sample_matches
+            if sample_matches > 0 and "all_core" in base:
+                share = sample_matches / float(matches)
+                base["extrapolation"] = {
+                    "kind": "extrapolation (not measured): all-core oracle time on the sample "
+                            "divided by the sample's share of all occurrences",
+                    "sample_share_of_occurrences": share,
+                    "whole_graph_seconds": base["all_core"]["seconds"] / share}
+        line["cpu_baseline"] = base
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def kernel_of(kind):
+    return {0: "match_kernel", 1: "wedge_heavy_kernel+wedge_pairs_kernel", 2: "clique_kernel"}[kind]
+
+
+def dominant_roofline(pm, g, plan, per_pattern_ms, alg_bytes_all, seq_ms, peak, peak_kind, stream):
+    """Roofline of the matched pattern whose launches take the most device
+    time in a step (per-pattern CUDA events on the launch stream): its
+    kernel, its algorithmic bytes (instrumented run of that pattern alone,
+    same plan family) over its own average time."""
+    fam = plan.autotune(stream=stream)
+    rooted = plan.export_plans(pm.PLANS_ROOTED)
+    mats = plan.matched_patterns()
+    ms = np.mean(np.array(per_pattern_ms), axis=0)
+    j = int(np.argmax(ms))
+    kind = 0
+    if fam[j] == pm.PLANS_ROOTED:
+        kinds = [int(r["kind"]) for r in rooted if int(r["counter"]) == j]
+        kind = kinds[0] if len(kinds) == 1 else 0
+    k, mask, induced, labels = mats[j]
+    single = pm.Plan(g, [pm.make_pattern(k, mask, induced, labels)], mode=pm.MORPH_NONE)
+    single.select(fam[j])
+    _, b = single.count_instrumented(stream=stream)
+    achieved = b / (ms[j] / 1000.0) / 1e9 if ms[j] > 0 else 0.0
+    trec = traffic_record(kernel_of(kind))
+    share = float(ms[j] / ms.sum()) if ms.sum() > 0 else None
+    return {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 5), "peak_source": peak_kind,
+            "traffic": trec["dram_bytes_per_launch"] if trec else None,
+            "traffic_frac": (round(trec["dram_bytes_per_launch"] / (ms[j] / 1000.0) / 1e9 / peak, 5)
+                             if trec else None),
+            "kernel": kernel_of(kind),
+            "pattern": {"k": k, "edge_mask": mask, "induced": induced,
+                        "family": "rooted" if fam[j] == pm.PLANS_ROOTED else "free"},
+            "kernel_ms": round(float(ms[j]), 3), "share_of_step_device_time": share,
+            "algorithmic_bytes_per_launch": int(b),
+            "per_pattern_ms": [round(float(x), 3) for x in ms],
+            "whole_step": {"algorithmic_bytes": int(alg_bytes_all), "launch_sequence_ms": round(seq_ms, 3)}}
 
 
 if __name__ == "__main__":

@@ -208,7 +208,9 @@ pm_status pm_plan_export(const pm_query_plan *p, int32_t family, void *out, int6
  * Pure host arithmetic, usable on its own. */
 pm_status pm_morph(const pm_query_plan *p, const uint64_t *matched, uint64_t *requested);
 
-/* Count every query pattern (distinct occurrences = matches / |Aut(p)|).
+/* Count every query pattern (Section 2, Motif Counting: sum aggregation of
+ * distinct occurrences = matches / |Aut(p)|; morphed plans combine the
+ * matched patterns' counts by Theorem 3.1 / Corollary 3.1).
  * Runs the matching kernels on `stream`, waits for them, applies pm_morph.
  * counts: 2*n_queries words (128-bit, low word first).  matched (nullable):
  * 2*n_matched words receiving the alternative set's raw counts.
@@ -255,13 +257,34 @@ pm_status pm_count_instrumented(pm_query_plan *p, void *stream, uint64_t *counts
  * 0 if that call launched none. */
 pm_status pm_plan_last_kernel_ms(const pm_query_plan *p, float *ms);
 
-/* MNI support (Section 2, FSM) of every query of a PM_OP_SUPPORT plan:
- * one column per orbit of the query's label-preserving automorphism group,
- * holding the images of the orbit's vertices over all matches; support = the
- * smallest column.  support: n_queries words; frequent (nullable): n_queries
- * bytes, 1 when support >= threshold. */
+/* Device time (CUDA events on the launch stream) of each matched pattern's
+ * launch sequence in the plan's last completed pm_count (or its captured
+ * replay), in per-pattern launch mode: ms[j] for matched pattern j
+ * (n_matched entries), 0 for patterns that did not run on their own
+ * (single-launch mode, pm_count_roots, pm_count_instrumented). */
+pm_status pm_plan_pattern_ms(const pm_query_plan *p, float *ms);
+
+/* MNI support (Section 2, FSM; Theorem 3.2 with MNI tables for morphed
+ * plans) of every query of a PM_OP_SUPPORT plan: one column per orbit of the
+ * query's label-preserving automorphism group, holding the images of the
+ * orbit's vertices over all matches; support = the smallest column.
+ * support: n_queries words; frequent (nullable): n_queries bytes, 1 when
+ * support >= threshold.  domains_dev (nullable, device memory on the
+ * graph's device, caller-owned): the columns themselves, one bitset of
+ * ceil(n / 32) uint32 words per column, queries in order and each query's
+ * columns in column order (pm_plan_query_columns); bit v % 32 of word v / 32
+ * is set when caller vertex v is in the column.  Written asynchronously on
+ * `stream` and complete when the call returns.  The first call with
+ * domains_dev on a graph uploads the caller-to-internal vertex map (4n bytes,
+ * kept with the graph).  Errors: PM_EINVAL, PM_ENOMEM, PM_ECUDA,
+ * PM_ETIMEOUT (nothing returned). */
 pm_status pm_support(pm_query_plan *p, void *stream, double timeout_s, uint64_t threshold,
-                     uint64_t *support, uint8_t *frequent);
+                     uint64_t *support, uint8_t *frequent, uint32_t *domains_dev);
+/* Column of every vertex of every query of a PM_OP_SUPPORT plan:
+ * columns[i * PM_MAX_K + u] for vertex u of query i (-1 for u >= k).
+ * Columns are the automorphism orbits numbered by their smallest vertex;
+ * query i has 1 + max_u columns[i * PM_MAX_K + u] of them. */
+pm_status pm_plan_query_columns(const pm_query_plan *p, int32_t *columns);
 
 /* Frequent subgraph mining with MNI support (Section 2, FSM), level-wise
  * up to max_edges (1..5) edges on a labeled graph.  Level 1: every labeled
@@ -290,7 +313,10 @@ pm_status pm_fsm(const pm_graph *g, int32_t max_edges, uint64_t threshold, pm_mo
  * receiving the exact 128-bit count.  Asynchronous on `stream`.  The call
  * allocates nothing: its scratch is a 16 MiB array built into the library
  * (held on every GPU that loads it until exit), so n may be at most
- * 4194304 (PM_EINVAL beyond).  The first call on a device looks up that
+ * 4194304 (PM_EINVAL beyond).  Each block keeps n counters in that array,
+ * so the call runs min(SMs, 4194304 / n) blocks: all SMs up to about 28K
+ * vertices, 64 blocks at 65536, 4 blocks at 2^20 and one above 2^21, so
+ * large graphs count much more slowly here than with pm_count.  The first call on a device looks up that
  * array's device address, so make it before any stream capture.  All calls
  * share the array: calls that overlap on the GPU (other streams, other host
  * threads) race and must be serialised by the caller. */

@@ -52,12 +52,24 @@ def _load():
             ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
             ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
         lib.orc_max_threads.restype = ctypes.c_int
+        lib.orc_set_budget.restype = None
+        lib.orc_set_budget.argtypes = [ctypes.c_double]
         _lib = lib
     return _lib
 
 
 def max_threads():
     return _load().orc_max_threads()
+
+
+class OracleTimeout(RuntimeError):
+    """The wall-clock budget set with set_budget() ran out during a count."""
+
+
+def set_budget(seconds):
+    """Wall-clock budget (from now) for the following counts; 0 = none.  A
+    count still running when it passes raises OracleTimeout."""
+    _load().orc_set_budget(float(seconds))
 
 
 class Graph:
@@ -126,6 +138,8 @@ def match_count(g, p, roots=None, threads=0, domains=False):
         p.k, rel.ctypes.data, plab.ctypes.data,
         0 if r is None else len(r), None if r is None else r.ctypes.data,
         int(threads), out.ctypes.data, None if dom is None else dom.ctypes.data)
+    if rc == -2:
+        raise OracleTimeout("oracle budget expired")
     if rc != 0:
         raise ValueError(f"orc_count rejected pattern {p}")
     total = int(out[0]) | (int(out[1]) << 64)

@@ -73,8 +73,24 @@ static int admissible(const ctx_t *c, int level, int32_t x)
     return 1;
 }
 
+/* Optional wall-clock budget (orc_set_budget): once it has passed, every
+ * walk returns at once and orc_count reports -2.  Checked every 4096 calls
+ * per thread; it changes no count that completes within the budget. */
+static double g_deadline = 0.0;
+static volatile int g_expired = 0;
+
+static int expired(void)
+{
+    static __thread unsigned tick = 0;
+    if (g_deadline <= 0.0) return 0;
+    if (g_expired) return 1;
+    if ((++tick & 4095u) == 0 && omp_get_wtime() > g_deadline) g_expired = 1;
+    return g_expired;
+}
+
 static u128 extend(ctx_t *c, int level)
 {
+    if (expired()) return 0;
     int u = c->order[level];
     int32_t pv = c->map[c->parent[level]];
     u128 total = 0;
@@ -118,7 +134,9 @@ static int bfs_order(ctx_t *c, int j)
  * labels plab[k]) whose highest-ranked image vertex is one of roots[0..nroots)
  * (roots == NULL: every vertex).  Result as 128 bits in out[0] (low), out[1].
  * If dom != NULL, also sets dom[u*n + x] = 1 for every match m with m(u) = x.
- * Returns 0, or -1 on bad arguments (k out of range, pattern disconnected).
+ * Returns 0, -1 on bad arguments (k out of range, pattern disconnected), or
+ * -2 when the budget set by orc_set_budget ran out (the result is then
+ * incomplete).
  */
 int orc_count(int64_t n, const int64_t *rowptr, const int32_t *col,
               const int32_t *labels, const int64_t *rank,
@@ -164,7 +182,14 @@ int orc_count(int64_t n, const int64_t *rowptr, const int32_t *col,
     }
     out[0] = (uint64_t)total;
     out[1] = (uint64_t)(total >> 64);
-    return 0;
+    return g_expired ? -2 : 0;
+}
+
+/* Wall-clock budget for the following orc_count calls, from now; 0 = none. */
+void orc_set_budget(double seconds)
+{
+    g_expired = 0;
+    g_deadline = seconds > 0.0 ? omp_get_wtime() + seconds : 0.0;
 }
 
 int orc_max_threads(void) { return omp_get_max_threads(); }

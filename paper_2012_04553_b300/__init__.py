@@ -87,7 +87,8 @@ def _load():
         "pm_morph": [vp, vp, vp],
         "pm_count": [vp, vp, dbl, vp, vp],
         "pm_count_roots": [vp, vp, dbl, vp, i64, vp, vp],
-        "pm_support": [vp, vp, dbl, ctypes.c_uint64, vp, vp],
+        "pm_support": [vp, vp, dbl, ctypes.c_uint64, vp, vp, vp],
+        "pm_plan_query_columns": [vp, vp],
         "pm_plan_export": [vp, i32, vp, i64],
         "pm_plan_select": [vp, i32],
         "pm_plan_set_launch": [vp, i32],
@@ -103,6 +104,7 @@ def _load():
         "pm_fsm": [vp, i32, ctypes.c_uint64, ctypes.c_int, vp, dbl, vp, vp, vp, i32, ctypes.POINTER(i32)],
         "pm_count_instrumented": [vp, vp, vp, vp],
         "pm_plan_last_kernel_ms": [vp, ctypes.POINTER(ctypes.c_float)],
+        "pm_plan_pattern_ms": [vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -131,7 +133,8 @@ ABI_SYMBOLS = [
     "pm_plan_export", "pm_count_instrumented", "pm_plan_last_kernel_ms", "pm_plan_select",
     "pm_plan_autotune", "pm_count_c4_noalloc", "pm_fsm", "pm_plan_capture",
     "pm_server_create", "pm_server_submit", "pm_server_wait", "pm_server_get_stats",
-    "pm_server_destroy", "pm_plan_set_launch", "pm_count_each",
+    "pm_server_destroy", "pm_plan_set_launch", "pm_count_each", "pm_plan_query_columns",
+    "pm_plan_pattern_ms",
 ]
 
 
@@ -213,7 +216,32 @@ def count_c4_noalloc(rowptr, col, n, out, stream=None):
     """pm_count_c4_noalloc: edge-induced 4-cycle count of a device CSR into
     `out` (2 device uint64 words), with no device allocation in the call.
     rowptr, col and out are CUDA tensors (int64, int32, 2 x int64) the caller
-    owns; the call is asynchronous on the stream."""
+    owns; the call is asynchronous on the stream.  The tensors' types, device,
+    layout and sizes are checked here (PMError with PM_EINVAL otherwise), so
+    the kernel never reads past them; reading rowptr[n] costs one device to
+    host copy."""
+    n = int(n)
+    bad = None
+    for name, t, dt in (("rowptr", rowptr, "int64"), ("col", col, "int32"), ("out", out, "int64")):
+        if not getattr(t, "is_cuda", False):
+            bad = f"{name} must be a CUDA tensor"
+        elif str(t.dtype) != f"torch.{dt}":
+            bad = f"{name} must have dtype {dt}, not {t.dtype}"
+        elif not t.is_contiguous():
+            bad = f"{name} must be contiguous"
+        if bad:
+            break
+    if bad is None:
+        if not (rowptr.device == col.device == out.device):
+            bad = "rowptr, col and out must be on one device"
+        elif n < 1 or rowptr.numel() != n + 1:
+            bad = f"rowptr must hold n + 1 = {n + 1} offsets (has {rowptr.numel()})"
+        elif out.numel() < 2:
+            bad = "out must hold 2 words"
+        elif col.numel() < int(rowptr[-1].item()):
+            bad = "col is shorter than rowptr[n]"
+    if bad is not None:
+        raise PMError(PM_EINVAL, f"count_c4_noalloc: {bad}")
     _check(_lib.pm_count_c4_noalloc(ctypes.c_void_p(rowptr.data_ptr()), ctypes.c_void_p(col.data_ptr()),
                                     int(n), ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
            "pm_count_c4_noalloc")
@@ -345,6 +373,12 @@ class Plan:
         _check(_lib.pm_plan_last_kernel_ms(self._h, ctypes.byref(v)), "pm_plan_last_kernel_ms")
         return float(v.value)
 
+    def pattern_ms(self):
+        """Device time of each matched pattern in the last count() (per-pattern launches)."""
+        ms = np.zeros(self.n_matched, dtype=np.float32)
+        _check(_lib.pm_plan_pattern_ms(self._h, _ptr(ms)), "pm_plan_pattern_ms")
+        return [float(x) for x in ms]
+
     def count_each(self, timeout_per_pattern_s=0.0, timeout_total_s=0.0, stream=None):
         """(counts, statuses): a deadline per matched pattern, a status per query."""
         out = np.zeros(2 * self.n_queries, dtype=np.uint64)
@@ -369,12 +403,37 @@ class Plan:
                                    _ptr(out), _ptr(mat)), "pm_count_roots")
         return (_words_to_ints(out), _words_to_ints(mat)) if with_matched else _words_to_ints(out)
 
-    def support(self, threshold=0, stream=None, timeout_s=0.0):
+    def query_columns(self):
+        """Per query, the MNI column of each of its k vertices."""
+        cols = np.zeros(self.n_queries * MAX_K, dtype=np.int32)
+        _check(_lib.pm_plan_query_columns(self._h, _ptr(cols)), "pm_plan_query_columns")
+        return [[int(c) for c in cols[i * MAX_K:(i + 1) * MAX_K] if c >= 0] for i in range(self.n_queries)]
+
+    def support(self, threshold=0, stream=None, timeout_s=0.0, domains=False):
+        """MNI supports and frequent flags; with domains=True also the MNI
+        columns, per query a list of device bitsets (torch int32 tensors of
+        ceil(n / 32) words, bit v = caller vertex v), written by the library."""
         sup = np.zeros(self.n_queries, dtype=np.uint64)
         freq = np.zeros(self.n_queries, dtype=np.uint8)
+        dom = None
+        if domains:
+            import torch
+            cols = self.query_columns()
+            total = sum(max(c) + 1 for c in cols)
+            words = (self.graph.info()["n"] + 31) // 32
+            dev = torch.device("cuda", self.graph.info()["device"])
+            dom = torch.empty((total, words), dtype=torch.int32, device=dev)
         _check(_lib.pm_support(self._h, _stream_handle(stream), float(timeout_s), int(threshold),
-                               _ptr(sup), _ptr(freq)), "pm_support")
-        return [int(x) for x in sup], [bool(x) for x in freq]
+                               _ptr(sup), _ptr(freq), dom.data_ptr() if dom is not None else None),
+               "pm_support")
+        out = [int(x) for x in sup], [bool(x) for x in freq]
+        if not domains:
+            return out
+        per_query, at = [], 0
+        for c in cols:
+            per_query.append(dom[at:at + max(c) + 1])
+            at += max(c) + 1
+        return out + (per_query,)
 
     def free(self):
         if self._h:

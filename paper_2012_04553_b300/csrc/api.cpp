@@ -110,6 +110,10 @@ struct pm_query_plan {
     uint32_t defer_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // bracket the last matching launch
     bool timed = false;
+    // per matched pattern: events around its launch sequence in the last
+    // pm_count (per-pattern launch mode), and whether they were recorded
+    std::vector<cudaEvent_t> pat_ev;
+    std::vector<char> pat_recorded;
     unsigned long long *d_stats = nullptr;
     uint8_t *d_timed_out = nullptr;          // pm_count_each: expired matched patterns
     uint32_t *d_wedge = nullptr;             // wedge-kernel counters: blocks x n, kept zero
@@ -359,6 +363,11 @@ pm_status ensure_device(pm_query_plan *p) {
         e = cudaEventCreate(&p->ev0);
         if (!e) e = cudaEventCreate(&p->ev1);
     }
+    if (!e && p->pat_ev.empty()) {
+        p->pat_ev.assign(2 * nm, nullptr);
+        p->pat_recorded.assign(nm, 0);
+        for (size_t i = 0; i < 2 * nm && !e; i++) e = cudaEventCreate(&p->pat_ev[i]);
+    }
     if (e) {
         free_plan_device(p);
         return cuda_fail("plan set-up", e);
@@ -438,7 +447,14 @@ pm_status ensure_clique(pm_query_plan *p) {
 pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tasks,
                        int sample_stride, bool domains, unsigned long long *stats,
                        cudaStream_t s, uint64_t gate_budget_ns = 0,
-                       uint8_t *gate_flags = nullptr) {
+                       uint8_t *gate_flags = nullptr, bool record = false) {
+    // events around each matched pattern's launches (per-pattern mode only)
+    if (record) std::fill(p->pat_recorded.begin(), p->pat_recorded.end(), 0);
+    auto mark = [&](int counter, int end) {
+        if (!record || counter < 0 || size_t(counter) >= p->pat_recorded.size()) return;
+        cudaEventRecord(p->pat_ev[2 * size_t(counter) + size_t(end)], s);
+        if (end) p->pat_recorded[size_t(counter)] = 1;
+    };
     const pm_graph *g = p->g;
     MatchLaunch L{};
     L.g = g->dev();
@@ -478,8 +494,10 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
             } else if (b > 0 && launch_rearm(p->d_ctl, s)) {
                 return PM_ECUDA;
             }
+            mark(t.plans[b].counter, 0);
             const int rc = domains ? launch_domains(G, s) : launch_count(G, s);
             if (rc) return PM_ECUDA;
+            mark(t.plans[b].counter, 1);
             b = e;
         }
     } else if (n_setops > 0 && L.n_echunks > 0) {
@@ -498,6 +516,7 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
         if (st != PM_OK) return st;
         if (gate_flags && launch_pattern_gate(p->d_ctl, gate_flags, last, gate_budget_ns, s))
             return PM_ECUDA;
+        mark(dp.counter, 0);
         if (dp.kind == PLAN_WEDGE_PAIRS) {
             if (launch_wedge_pairs(L.g, tasks, p->heavy_from, dp.counter, p->d_counters, p->d_wedge,
                                    p->d_lists, p->list_cap, p->wedge_nblocks, sample_stride,
@@ -507,6 +526,7 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
                                  p->spill_len, sample_stride, p->d_ctl, stats, s)) {
             return PM_ECUDA;
         }
+        mark(dp.counter, 1);
         last = dp.counter;
     }
     if (gate_flags && last >= 0 && launch_pattern_gate(p->d_ctl, gate_flags, last, 0, s))
@@ -703,7 +723,8 @@ pm_status run_count(pm_query_plan *p, void *stream, double timeout_s, const int3
         if (e) return cuda_fail("pm_count: memset", e);
     }
     cudaEventRecord(p->ev0, s);
-    st = launch_table(p, *table, tasks, 1, false, alg_bytes ? p->d_stats : nullptr, s);
+    st = launch_table(p, *table, tasks, 1, false, alg_bytes ? p->d_stats : nullptr, s, 0, nullptr,
+                      !use_roots && !alg_bytes);
     if (st != PM_OK) return st;
     cudaEventRecord(p->ev1, s);
     p->timed = true;
@@ -882,6 +903,7 @@ void pm_free_graph(pm_graph *g) {
     dev_free(g->d_labels, g->n, g->device);
     dev_free(g->d_hub, sizeof(int32_t) * g->n, g->device);
     dev_free(g->d_bits, sizeof(uint32_t) * size_t(g->n_hubs) * size_t(g->hub_words), g->device);
+    dev_free(g->d_new_id, sizeof(int32_t) * size_t(g->n), g->device);
     delete g;
 }
 
@@ -1033,6 +1055,18 @@ pm_status pm_plan_last_kernel_ms(const pm_query_plan *p, float *ms) {
     return PM_OK;
 }
 
+pm_status pm_plan_pattern_ms(const pm_query_plan *p, float *ms) {
+    if (!p || !ms) return PM_EINVAL;
+    for (size_t j = 0; j < p->morph.matched.size(); j++) {
+        ms[j] = 0.f;
+        if (j < p->pat_recorded.size() && p->pat_recorded[j]) {
+            cudaError_t e = cudaEventElapsedTime(&ms[j], p->pat_ev[2 * j], p->pat_ev[2 * j + 1]);
+            if (e) return cuda_fail("pm_plan_pattern_ms", e);
+        }
+    }
+    return PM_OK;
+}
+
 void pm_free_plan(pm_query_plan *p) {
     if (!p) return;
     if (p->g && p->device_ready) {
@@ -1043,6 +1077,8 @@ void pm_free_plan(pm_query_plan *p) {
     if (p->h_pinned) cudaFreeHost(p->h_pinned);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
+    for (cudaEvent_t ev : p->pat_ev)
+        if (ev) cudaEventDestroy(ev);
     delete p;
 }
 
@@ -1135,7 +1171,7 @@ pm_status pm_plan_capture(pm_query_plan *p, void *stream, double timeout_s) {
         const uint64_t budget = timeout_s > 0 ? uint64_t(timeout_s * 1e9) : 0;
         launch_arm(p->d_ctl, budget, cs);
         cudaEventRecord(p->ev0, cs);
-        st = launch_table(p, p->active, tasks, 1, false, nullptr, cs);
+        st = launch_table(p, p->active, tasks, 1, false, nullptr, cs, 0, nullptr, true);
         cudaEventRecord(p->ev1, cs);
         cudaMemcpyAsync(p->h_pinned, p->d_counters, sizeof(uint64_t) * 2 * nm,
                         cudaMemcpyDeviceToHost, cs);
@@ -1177,8 +1213,21 @@ pm_status pm_count_instrumented(pm_query_plan *p, void *stream, uint64_t *counts
     return run_count(p, stream, 0.0, nullptr, 0, false, counts, nullptr, alg_bytes);
 }
 
+pm_status pm_plan_query_columns(const pm_query_plan *p, int32_t *columns) {
+    if (!p || !columns) return PM_EINVAL;
+    if (p->op != PM_OP_SUPPORT) {
+        set_error("pm_plan_query_columns: plan was made for PM_OP_COUNT");
+        return PM_EINVAL;
+    }
+    for (size_t i = 0; i < p->morph.query_columns.size(); i++)
+        for (int u = 0; u < PM_MAX_K; u++)
+            columns[i * PM_MAX_K + u] =
+                u < int(p->morph.query_columns[i].size()) ? p->morph.query_columns[i][u] : -1;
+    return PM_OK;
+}
+
 pm_status pm_support(pm_query_plan *p, void *stream, double timeout_s, uint64_t threshold,
-                     uint64_t *support, uint8_t *frequent) {
+                     uint64_t *support, uint8_t *frequent, uint32_t *domains_dev) {
     if (!p || !support) {
         set_error("pm_support: null argument");
         return PM_EINVAL;
@@ -1214,6 +1263,24 @@ pm_status pm_support(pm_query_plan *p, void *stream, double timeout_s, uint64_t 
     if (launch_mni_reduce(p->d_bitsets, p->words, p->d_col_off, p->d_col_src, int(ncols),
                           p->d_popc, s))
         return PM_ECUDA;
+    if (domains_dev) {
+        {
+            std::lock_guard<std::mutex> lk(g->new_id_mu);
+            if (!g->d_new_id) {
+                g->d_new_id = (int32_t *)dev_alloc(sizeof(int32_t) * size_t(g->n), g->device);
+                if (!g->d_new_id) {
+                    set_error("pm_support: device allocation failed (vertex map)");
+                    return PM_ENOMEM;
+                }
+                e = cudaMemcpy(g->d_new_id, g->new_id.data(), sizeof(int32_t) * size_t(g->n),
+                               cudaMemcpyHostToDevice);
+                if (e) return cuda_fail("pm_support: vertex map upload", e);
+            }
+        }
+        if (launch_mni_domains(p->d_bitsets, p->words, p->d_col_off, p->d_col_src, int(ncols),
+                               g->d_new_id, g->n, domains_dev, s))
+            return PM_ECUDA;
+    }
     std::vector<unsigned long long> popc(ncols);
     Control ctl;
     e = ncols ? cudaMemcpyAsync(popc.data(), p->d_popc, sizeof(unsigned long long) * ncols,

@@ -101,7 +101,7 @@ extern "C" pm_status pm_fsm(const pm_graph *g, int32_t max_edges, uint64_t thres
         if (st != PM_OK) return st;
         std::vector<uint64_t> sup(q.size());
         std::vector<uint8_t> fr(q.size());
-        st = pm_support(plan, stream, timeout_s, threshold, sup.data(), fr.data());
+        st = pm_support(plan, stream, timeout_s, threshold, sup.data(), fr.data(), nullptr);
         pm_free_plan(plan);
         if (st != PM_OK) return st;
         std::set<Key> frequent_keys;

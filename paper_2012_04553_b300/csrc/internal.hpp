@@ -31,6 +31,10 @@ struct pm_graph {
     int64_t n_hubs = 0, hub_words = 0;
     int64_t ntasks[3] = {0, 0, 0};
     size_t bytes = 0;
+    // caller id -> internal id on the device, uploaded when MNI domains are
+    // first returned in caller ids (pm_support with domains_dev)
+    mutable std::mutex new_id_mu;
+    mutable int32_t *d_new_id = nullptr;
     // Autotuner cache: canonical pattern key -> chosen plan family
     // (0 rooted, 1 free); shared by every plan made on this graph.
     mutable std::mutex tune_mu;
@@ -60,6 +64,7 @@ struct MorphPlan {
     std::vector<std::vector<int>> matched_orbit;     // per matched pattern: column of each vertex
     std::vector<std::vector<std::vector<std::pair<int, int>>>> mni_sources;
     // mni_sources[query][query column] = list of (matched, matched column)
+    std::vector<std::vector<int>> query_columns;     // per query: column of each pattern vertex
 };
 
 // Morph selection (Section 4.1, step a).  Returns PM_OK or an error status
@@ -140,6 +145,11 @@ int launch_clique(const DevGraph &g, const DevTasks &tasks, int k, int counter,
 int launch_mni_reduce(const uint32_t *d_bitsets, int64_t words_per_bitset, const int32_t *d_src_off,
                       const int32_t *d_src, int n_columns, unsigned long long *d_popc,
                       void *stream);
+// Query columns as n-bit bitsets in caller vertex ids: bit v of column c of
+// out (words_per_bitset words each) = bit new_id[v] of the OR of c's sources.
+int launch_mni_domains(const uint32_t *d_bitsets, int64_t words_per_bitset,
+                       const int32_t *d_src_off, const int32_t *d_src, int n_columns,
+                       const int32_t *d_new_id, int64_t n, uint32_t *out, void *stream);
 int device_sm_count(int device);
 
 }  // namespace pm

@@ -688,6 +688,33 @@ __global__ void mni_reduce_kernel(const uint32_t *__restrict__ bitsets, int64_t 
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(popc + col, local);
 }
 
+// MNI domains returned to the caller (Theorem 3.2 with MNI tables): word w
+// of column c covers caller vertices 32w .. 32w + 31; each one's bit is the
+// bit of its internal id in the OR of the column's matched bitsets.
+__global__ void mni_domains_kernel(const uint32_t *__restrict__ bitsets, int64_t words,
+                                   const int32_t *__restrict__ src_off,
+                                   const int32_t *__restrict__ src, int n_columns,
+                                   const int32_t *__restrict__ new_id, int64_t n,
+                                   uint32_t *__restrict__ out) {
+    const int col = blockIdx.y;
+    if (col >= n_columns) return;
+    const int s0 = src_off[col], s1 = src_off[col + 1];
+    for (int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; w < words;
+         w += int64_t(gridDim.x) * blockDim.x) {
+        uint32_t word = 0;
+        const int64_t v0 = w * 32;
+        const int nv = int(n - v0 < 32 ? n - v0 : 32);
+        for (int j = 0; j < nv; j++) {
+            const int32_t iv = __ldg(new_id + v0 + j);
+            uint32_t bit = 0;
+            for (int s = s0; s < s1 && !bit; s++)
+                bit = (__ldg(bitsets + int64_t(src[s]) * words + (iv >> 5)) >> (iv & 31)) & 1u;
+            word |= bit << j;
+        }
+        out[int64_t(col) * words + w] = word;
+    }
+}
+
 int device_sm_count(int device) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
@@ -1019,6 +1046,27 @@ int launch_count(const MatchLaunch &L, void *stream) {
 
 int launch_domains(const MatchLaunch &L, void *stream) {
     return launch_match<true, false>(L, stream);
+}
+
+int launch_mni_domains(const uint32_t *d_bitsets, int64_t words, const int32_t *d_src_off,
+                       const int32_t *d_src, int n_columns, const int32_t *d_new_id, int64_t n,
+                       uint32_t *out, void *stream) {
+    if (n_columns == 0) return 0;
+    int device = 0;
+    cudaGetDevice(&device);
+    const int sms = device_sm_count(device);
+    int64_t bx = (words + 255) / 256;
+    if (bx > 4 * sms) bx = 4 * sms;
+    if (bx < 1) bx = 1;
+    dim3 grid{unsigned(bx), unsigned(n_columns), 1u};
+    mni_domains_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(d_bitsets, words, d_src_off, d_src,
+                                                               n_columns, d_new_id, n, out);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) {
+        set_error(std::string("mni domains launch: ") + cudaGetErrorString(err));
+        return -1;
+    }
+    return 0;
 }
 
 int launch_mni_reduce(const uint32_t *d_bitsets, int64_t words, const int32_t *d_src_off,

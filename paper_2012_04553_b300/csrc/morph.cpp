@@ -81,11 +81,13 @@ void fill_mni_sources(MorphPlan &out) {
     const std::vector<Pat> &queries = out.queries;
     {
         out.mni_sources.assign(queries.size(), {});
+        out.query_columns.assign(queries.size(), {});
         for (size_t i = 0; i < queries.size(); i++) {
             Pat p = queries[i];
             if (p.is_clique()) p.vi = false;
             int nqc = 0;
             std::vector<int> qcol = columns_of(p, &nqc);
+            out.query_columns[i] = qcol;
             out.mni_sources[i].assign(nqc, {});
             std::vector<int> rep(nqc, -1);
             for (int u = 0; u < p.k; u++)

@@ -273,14 +273,22 @@ def sampled_roots(deg, seed, count, max_degree):
     return np.unique(cand[pick]).astype(np.int32)
 
 
-def test_full_size_scale20_sampled_roots():
-    """The scale-20 R-MAT graph (edge factor 16, seed 2) in the bench's launch
-    configuration, checked exactly on sampled roots (uniform over vertices of
-    degree <= 160 for 4-motifs, <= 40 for 5-motifs), morphed and direct."""
+@pytest.fixture(scope="module")
+def scale20():
+    """The bench's graph: R-MAT scale 20, edge factor 16, seed 2 (oracle and library)."""
     s, d = cached_rmat(20, 16, seed=2)
     n = 1 << 20
-    og = oracle.prepare_graph(n, s, d)
-    g = load(n, s, d)
+    return oracle.prepare_graph(n, s, d), load(n, s, d)
+
+
+def test_full_size_scale20_sampled_roots(scale20):
+    """The scale-20 graph checked exactly on sampled roots through the rooted
+    plans (uniform over vertices of degree <= 160 for 4-motifs, <= 40 for
+    5-motifs), morphed and direct; 3-motifs also on a band of 32 hub roots
+    (ranks 1,000-1,031 from the top, degree ~3,800, where the oracle's cost per
+    root is about degree^2)."""
+    og, g = scale20
+    n = og.n
     roots = sampled_roots(og.degree, 2, 64, 160)
     want = oracle.motif_counts_direct(og, 4, roots=roots)
     for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
@@ -289,6 +297,58 @@ def test_full_size_scale20_sampled_roots():
     want5 = oracle.motif_counts_direct(og, 5, roots=roots5)
     for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
         assert pm.Plan(g, motif_queries(5), mode=mode).count_roots(roots5) == want5
+    by_rank = np.argsort(og.rank)                # by_rank[r] = vertex of rank r
+    band = by_rank[n - 1032:n - 1000]
+    roots3 = np.unique(np.concatenate([band, sampled_roots(og.degree, 4, 32, 1 << 30)])).astype(np.int32)
+    want3 = oracle.motif_counts_direct(og, 3, roots=roots3)
+    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+        assert pm.Plan(g, motif_queries(3), mode=mode).count_roots(roots3) == want3
+
+
+def test_full_size_scale20_closed_forms(scale20):
+    """Whole-graph counts on the scale-20 graph through count(), in the
+    bench's configuration (autotuned plan families, per-pattern launches)
+    and with the free family forced: the edge-induced stars K1,2, K1,3, K1,4
+    equal sum_v C(d_v, k-1) (computed from the oracle's degrees); the bench's
+    4-motif plan reports the edge-induced K1,3 among its matched counts."""
+    og, g = scale20
+    deg = [int(x) for x in og.degree]
+    stars = [pm.make_pattern(k, (1 << (k - 1)) - 1) for k in (3, 4, 5)]   # edges (0,1)..(0,k-1)
+    want = [sum(comb(x, k - 1) for x in deg) for k in (3, 4, 5)]
+    for family in (pm.PLANS_AUTO, pm.PLANS_FREE):
+        plan = pm.Plan(g, stars, mode=pm.MORPH_NONE)
+        plan.select(family)
+        assert plan.count() == want, family
+    bench = pm.Plan(g, motif_queries(4), mode=pm.MORPH_NAIVE)
+    counts, matched = bench.count(with_matched=True)
+    idx = [i for i, q in enumerate(bench.matched_patterns())
+           if q[0] == 4 and bin(q[1]).count("1") == 3 and q[2] == pm.EDGE_INDUCED and
+           max(bin(q[1] & m).count("1") for m in (0b000111, 0b011001, 0b101010, 0b110100)) == 3]
+    assert len(idx) == 1 and matched[idx[0]] == want[1]
+    assert all(c > 0 for c in counts)
+
+
+def test_counts_beyond_2_64_on_stars():
+    """Four disjoint stars with 2^17 leaves: the edge-induced 6-vertex star
+    occurs 4 * C(2^17, 5) ~ 1.3e24 times (beyond 2^64: the 128-bit carries of
+    the counter and of the warp sums), built from per-task binomials
+    C(c, 4) whose falling product exceeds 2^64 (the long division); the
+    5-vertex star gives 4 * C(2^17, 4).  Vertex-induced stars morphed from
+    edge-induced superpatterns give the same counts (no edges among leaves)."""
+    L = 1 << 17
+    n = 4 * (L + 1)
+    centres = np.repeat(np.arange(4) * (L + 1), L)
+    leaves = centres + np.tile(np.arange(1, L + 1), 4)
+    g = load(n, centres.astype(np.int32), leaves.astype(np.int32))
+    want = [4 * comb(L, 4), 4 * comb(L, 5)]
+    assert want[1] > 1 << 64
+    ei = [pm.make_pattern(5, 0b1111), pm.make_pattern(6, 0b11111)]
+    for family in (pm.PLANS_AUTO, pm.PLANS_ROOTED, pm.PLANS_FREE):
+        plan = pm.Plan(g, ei, mode=pm.MORPH_NONE)
+        plan.select(family)
+        assert plan.count() == want, family
+    vi = [pm.make_pattern(5, 0b1111, pm.VERTEX_INDUCED), pm.make_pattern(6, 0b11111, pm.VERTEX_INDUCED)]
+    assert pm.Plan(g, vi, mode=pm.MORPH_NAIVE).count() == want
 
 
 def test_mni_support_against_oracle():
@@ -307,6 +367,37 @@ def test_mni_support_against_oracle():
             sup, freq = plan.support(threshold=20)
             assert sup == want, (mode, family)
             assert freq == [w >= 20 for w in want]
+
+
+def test_mni_domains_returned_in_caller_ids():
+    """pm_support's domains_dev output: every query column as a bitset over
+    the caller's vertex ids equals the union, over the column's orbit, of the
+    oracle's per-vertex domains (all matches), morphed and direct."""
+    n = 512
+    s, d = rmat_edges(9, 8, seed=120)
+    labels = zipf_labels(n, 3, seed=121)
+    og = oracle.prepare_graph(n, s, d, labels)
+    g = load(n, s, d, labels)
+    qs = oracle.labeled_edge_patterns(3, [0, 1, 2])[1::3] + oracle.labeled_edge_patterns(1, [0, 1])
+    cq = [pm.make_pattern(p.k, p.mask, pm.EDGE_INDUCED, p.labels) for p in qs]
+    want = []
+    for p in qs:
+        dom = oracle.domains_direct(og, p)
+        want.append([np.logical_or.reduce([dom[u] for u in orb]) for orb in algebra.orbits(p)])
+    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+        plan = pm.Plan(g, cq, op=pm.OP_SUPPORT, mode=mode)
+        cols = plan.query_columns()
+        sup, _, doms = plan.support(threshold=1, domains=True)
+        for i, p in enumerate(qs):
+            # library columns are orbits numbered by their smallest vertex, as algebra.orbits
+            assert cols[i] == [next(c for c, orb in enumerate(algebra.orbits(p)) if u in orb)
+                               for u in range(p.k)]
+            words = doms[i].cpu().numpy().view(np.uint32)
+            bits = ((words[:, :, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(len(words), -1)
+            got = bits[:, :n].astype(bool)
+            for c in range(len(want[i])):
+                assert (got[c] == want[i][c]).all(), (mode, i, c)
+            assert sup[i] == min(int(w.sum()) for w in want[i])
 
 
 def test_fsm_against_oracle():

@@ -1,5 +1,6 @@
 """The allocation-free 4-cycle entry point (pm_count_c4_noalloc) against the
-regular one (pm_count), through the C ABI, on two calls in a row.
+regular one (pm_count) and the oracle, through the C ABI, on two calls in a
+row.
 
 The entry point exists for callers that cannot allocate device memory while
 counting; it keeps its scratch in an array built into the library, so its
@@ -8,6 +9,8 @@ call left in that shared array.  This file is collected last on purpose."""
 import numpy as np
 import pytest
 
+import oracle
+from oracle import algebra
 import paper_2012_04553_b300 as pm
 from pm_inputs import rmat_edges
 
@@ -35,7 +38,9 @@ def as_int(words):
     return lo | (hi << 64)
 
 
-@pytest.mark.parametrize("scale,ef,seed", [(12, 8, 71), (14, 16, 72)])
+# scale 16 holds 65,536 vertices: the scratch then fits 64 blocks, fewer
+# than the SMs, so each block's counters sit far into the shared array
+@pytest.mark.parametrize("scale,ef,seed", [(12, 8, 71), (14, 16, 72), (16, 8, 73)])
 def test_noalloc_c4_matches_pm_count_on_two_calls(scale, ef, seed):
     import torch
     n = 1 << scale
@@ -43,6 +48,9 @@ def test_noalloc_c4_matches_pm_count_on_two_calls(scale, ef, seed):
     g = pm.Graph(n, s, d)
     want = pm.Plan(g, [pm.make_pattern(4, C4_MASK)], mode=pm.MORPH_NONE).count()[0]
     assert want > 0
+    if scale == 12:
+        # and against the oracle (plain backtracking), not only the other entry point
+        assert want == oracle.count(oracle.prepare_graph(n, s, d), algebra.Pattern.from_mask(4, C4_MASK))
     rowptr, col = undirected_csr(n, s, d)
     rowptr_d = torch.from_numpy(rowptr).cuda()
     col_d = torch.from_numpy(col).cuda()
@@ -54,11 +62,24 @@ def test_noalloc_c4_matches_pm_count_on_two_calls(scale, ef, seed):
         assert as_int(out.cpu().tolist()) == want
 
 
+def test_noalloc_rejects_malformed_tensors():
+    import torch
+    rowptr_d = torch.zeros(5, dtype=torch.int64, device="cuda")
+    col_d = torch.zeros(4, dtype=torch.int32, device="cuda")
+    out = torch.zeros(2, dtype=torch.int64, device="cuda")
+    for args in ((rowptr_d.int(), col_d, 4, out), (rowptr_d, col_d.long(), 4, out),
+                 (rowptr_d, col_d, 5, out), (rowptr_d, col_d, 4, out[:1]), (rowptr_d.cpu(), col_d, 4, out)):
+        with pytest.raises(pm.PMError) as e:
+            pm.count_c4_noalloc(*args)
+        assert e.value.status == pm.PM_EINVAL
+
+
 def test_noalloc_rejects_graphs_beyond_its_scratch():
     import torch
-    rowptr_d = torch.zeros(2, dtype=torch.int64, device="cuda")
+    n = (1 << 22) + 1
+    rowptr_d = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
     col_d = torch.zeros(1, dtype=torch.int32, device="cuda")
     out = torch.zeros(2, dtype=torch.int64, device="cuda")
     with pytest.raises(pm.PMError) as e:
-        pm.count_c4_noalloc(rowptr_d, col_d, (1 << 22) + 1, out)
+        pm.count_c4_noalloc(rowptr_d, col_d, n, out)
     assert e.value.status == pm.PM_EINVAL
