@@ -290,24 +290,6 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def launches_per_count(plan, n):
-    """Library kernels one pm_count launches (per-pattern launch mode): the
-    arming kernel; per matched pattern run by set operations, the two
-    matching passes and the piece scan (plus a counter reset before every
-    pattern but the first); one wedge or clique kernel for a 4-cycle or a
-    clique run with its rooted plan."""
-    import paper_2012_04553_b300 as pm
-    fam = plan.autotune()            # the cached per-pattern decisions
-    rooted = plan.export_plans(pm.PLANS_ROOTED)
-    chosen = [int(r["kind"]) for r in rooted if r["kind"] != 0 and fam[int(r["counter"])] == pm.PLANS_ROOTED]
-    # the wedge plan launches a heavy-root kernel (top H ranks) and, when
-    # n > H, a light-root kernel
-    heavy = int(os.environ.get("PM_WEDGE_HEAVY", "16384"))
-    wedge = int(heavy > 0) + int(n > heavy)
-    setops = plan.n_matched - len(chosen)
-    return 1 + 3 * setops + max(0, setops - 1) + sum(wedge if k == 1 else 1 for k in chosen)
-
-
 def metric_name(args):
     return "4-motif counting matches/s (morphed), R-MAT scale 20"
 
@@ -638,7 +620,7 @@ def main():
                 "phases_s": {"load_and_upload": round(float(ph[0]), 3),
                              "plan_and_autotune": round(float(ph[1]), 3),
                              "count_and_readback": round(float(ph[2]), 3)}},
-        "gpu_launches": args.steps * launches_per_count(plan0, n),
+        "gpu_launches": args.steps * plan.last_launches(),
         "clocks": clocks,
         "graph": {"n": info["n"], "m": info["m"], "max_degree": info["max_degree"]},
     }

@@ -170,8 +170,23 @@ void pm_free_plan(pm_query_plan *p);
 #define PM_PLANS_ROOTED 0
 #define PM_PLANS_FREE 1
 /* No timing: free plans, except the rooted 4-cycle plan that runs the
- * wedge kernel (for latency-bound callers such as the serving loop). */
+ * wedge kernel (for latency-bound callers such as the serving loop), and the
+ * decomposition kernels where they apply. */
 #define PM_PLANS_QUICK 2
+/* Decomposition kernels for the unlabeled edge-induced patterns they cover
+ * (4 vertices: star K1,3, path P4, tailed triangle, diamond; 5 vertices:
+ * star, fork, path, cricket, bull, lollipop, banner, 5-cycle, kite, dart,
+ * bowtie, house, book K1,1,3, gem, 4-clique with a pendant), autotuned
+ * families for the other patterns.  Their counts come from exact identities
+ * over per-vertex and per-edge quantities (degrees, triangles per edge,
+ * 2-paths from each vertex to the vertices below it, 4-cliques with their
+ * degree sums) instead of enumerating occurrences.  Counting plans use them
+ * by default (PM_PLANS_AUTO and PM_PLANS_QUICK); PM_PLANS_ROOTED or
+ * PM_PLANS_FREE forces set-operation plans for every pattern.  Scratch:
+ * 4 bytes per CSR entry, and for the 4-cycle based patterns (path P5,
+ * banner, house, 5-cycle) 8 bytes per vertex per resident block of the
+ * 2-path kernel (at most 2 per SM). */
+#define PM_PLANS_DECOMP 3
 pm_status pm_plan_select(pm_query_plan *p, int32_t family);
 /* How a plan's set-operation plans are launched.  PM_LAUNCH_PER_PATTERN
  * (default): one launch sequence (both matching passes and the piece scan)
@@ -188,7 +203,8 @@ pm_status pm_plan_set_launch(pm_query_plan *p, int32_t mode);
  * pm_support): for each matched pattern not yet decided on this graph, time
  * its rooted and free plans on the same sample of about 4096 task chunks and
  * keep the faster; decisions are cached on the graph.  families (nullable):
- * n_matched entries receiving PM_PLANS_ROOTED or PM_PLANS_FREE. */
+ * n_matched entries receiving PM_PLANS_ROOTED, PM_PLANS_FREE or (counting
+ * plans, unless a set-operation family is forced) PM_PLANS_DECOMP. */
 pm_status pm_plan_autotune(pm_query_plan *p, void *stream, int32_t *families);
 /* Copy the compiled plans of one family (PM_PLANS_ROOTED: n_kernels_plans
  * records; PM_PLANS_FREE: n_matched records) into out (cap bytes).  A record
@@ -263,6 +279,10 @@ pm_status pm_plan_last_kernel_ms(const pm_query_plan *p, float *ms);
  * (n_matched entries), 0 for patterns that did not run on their own
  * (single-launch mode, pm_count_roots, pm_count_instrumented). */
 pm_status pm_plan_pattern_ms(const pm_query_plan *p, float *ms);
+/* Number of the library's kernels launched by the plan's last pm_count
+ * (or pm_count_each, or captured into its CUDA graph), counting the arming
+ * and gate kernels. */
+pm_status pm_plan_last_launches(const pm_query_plan *p, int64_t *launches);
 
 /* MNI support (Section 2, FSM; Theorem 3.2 with MNI tables for morphed
  * plans) of every query of a PM_OP_SUPPORT plan: one column per orbit of the

@@ -22,7 +22,7 @@ EDGE_INDUCED, VERTEX_INDUCED = 0, 1
 OP_COUNT, OP_SUPPORT = 0, 1
 MORPH_NONE, MORPH_NAIVE, MORPH_COST = 0, 1, 2
 MAX_K = 8
-PLANS_AUTO, PLANS_ROOTED, PLANS_FREE, PLANS_QUICK = -1, 0, 1, 2
+PLANS_AUTO, PLANS_ROOTED, PLANS_FREE, PLANS_QUICK, PLANS_DECOMP = -1, 0, 1, 2, 3
 LAUNCH_PER_PATTERN, LAUNCH_SINGLE = 0, 1
 
 
@@ -105,6 +105,7 @@ def _load():
         "pm_count_instrumented": [vp, vp, vp, vp],
         "pm_plan_last_kernel_ms": [vp, ctypes.POINTER(ctypes.c_float)],
         "pm_plan_pattern_ms": [vp, vp],
+        "pm_plan_last_launches": [vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -134,7 +135,7 @@ ABI_SYMBOLS = [
     "pm_plan_autotune", "pm_count_c4_noalloc", "pm_fsm", "pm_plan_capture",
     "pm_server_create", "pm_server_submit", "pm_server_wait", "pm_server_get_stats",
     "pm_server_destroy", "pm_plan_set_launch", "pm_count_each", "pm_plan_query_columns",
-    "pm_plan_pattern_ms",
+    "pm_plan_pattern_ms", "pm_plan_last_launches",
 ]
 
 
@@ -372,6 +373,12 @@ class Plan:
         v = ctypes.c_float()
         _check(_lib.pm_plan_last_kernel_ms(self._h, ctypes.byref(v)), "pm_plan_last_kernel_ms")
         return float(v.value)
+
+    def last_launches(self):
+        """Library kernels launched by the last count()."""
+        v = np.zeros(1, dtype=np.int64)
+        _check(_lib.pm_plan_last_launches(self._h, _ptr(v)), "pm_plan_last_launches")
+        return int(v[0])
 
     def pattern_ms(self):
         """Device time of each matched pattern in the last count() (per-pattern launches)."""

@@ -114,6 +114,7 @@ struct pm_query_plan {
     // pm_count (per-pattern launch mode), and whether they were recorded
     std::vector<cudaEvent_t> pat_ev;
     std::vector<char> pat_recorded;
+    int64_t launches = 0;                    // library kernels launched by the last count
     unsigned long long *d_stats = nullptr;
     uint8_t *d_timed_out = nullptr;          // pm_count_each: expired matched patterns
     uint32_t *d_wedge = nullptr;             // wedge-kernel counters: blocks x n, kept zero
@@ -127,6 +128,20 @@ struct pm_query_plan {
     size_t bytes_counters = 0, bytes_bitsets = 0, bytes_cols = 0, bytes_wedge = 0, bytes_spill = 0;
     bool spill_ready = false;
     bool device_ready = false;
+    // decomposition kernels (decomp.cu): formula of each matched pattern
+    // (-1: none), the active (formula, counter) pairs and their passes
+    std::vector<int> decomp_f;
+    std::vector<int32_t> decomp_targets;
+    int decomp_passes_active = 0;
+    int32_t *d_targets = nullptr;
+    size_t bytes_targets = 0;
+    int32_t *d_tslot = nullptr;              // triangle count per CSR slot
+    size_t bytes_tslot = 0;
+    uint32_t *d_dW = nullptr;                // 2-path counters (path blocks x n, kept zero)
+    int32_t *d_dtouched = nullptr;
+    size_t bytes_dW = 0;
+    int dpath_blocks = 0;
+    uint64_t *d_basis = nullptr;
     // CUDA graph of a whole pm_count (pm_plan_capture): replayed by pm_count
     cudaGraphExec_t graph_exec = nullptr;
     uint64_t *h_pinned = nullptr;            // counters (2 per matched) then the Control block
@@ -239,6 +254,19 @@ void free_plan_device(pm_query_plan *p) {
     p->d_spill = nullptr;
     p->bytes_spill = 0;
     p->spill_ready = false;
+    dev_free(p->d_targets, p->bytes_targets, dev);
+    dev_free(p->d_tslot, p->bytes_tslot, dev);
+    dev_free(p->d_dW, p->bytes_dW, dev);
+    dev_free(p->d_dtouched, p->bytes_dW, dev);
+    dev_free(p->d_basis, sizeof(uint64_t) * 2 * DB_COUNT, dev);
+    p->d_targets = nullptr;
+    p->bytes_targets = 0;
+    p->d_tslot = nullptr;
+    p->bytes_tslot = 0;
+    p->d_dW = nullptr;
+    p->d_dtouched = nullptr;
+    p->bytes_dW = 0;
+    p->d_basis = nullptr;
     dev_free(p->d_defer, sizeof(Deferred) * std::max<uint32_t>(p->defer_cap, 1), dev);
     dev_free(p->d_piece_off, sizeof(uint32_t) * std::max<uint32_t>(p->defer_cap, 1), dev);
     p->d_counters = nullptr;
@@ -441,13 +469,60 @@ pm_status ensure_clique(pm_query_plan *p) {
     return PM_OK;
 }
 
+// Scratch of the decomposition kernels for the active passes: the sums, the
+// per-slot triangle counts and, for 2-path passes, per-block counters
+// (zeroed once; the kernel leaves them zero) and touched lists.
+pm_status ensure_decomp(pm_query_plan *p, cudaStream_t s) {
+    const pm_graph *g = p->g;
+    const int passes = p->decomp_passes_active;
+    if (!p->d_basis) {
+        p->d_basis = (uint64_t *)dev_alloc(sizeof(uint64_t) * 2 * DB_COUNT, g->device);
+        if (!p->d_basis) {
+            set_error("device allocation failed (decomposition sums)");
+            return PM_ENOMEM;
+        }
+    }
+    if (!p->d_tslot) {
+        p->bytes_tslot = sizeof(int32_t) * size_t(std::max<int64_t>(2 * g->m, 1));
+        p->d_tslot = (int32_t *)dev_alloc(p->bytes_tslot, g->device);
+        if (!p->d_tslot) {
+            p->bytes_tslot = 0;
+            set_error("device allocation failed (triangle counts per edge)");
+            return PM_ENOMEM;
+        }
+    }
+    if ((passes & DP_PATHS) && !p->d_dW) {
+        p->dpath_blocks = decomp_path_blocks(g->device);
+        p->bytes_dW = sizeof(uint32_t) * size_t(g->n) * size_t(p->dpath_blocks);
+        p->d_dW = (uint32_t *)dev_alloc(p->bytes_dW, g->device);
+        p->d_dtouched = (int32_t *)dev_alloc(p->bytes_dW, g->device);
+        if (!p->d_dW || !p->d_dtouched) {
+            dev_free(p->d_dW, p->bytes_dW, g->device);
+            dev_free(p->d_dtouched, p->bytes_dW, g->device);
+            p->d_dW = nullptr;
+            p->d_dtouched = nullptr;
+            p->bytes_dW = 0;
+            set_error("device allocation failed (2-path counters)");
+            return PM_ENOMEM;
+        }
+        cudaError_t e = cudaMemsetAsync(p->d_dW, 0, p->bytes_dW, s);
+        if (e) return cuda_fail("2-path counters", e);
+    }
+    if (passes & DP_CLIQUE) {
+        pm_status st = ensure_clique(p);
+        if (st != PM_OK) return st;
+    }
+    return PM_OK;
+}
+
 // Launch both matching passes for one plan table on the given tasks.
 // gate_budget_ns > 0 (with gate_flags): every matched pattern gets its own
 // deadline and its expiry is flagged per pattern (pm_count_each).
 pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tasks,
                        int sample_stride, bool domains, unsigned long long *stats,
                        cudaStream_t s, uint64_t gate_budget_ns = 0,
-                       uint8_t *gate_flags = nullptr, bool record = false) {
+                       uint8_t *gate_flags = nullptr, bool record = false,
+                       bool with_decomp = false) {
     // events around each matched pattern's launches (per-pattern mode only)
     if (record) std::fill(p->pat_recorded.begin(), p->pat_recorded.end(), 0);
     auto mark = [&](int counter, int end) {
@@ -488,13 +563,15 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
             G.max_enum = 2;
             for (const DevPlan &dp : sub) G.max_enum = std::max(G.max_enum, int(dp.n_enum));
             if (gate_flags) {
+                p->launches++;
                 if (launch_pattern_gate(p->d_ctl, gate_flags, b > 0 ? t.plans[b - 1].counter : -1,
                                         gate_budget_ns, s))
                     return PM_ECUDA;
-            } else if (b > 0 && launch_rearm(p->d_ctl, s)) {
+            } else if (b > 0 && (p->launches++, launch_rearm(p->d_ctl, s))) {
                 return PM_ECUDA;
             }
             mark(t.plans[b].counter, 0);
+            p->launches += 3;
             const int rc = domains ? launch_domains(G, s) : launch_count(G, s);
             if (rc) return PM_ECUDA;
             mark(t.plans[b].counter, 1);
@@ -502,6 +579,7 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
         }
     } else if (n_setops > 0 && L.n_echunks > 0) {
         L.nplans = n_setops;
+        p->launches += 3;
         const int rc = domains ? launch_domains(L, s) : launch_count(L, s);
         if (rc) return PM_ECUDA;
     }
@@ -514,9 +592,12 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
         }
         pm_status st = dp.kind == PLAN_WEDGE_PAIRS ? ensure_wedge(p, s) : ensure_clique(p);
         if (st != PM_OK) return st;
-        if (gate_flags && launch_pattern_gate(p->d_ctl, gate_flags, last, gate_budget_ns, s))
+        if (gate_flags && (p->launches++, launch_pattern_gate(p->d_ctl, gate_flags, last, gate_budget_ns, s)))
             return PM_ECUDA;
         mark(dp.counter, 0);
+        p->launches += dp.kind == PLAN_WEDGE_PAIRS
+                           ? int(p->heavy_from < L.g.n) + int(p->heavy_from > 0)
+                           : 1;
         if (dp.kind == PLAN_WEDGE_PAIRS) {
             if (launch_wedge_pairs(L.g, tasks, p->heavy_from, dp.counter, p->d_counters, p->d_wedge,
                                    p->d_lists, p->list_cap, p->wedge_nblocks, sample_stride,
@@ -529,7 +610,41 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
         mark(dp.counter, 1);
         last = dp.counter;
     }
-    if (gate_flags && last >= 0 && launch_pattern_gate(p->d_ctl, gate_flags, last, 0, s))
+    if (with_decomp && !p->decomp_targets.empty()) {
+        // the decomposable patterns together: the passes they need, then
+        // one combine writing each one's count (timed as one group, on the
+        // first of them)
+        pm_status st = ensure_decomp(p, s);
+        if (st != PM_OK) return st;
+        if (gate_flags && (p->launches++, launch_pattern_gate(p->d_ctl, gate_flags, last, gate_budget_ns, s)))
+            return PM_ECUDA;
+        const int first = p->decomp_targets[1];
+        const int nt = int(p->decomp_targets.size() / 2);
+        mark(first, 0);
+        DecompLaunch D{};
+        D.g = L.g;
+        D.tasks = tasks;
+        D.passes = p->decomp_passes_active;
+        D.t = p->d_tslot;
+        D.W = p->d_dW;
+        D.touched = p->d_dtouched;
+        D.path_blocks = p->dpath_blocks;
+        D.basis = p->d_basis;
+        D.ctl = p->d_ctl;
+        p->launches += 3 + int((D.passes & DP_TRI2) != 0) + int((D.passes & DP_PATHS) != 0) +
+                       int((D.passes & DP_CLIQUE) != 0) + 1;
+        if (launch_decomp(D, s)) return PM_ECUDA;
+        if ((D.passes & DP_CLIQUE) &&
+            launch_clique(L.g, tasks, 4, DB_K4, p->d_basis, p->d_spill, p->spill_len, 1, p->d_ctl,
+                          nullptr, s, p->d_basis + 2 * DB_K4DEG))
+            return PM_ECUDA;
+        if (launch_decomp_combine(p->d_basis, p->d_targets, nt, p->d_counters, s)) return PM_ECUDA;
+        mark(first, 1);
+        if (gate_flags && (p->launches++, launch_flag_targets(p->d_ctl, gate_flags, p->d_targets, nt, s)))
+            return PM_ECUDA;
+        last = -1;
+    }
+    if (gate_flags && last >= 0 && (p->launches++, launch_pattern_gate(p->d_ctl, gate_flags, last, 0, s)))
         return PM_ECUDA;
     return PM_OK;
 }
@@ -537,6 +652,7 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
 // After an expired deadline the wedge counters may be left non-zero.
 void rezero_wedge(pm_query_plan *p, cudaStream_t s) {
     if (p->d_wedge) cudaMemsetAsync(p->d_wedge, 0, p->bytes_wedge, s);
+    if (p->d_dW) cudaMemsetAsync(p->d_dW, 0, p->bytes_dW, s);
 }
 
 // The plans of matched pattern j in family f (0 rooted, 1 free).
@@ -544,6 +660,14 @@ std::vector<DevPlan> family_plans(const pm_query_plan *p, size_t j, int f) {
     if (f == PM_PLANS_FREE) return {p->free_plans[j]};
     return std::vector<DevPlan>(p->rooted.begin() + p->rooted_begin[j],
                                 p->rooted.begin() + p->rooted_begin[j + 1]);
+}
+
+// Decomposable patterns of counting plans use the decomposition kernels
+// unless a set-operation family is forced.
+bool decomp_default(const pm_query_plan *p, size_t j) {
+    return p->op == PM_OP_COUNT && p->decomp_f[j] >= 0 &&
+           (p->forced == PM_PLANS_AUTO || p->forced == PM_PLANS_QUICK ||
+            p->forced == PM_PLANS_DECOMP);
 }
 
 // Autotuner: for every matched pattern without a decision, time its rooted
@@ -556,6 +680,10 @@ pm_status autotune(pm_query_plan *p, cudaStream_t s) {
     const size_t nm = p->morph.matched.size();
     for (size_t j = 0; j < nm; j++) {
         if (p->choice[j] >= 0) continue;
+        if (decomp_default(p, j)) {
+            p->choice[j] = PM_PLANS_DECOMP;   // per plan: the decision depends on the operation
+            continue;
+        }
         const Key key = canonical(p->morph.matched[j]);
         {
             std::lock_guard<std::mutex> lk(g->tune_mu);
@@ -618,13 +746,15 @@ pm_status prepare_active(pm_query_plan *p, cudaStream_t s) {
     const size_t nm = p->morph.matched.size();
     std::vector<int> want(nm);
     if (p->forced == PM_PLANS_QUICK) {
-        // no timing: the rooted family where it runs the wedge kernel, else free
+        // no timing: decomposition where it applies, the rooted family where
+        // it runs the wedge kernel, else free
         for (size_t j = 0; j < nm; j++) {
             const bool wedge = p->rooted_begin[j + 1] - p->rooted_begin[j] == 1 &&
                                p->rooted[p->rooted_begin[j]].kind == PLAN_WEDGE_PAIRS;
-            want[j] = wedge ? PM_PLANS_ROOTED : PM_PLANS_FREE;
+            want[j] = decomp_default(p, j) ? PM_PLANS_DECOMP
+                                            : (wedge ? PM_PLANS_ROOTED : PM_PLANS_FREE);
         }
-    } else if (p->forced >= 0) {
+    } else if (p->forced == PM_PLANS_ROOTED || p->forced == PM_PLANS_FREE) {
         std::fill(want.begin(), want.end(), p->forced);
     } else {
         pm_status st = autotune(p, s);
@@ -632,10 +762,37 @@ pm_status prepare_active(pm_query_plan *p, cudaStream_t s) {
         want = p->choice;
     }
     std::vector<DevPlan> plans;
+    std::vector<int32_t> targets;
+    int passes = 0;
     for (size_t j = 0; j < nm; j++) {
+        if (want[j] == PM_PLANS_DECOMP) {
+            targets.push_back(p->decomp_f[j]);
+            targets.push_back(int32_t(j));
+            passes |= decomp_passes(p->decomp_f[j]);
+            continue;
+        }
         std::vector<DevPlan> v = family_plans(p, j, want[j]);
         plans.insert(plans.end(), v.begin(), v.end());
     }
+    if (targets != p->decomp_targets || !p->d_targets) {
+        const size_t bytes = sizeof(int32_t) * std::max<size_t>(targets.size(), 2);
+        if (bytes > p->bytes_targets) {
+            dev_free(p->d_targets, p->bytes_targets, p->g->device);
+            p->d_targets = (int32_t *)dev_alloc(bytes, p->g->device);
+            p->bytes_targets = p->d_targets ? bytes : 0;
+            if (!p->d_targets) {
+                set_error("device allocation failed (decomposition targets)");
+                return PM_ENOMEM;
+            }
+        }
+        if (!targets.empty()) {
+            cudaError_t e = cudaMemcpy(p->d_targets, targets.data(), sizeof(int32_t) * targets.size(),
+                                       cudaMemcpyHostToDevice);
+            if (e) return cuda_fail("decomposition targets upload", e);
+        }
+        p->decomp_targets = targets;
+    }
+    p->decomp_passes_active = passes;
     std::stable_partition(plans.begin(), plans.end(),
                           [](const DevPlan &dp) { return dp.kind == PLAN_SETOPS; });
     if (p->active.plans.size() != plans.size() ||
@@ -650,6 +807,34 @@ pm_status prepare_active(pm_query_plan *p, cudaStream_t s) {
 // the autotuner's sampled time of its faster plan family (cached per graph);
 // a pattern whose sampled runs both hit the deadline costs 1e9 ms.
 double pattern_cost(const pm_graph *g, const Pat &q) {
+    const int f = decomp_formula(q);
+    if (f >= 0) {
+        // the decomposition passes this pattern needs, timed once per graph
+        const int passes = decomp_passes(f);
+        {
+            std::lock_guard<std::mutex> lk(g->tune_mu);
+            auto it = g->decomp_ms.find(passes);
+            if (it != g->decomp_ms.end()) return it->second;
+        }
+        pm_pattern r{};
+        r.k = q.k;
+        r.edge_mask = q.mask();
+        for (int u = 0; u < PM_MAX_K; u++) r.label[u] = -1;
+        r.induced = PM_EDGE_INDUCED;
+        pm_query_plan *tmp = nullptr;
+        double ms = 1e9;
+        if (pm_plan(g, &r, 1, PM_OP_COUNT, PM_MORPH_NONE, &tmp) == PM_OK) {
+            uint64_t c[2];
+            float t = 0.f;
+            if (pm_count(tmp, nullptr, 10.0, c, nullptr) == PM_OK &&
+                pm_plan_pattern_ms(tmp, &t) == PM_OK)
+                ms = t;
+            pm_free_plan(tmp);
+        }
+        std::lock_guard<std::mutex> lk(g->tune_mu);
+        g->decomp_ms[passes] = ms;
+        return ms;
+    }
     const Key key = canonical(q);
     {
         std::lock_guard<std::mutex> lk(g->tune_mu);
@@ -713,6 +898,7 @@ pm_status run_count(pm_query_plan *p, void *stream, double timeout_s, const int3
     cudaError_t e = cudaMemsetAsync(p->d_counters, 0, p->bytes_counters, s);
     if (e) return cuda_fail("pm_count: memset", e);
     const uint64_t budget = timeout_s > 0 ? uint64_t(timeout_s * 1e9) : 0;
+    p->launches = 1;
     if (launch_arm(p->d_ctl, budget, s)) return PM_ECUDA;
     if (alg_bytes && !p->d_stats) {
         p->d_stats = (unsigned long long *)dev_alloc(256, g->device);
@@ -724,7 +910,7 @@ pm_status run_count(pm_query_plan *p, void *stream, double timeout_s, const int3
     }
     cudaEventRecord(p->ev0, s);
     st = launch_table(p, *table, tasks, 1, false, alg_bytes ? p->d_stats : nullptr, s, 0, nullptr,
-                      !use_roots && !alg_bytes);
+                      !use_roots && !alg_bytes, !use_roots);
     if (st != PM_OK) return st;
     cudaEventRecord(p->ev1, s);
     p->timed = true;
@@ -784,13 +970,14 @@ pm_status run_count_each(pm_query_plan *p, void *stream, double timeout_s, doubl
         return cuda_fail("pm_count_each: memset", e);
     }
     const uint64_t budget = timeout_s > 0 ? uint64_t(timeout_s * 1e9) : 0;
+    p->launches = 1;
     if (launch_arm(p->d_ctl, total_s > 0 ? uint64_t(total_s * 1e9) : 0, s)) {
         p->launch_mode = saved_mode;
         return PM_ECUDA;
     }
     cudaEventRecord(p->ev0, s);
     st = launch_table(p, p->active, all_tasks(g), 1, false, nullptr, s, budget,
-                      p->d_timed_out);
+                      p->d_timed_out, false, true);
     p->launch_mode = saved_mode;
     if (st != PM_OK) return st;
     cudaEventRecord(p->ev1, s);
@@ -961,6 +1148,9 @@ pm_status pm_plan(const pm_graph *g, const pm_pattern *queries, int32_t nq, pm_o
                                                   p->morph.matched_orbit[j], op == PM_OP_COUNT));
     }
     p->choice.assign(nm, -1);
+    p->decomp_f.assign(nm, -1);
+    if (op == PM_OP_COUNT)
+        for (size_t j = 0; j < nm; j++) p->decomp_f[j] = decomp_formula(p->morph.matched[j]);
     if (op == PM_OP_SUPPORT) {
         // query columns -> bitset sources
         p->col_off.push_back(0);
@@ -1024,8 +1214,9 @@ pm_status pm_plan_set_launch(pm_query_plan *p, int32_t mode) {
 }
 
 pm_status pm_plan_select(pm_query_plan *p, int32_t family) {
-    if (!p || family < PM_PLANS_AUTO || family > PM_PLANS_QUICK) return PM_EINVAL;
+    if (!p || family < PM_PLANS_AUTO || family > PM_PLANS_DECOMP) return PM_EINVAL;
     p->forced = family;
+    std::fill(p->choice.begin(), p->choice.end(), -1);
     return PM_OK;
 }
 
@@ -1052,6 +1243,12 @@ pm_status pm_plan_last_kernel_ms(const pm_query_plan *p, float *ms) {
     if (!p->timed) return PM_OK;
     cudaError_t e = cudaEventElapsedTime(ms, p->ev0, p->ev1);
     if (e) return cuda_fail("pm_plan_last_kernel_ms", e);
+    return PM_OK;
+}
+
+pm_status pm_plan_last_launches(const pm_query_plan *p, int64_t *launches) {
+    if (!p || !launches) return PM_EINVAL;
+    *launches = p->launches;
     return PM_OK;
 }
 
@@ -1153,6 +1350,10 @@ pm_status pm_plan_capture(pm_query_plan *p, void *stream, double timeout_s) {
         st = ensure_clique(p);
         if (st != PM_OK) return st;
     }
+    if (!p->decomp_targets.empty()) {
+        st = ensure_decomp(p, user);
+        if (st != PM_OK) return st;
+    }
     const size_t nm = p->morph.matched.size();
     if (!p->h_pinned) {
         cudaError_t e = cudaMallocHost(&p->h_pinned, sizeof(uint64_t) * 2 * nm + sizeof(Control));
@@ -1169,9 +1370,10 @@ pm_status pm_plan_capture(pm_query_plan *p, void *stream, double timeout_s) {
         const DevTasks tasks = all_tasks(g);
         cudaMemsetAsync(p->d_counters, 0, p->bytes_counters, cs);
         const uint64_t budget = timeout_s > 0 ? uint64_t(timeout_s * 1e9) : 0;
+        p->launches = 1;
         launch_arm(p->d_ctl, budget, cs);
         cudaEventRecord(p->ev0, cs);
-        st = launch_table(p, p->active, tasks, 1, false, nullptr, cs, 0, nullptr, true);
+        st = launch_table(p, p->active, tasks, 1, false, nullptr, cs, 0, nullptr, true, true);
         cudaEventRecord(p->ev1, cs);
         cudaMemcpyAsync(p->h_pinned, p->d_counters, sizeof(uint64_t) * 2 * nm,
                         cudaMemcpyDeviceToHost, cs);

@@ -45,6 +45,7 @@ struct CliqueArgs {
     int64_t spill_len;
     unsigned long long *stats;
     int32_t balanced;            // 1: strided chunks, weighted sides, per-task deadline checks
+    uint64_t *deg_out;           // K4 only, nullable: 128-bit sum over 4-cliques of their degrees
 };
 
 // First index in s[0, len) whose value is >= key; s is written by this
@@ -93,9 +94,9 @@ constexpr int32_t CQ_TEST_ALWAYS = 24;
 
 // Edges inside the sorted set S[0, s): this lane's share of
 // sum over i of |S[0, i) n N(S[i])|.
-template <bool STATS>
+template <bool STATS, bool DEG = false>
 __device__ uint64_t edges_within(const DevGraph &g, const int32_t *S, int32_t s, int lane,
-                                 uint64_t &stat, bool weighted) {
+                                 uint64_t &stat, bool weighted, uint64_t *dsum = nullptr) {
     uint64_t hits = 0;
     if (s < 2) return 0;
     const int32_t s0 = S[0];
@@ -142,14 +143,20 @@ __device__ uint64_t edges_within(const DevGraph &g, const int32_t *S, int32_t s,
             if (t < total) {
                 const int32_t j = t - eo;
                 bool hit;
+                int32_t y;
                 if (!wo) {
-                    hit = contains(g, xo, S[j]);
+                    y = S[j];
+                    hit = contains(g, xo, y);
                 } else {
-                    const int32_t y = __ldg(g.col + so + j);
+                    y = __ldg(g.col + so + j);
                     const int32_t p = lower_bound_set(S, io, y);
                     hit = p < io && S[p] == y;
                 }
                 hits += hit ? 1 : 0;
+                // DEG: the degrees of both endpoints of every edge found
+                if (DEG && hit)
+                    *dsum += uint64_t(__ldg(g.rowptr + xo + 1) - __ldg(g.rowptr + xo)) +
+                             uint64_t(__ldg(g.rowptr + y + 1) - __ldg(g.rowptr + y));
             }
         }
     }
@@ -208,7 +215,7 @@ __device__ __forceinline__ bool cq_stop(Control *ctl, uint64_t deadline, int lan
     return __shfl_sync(FULL, stop, 0) != 0;
 }
 
-template <bool STATS>
+template <bool STATS, bool DEG>
 __global__ void __launch_bounds__(CQ_WARPS * 32)
 clique_kernel(CliqueArgs A) {
     extern __shared__ __align__(16) int32_t cq_smem[];
@@ -231,6 +238,7 @@ clique_kernel(CliqueArgs A) {
     const unsigned long long n_chunks = (unsigned long long)((ntasks + 31) / 32);
     const unsigned long long n_sampled = (n_chunks + stride - 1) / stride;
     uint64_t hits = 0, stat = 0;
+    u128 degsum = 0;
     bool alive = true;
     while (alive) {
         unsigned long long w = 0;
@@ -295,7 +303,16 @@ clique_kernel(CliqueArgs A) {
             }
             __syncwarp();
             if (A.k == 4) {
-                hits += edges_within<STATS>(g, S, s, lane, stat, A.balanced != 0);
+                if (DEG) {
+                    uint64_t ds = 0;
+                    const uint64_t h = edges_within<STATS, true>(g, S, s, lane, stat, A.balanced != 0, &ds);
+                    hits += h;
+                    const uint64_t dab = uint64_t(__ldg(g.rowptr + ra + 1) - rowa) +
+                                         uint64_t(__ldg(g.rowptr + rb + 1) - rowb);
+                    degsum += u128(h) * dab + ds;
+                } else {
+                    hits += edges_within<STATS>(g, S, s, lane, stat, A.balanced != 0);
+                }
                 continue;
             }
             for (int32_t i = 2; i < s; i++) {
@@ -318,6 +335,15 @@ clique_kernel(CliqueArgs A) {
         acc += (u128(hi) << 64) | lo;
     }
     if (lane == 0 && acc != 0) add_u128(A.counters + 2 * int64_t(A.counter), acc);
+    if (DEG) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t lo = __shfl_xor_sync(FULL, uint64_t(degsum), o);
+            const uint64_t hi = __shfl_xor_sync(FULL, uint64_t(degsum >> 64), o);
+            degsum += (u128(hi) << 64) | lo;
+        }
+        if (lane == 0 && degsum != 0) add_u128(A.deg_out, degsum);
+    }
     if (STATS) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) stat += __shfl_xor_sync(FULL, stat, o);
@@ -329,9 +355,9 @@ static size_t clique_smem(int k) {
     return size_t(CQ_WARPS) * (k == 5 ? 2 : 1) * CQ_CAP * sizeof(int32_t);
 }
 
-template <bool STATS>
+template <bool STATS, bool DEG = false>
 static int clique_blocks_for(int device, int k) {
-    auto kern = clique_kernel<STATS>;
+    auto kern = clique_kernel<STATS, DEG>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(clique_smem(5)));
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CQ_WARPS * 32, clique_smem(k));
@@ -344,6 +370,7 @@ int64_t clique_warps(int device) {
     for (int k = 4; k <= 5; k++) {
         most = std::max(most, clique_blocks_for<false>(device, k));
         most = std::max(most, clique_blocks_for<true>(device, k));
+        most = std::max(most, clique_blocks_for<false, true>(device, k));
     }
     return int64_t(most) * CQ_WARPS;
 }
@@ -352,7 +379,7 @@ int64_t clique_spill_len(int64_t max_degree) { return max_degree > CQ_CAP ? max_
 
 int launch_clique(const DevGraph &g, const DevTasks &tasks, int k, int counter,
                   uint64_t *counters, int32_t *spill, int64_t spill_len, int sample_stride,
-                  Control *ctl, unsigned long long *stats, void *stream) {
+                  Control *ctl, unsigned long long *stats, void *stream, uint64_t *deg_out) {
     int device = 0;
     cudaGetDevice(&device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -367,17 +394,21 @@ int launch_clique(const DevGraph &g, const DevTasks &tasks, int k, int counter,
     A.spill = spill;
     A.spill_len = spill_len;
     A.stats = stats;
+    A.deg_out = deg_out;
     // balanced scheduling is opt-in until it has been timed against the
     // plain one (PM_CLIQUE_BALANCED=1)
     const char *bal = std::getenv("PM_CLIQUE_BALANCED");
     A.balanced = (bal && bal[0] == '1') ? 1 : 0;
     cudaMemsetAsync(&ctl->work3, 0, sizeof(unsigned long long), s);
-    if (stats) {
+    if (deg_out && k == 4) {
+        const int blocks = clique_blocks_for<false, true>(device, k);
+        clique_kernel<false, true><<<blocks, CQ_WARPS * 32, clique_smem(k), s>>>(A);
+    } else if (stats) {
         const int blocks = clique_blocks_for<true>(device, k);
-        clique_kernel<true><<<blocks, CQ_WARPS * 32, clique_smem(k), s>>>(A);
+        clique_kernel<true, false><<<blocks, CQ_WARPS * 32, clique_smem(k), s>>>(A);
     } else {
         const int blocks = clique_blocks_for<false>(device, k);
-        clique_kernel<false><<<blocks, CQ_WARPS * 32, clique_smem(k), s>>>(A);
+        clique_kernel<false, false><<<blocks, CQ_WARPS * 32, clique_smem(k), s>>>(A);
     }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) {

@@ -40,6 +40,7 @@ struct pm_graph {
     mutable std::mutex tune_mu;
     mutable std::map<pm::Key, int> tuned;
     mutable std::map<pm::Key, double> tuned_ms;   // sampled time of the chosen family
+    mutable std::map<int, double> decomp_ms;      // decomposition time per pass set
     pm::DevGraph dev() const {
         return pm::DevGraph{n, 2 * m, d_rowptr, d_col, d_labels,
                             n_hubs ? d_hub : nullptr, d_bits, hub_words};
@@ -141,7 +142,47 @@ int64_t clique_warps(int device);
 int64_t clique_spill_len(int64_t max_degree);
 int launch_clique(const DevGraph &g, const DevTasks &tasks, int k, int counter,
                   uint64_t *counters, int32_t *spill, int64_t spill_len, int sample_stride,
-                  Control *ctl, unsigned long long *stats, void *stream);
+                  Control *ctl, unsigned long long *stats, void *stream,
+                  uint64_t *deg_out = nullptr);
+
+// Edge-induced counts from local statistics (decomp.cu).  Sums (128-bit,
+// 2 words each, DB_COUNT entries) accumulated by the passes:
+enum DecompSum : int {
+    DB_TRI, DB_K4, DB_K4DEG, DB_DE, DB_C4,
+    DB_STAR3, DB_STAR4, DB_P4E, DB_TX3, DB_PAW, DB_FORK, DB_P5A, DB_TVD, DB_CRICKET,
+    DB_LOLLI_V, DB_BOWTIE_V, DB_BULL, DB_LOLLI_E, DB_KITE, DB_DART_E, DB_BOOK,
+    DB_C5TRI, DB_DART_TRI, DB_GEM_TRI, DB_BANNER2, DB_HOUSE, DB_C5Q, DB_C5CORR, DB_C5TM,
+    DB_K23I, DB_COUNT
+};
+// The patterns counted this way (unlabeled, edge-induced).
+enum DecompFormula : int {
+    DF_STAR3, DF_P4, DF_PAW, DF_DIAMOND,                       // 4 vertices
+    DF_STAR4, DF_FORK, DF_P5, DF_CRICKET, DF_BULL, DF_LOLLIPOP, DF_BANNER, DF_C5, DF_KITE,
+    DF_DART, DF_BOWTIE, DF_HOUSE, DF_BOOK, DF_GEM, DF_K4PENDANT,   // 5 vertices
+    DF_COUNT
+};
+// Passes beyond triangle pass 1, the mirror and the vertex/edge pass.
+enum DecompPass : int { DP_TRI2 = 1, DP_PATHS = 2, DP_C5 = 4, DP_CLIQUE = 8 };
+// formula of an unlabeled edge-induced pattern, or -1 (morph.cpp)
+int decomp_formula(const Pat &p);
+int decomp_passes(int formula);
+struct DecompLaunch {
+    DevGraph g;
+    DevTasks tasks;           // lower-neighbour tasks over every root
+    int passes;
+    int32_t *t;               // one int32 per CSR slot
+    uint32_t *W;              // path_blocks x n (zero on entry and exit)
+    int32_t *touched;         // path_blocks x n
+    int path_blocks;
+    uint64_t *basis;          // 2 x DB_COUNT words
+    Control *ctl;
+};
+int decomp_path_blocks(int device);
+int launch_decomp(const DecompLaunch &L, void *stream);
+int launch_flag_targets(Control *ctl, uint8_t *timed_out, const int32_t *targets, int n_targets,
+                        void *stream);
+int launch_decomp_combine(const uint64_t *basis, const int32_t *targets, int n_targets,
+                          uint64_t *counters, void *stream);
 int launch_mni_reduce(const uint32_t *d_bitsets, int64_t words_per_bitset, const int32_t *d_src_off,
                       const int32_t *d_src, int n_columns, unsigned long long *d_popc,
                       void *stream);

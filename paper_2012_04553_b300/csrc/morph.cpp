@@ -465,4 +465,37 @@ DevPlan compile_free_plan(const Pat &p, int counter, int dom_base,
                       column_of_vertex, counting);
 }
 
+// Patterns whose edge-induced count the decomposition kernels produce
+// (decomp.cu), by canonical class: the representative edge masks in
+// lexicographic pair order.
+int decomp_formula(const Pat &p) {
+    if ((p.vi && !p.is_clique()) || p.labeled() || (p.k != 4 && p.k != 5)) return -1;
+    static const std::map<Key, int> table = [] {
+        const int8_t none[KMAX] = {-1, -1, -1, -1, -1, -1, -1, -1};
+        const struct { int k; uint32_t mask; int f; } rows[] = {
+            {4, 7, DF_STAR3}, {4, 13, DF_P4}, {4, 15, DF_PAW}, {4, 31, DF_DIAMOND},
+            {5, 15, DF_STAR4}, {5, 29, DF_FORK}, {5, 58, DF_P5}, {5, 31, DF_CRICKET},
+            {5, 59, DF_BULL}, {5, 185, DF_LOLLIPOP}, {5, 62, DF_BANNER}, {5, 220, DF_C5},
+            {5, 63, DF_KITE}, {5, 187, DF_DART}, {5, 207, DF_BOWTIE}, {5, 221, DF_HOUSE},
+            {5, 127, DF_BOOK}, {5, 223, DF_GEM}, {5, 191, DF_K4PENDANT}};
+        std::map<Key, int> m;
+        for (const auto &r : rows) m[canonical(Pat::from_mask(r.k, r.mask, none, false))] = r.f;
+        return m;
+    }();
+    Pat q = p;
+    q.vi = false;
+    auto it = table.find(canonical(q));
+    return it == table.end() ? -1 : it->second;
+}
+
+int decomp_passes(int f) {
+    switch (f) {
+        case DF_P5: case DF_BANNER: case DF_HOUSE: return DP_PATHS;
+        case DF_C5: return DP_PATHS | DP_C5;
+        case DF_DART: case DF_GEM: return DP_TRI2 | DP_CLIQUE;
+        case DF_K4PENDANT: return DP_CLIQUE;
+        default: return 0;
+    }
+}
+
 }  // namespace pm
