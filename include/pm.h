@@ -306,6 +306,28 @@ pm_status pm_support(pm_query_plan *p, void *stream, double timeout_s, uint64_t 
  * query i has 1 + max_u columns[i * PM_MAX_K + u] of them. */
 pm_status pm_plan_query_columns(const pm_query_plan *p, int32_t *columns);
 
+/* Sharded MNI support.  Every match has one highest-ranked vertex (rank =
+ * (degree, caller id)), so the MNI columns of a query over all matches are
+ * the union (OR) of its columns over the matches whose highest-ranked vertex
+ * lies in each part of a partition of the vertices; a process per part fills
+ * its columns with pm_support_roots, the columns are gathered, ORed with
+ * pm_domains_or, and pm_support_from_domains takes each query's smallest
+ * column.
+ * pm_support_roots: the query columns (layout of pm_support's domains_dev,
+ * device memory on the graph's device) over the matches whose highest-ranked
+ * vertex is one of the nroots caller ids in roots (rooted plans).
+ * pm_domains_or: out[w] = OR over p < n_parts of parts[p * words + w]
+ * (device memory, asynchronous on stream).
+ * pm_support_from_domains: support (n_queries words) and frequent (nullable)
+ * from a complete set of query columns.  Errors: PM_EINVAL, PM_ENOMEM,
+ * PM_ECUDA, PM_ETIMEOUT. */
+pm_status pm_support_roots(pm_query_plan *p, void *stream, double timeout_s, const int32_t *roots,
+                           int64_t nroots, uint32_t *domains_dev);
+pm_status pm_domains_or(const uint32_t *parts_dev, int32_t n_parts, int64_t words, uint32_t *out_dev,
+                        void *stream);
+pm_status pm_support_from_domains(pm_query_plan *p, const uint32_t *domains_dev, void *stream,
+                                  uint64_t threshold, uint64_t *support, uint8_t *frequent);
+
 /* Frequent subgraph mining with MNI support (Section 2, FSM), level-wise
  * up to max_edges (1..5) edges on a labeled graph.  Level 1: every labeled
  * edge whose two labels occur in the graph.  Level j+1: connected labeled

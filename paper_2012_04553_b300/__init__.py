@@ -106,6 +106,9 @@ def _load():
         "pm_plan_last_kernel_ms": [vp, ctypes.POINTER(ctypes.c_float)],
         "pm_plan_pattern_ms": [vp, vp],
         "pm_plan_last_launches": [vp, vp],
+        "pm_support_roots": [vp, vp, dbl, vp, i64, vp],
+        "pm_domains_or": [vp, i32, i64, vp, vp],
+        "pm_support_from_domains": [vp, vp, vp, ctypes.c_uint64, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -135,7 +138,8 @@ ABI_SYMBOLS = [
     "pm_plan_autotune", "pm_count_c4_noalloc", "pm_fsm", "pm_plan_capture",
     "pm_server_create", "pm_server_submit", "pm_server_wait", "pm_server_get_stats",
     "pm_server_destroy", "pm_plan_set_launch", "pm_count_each", "pm_plan_query_columns",
-    "pm_plan_pattern_ms", "pm_plan_last_launches",
+    "pm_plan_pattern_ms", "pm_plan_last_launches", "pm_support_roots", "pm_domains_or",
+    "pm_support_from_domains",
 ]
 
 
@@ -246,6 +250,18 @@ def count_c4_noalloc(rowptr, col, n, out, stream=None):
     _check(_lib.pm_count_c4_noalloc(ctypes.c_void_p(rowptr.data_ptr()), ctypes.c_void_p(col.data_ptr()),
                                     int(n), ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
            "pm_count_c4_noalloc")
+
+
+def domains_or(parts, stream=None):
+    """OR of a stack of equally shaped device bitsets (parts[0] | parts[1] | ...),
+    computed by the library (pm_domains_or)."""
+    import torch
+    parts = parts.contiguous()
+    out = torch.empty(parts.shape[1:], dtype=parts.dtype, device=parts.device)
+    words = out.numel()
+    _check(_lib.pm_domains_or(parts.data_ptr(), int(parts.shape[0]), int(words), out.data_ptr(),
+                              _stream_handle(stream)), "pm_domains_or")
+    return out
 
 
 def make_pattern(k, edge_mask, induced=EDGE_INDUCED, labels=None):
@@ -441,6 +457,31 @@ class Plan:
             per_query.append(dom[at:at + max(c) + 1])
             at += max(c) + 1
         return out + (per_query,)
+
+    def _columns_tensor(self):
+        import torch
+        total = sum(max(c) + 1 for c in self.query_columns())
+        info = self.graph.info()
+        return torch.empty((total, (info["n"] + 31) // 32), dtype=torch.int32,
+                           device=torch.device("cuda", info["device"]))
+
+    def support_roots(self, roots, stream=None, timeout_s=0.0):
+        """MNI columns (all queries, one row of ceil(n / 32) words each) over
+        the matches whose highest-ranked vertex is among `roots` (caller ids)."""
+        r = np.ascontiguousarray(roots, dtype=np.int32)
+        out = self._columns_tensor()
+        _check(_lib.pm_support_roots(self._h, _stream_handle(stream), float(timeout_s), _ptr(r), len(r),
+                                     out.data_ptr()), "pm_support_roots")
+        return out
+
+    def support_from_domains(self, columns, threshold=0, stream=None):
+        """(supports, frequent flags) from a complete set of MNI columns."""
+        sup = np.zeros(self.n_queries, dtype=np.uint64)
+        freq = np.zeros(self.n_queries, dtype=np.uint8)
+        _check(_lib.pm_support_from_domains(self._h, columns.data_ptr(), _stream_handle(stream),
+                                            int(threshold), _ptr(sup), _ptr(freq)),
+               "pm_support_from_domains")
+        return [int(x) for x in sup], [bool(x) for x in freq]
 
     def free(self):
         if self._h:

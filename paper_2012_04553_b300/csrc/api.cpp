@@ -142,6 +142,12 @@ struct pm_query_plan {
     size_t bytes_dW = 0;
     int dpath_blocks = 0;
     uint64_t *d_basis = nullptr;
+    uint32_t *d_k4e = nullptr;               // 4-cliques per edge (CSR slot of the lower endpoint)
+    size_t bytes_k4e = 0;
+    uint32_t *d_local = nullptr;             // neighbourhood bitmap overflow (large out-degrees)
+    size_t bytes_local = 0;
+    int local_blocks = 0;
+    bool local_ready = false;
     // CUDA graph of a whole pm_count (pm_plan_capture): replayed by pm_count
     cudaGraphExec_t graph_exec = nullptr;
     uint64_t *h_pinned = nullptr;            // counters (2 per matched) then the Control block
@@ -259,6 +265,13 @@ void free_plan_device(pm_query_plan *p) {
     dev_free(p->d_dW, p->bytes_dW, dev);
     dev_free(p->d_dtouched, p->bytes_dW, dev);
     dev_free(p->d_basis, sizeof(uint64_t) * 2 * DB_COUNT, dev);
+    dev_free(p->d_k4e, p->bytes_k4e, dev);
+    dev_free(p->d_local, p->bytes_local, dev);
+    p->d_k4e = nullptr;
+    p->bytes_k4e = 0;
+    p->d_local = nullptr;
+    p->bytes_local = 0;
+    p->local_ready = false;
     p->d_targets = nullptr;
     p->bytes_targets = 0;
     p->d_tslot = nullptr;
@@ -508,9 +521,31 @@ pm_status ensure_decomp(pm_query_plan *p, cudaStream_t s) {
         cudaError_t e = cudaMemsetAsync(p->d_dW, 0, p->bytes_dW, s);
         if (e) return cuda_fail("2-path counters", e);
     }
-    if (passes & DP_CLIQUE) {
-        pm_status st = ensure_clique(p);
-        if (st != PM_OK) return st;
+    if ((passes & DP_K4E) && !p->d_k4e) {
+        p->bytes_k4e = sizeof(uint32_t) * size_t(std::max<int64_t>(2 * g->m, 1));
+        p->d_k4e = (uint32_t *)dev_alloc(p->bytes_k4e, g->device);
+        if (!p->d_k4e) {
+            p->bytes_k4e = 0;
+            set_error("device allocation failed (4-cliques per edge)");
+            return PM_ENOMEM;
+        }
+    }
+    if ((passes & DP_LOCAL) && !p->local_ready) {
+        p->local_blocks = local_blocks(g->device);
+        const int64_t gw = local_grow_words(g->max_updeg);
+        if (gw > 0) {
+            // neighbourhoods too large for shared memory: per-block rows,
+            // members and per-member sums in global memory
+            p->bytes_local = size_t(p->local_blocks) *
+                             (sizeof(uint32_t) * size_t(gw) + 2 * sizeof(int32_t) * size_t(g->max_updeg));
+            p->d_local = (uint32_t *)dev_alloc(p->bytes_local, g->device);
+            if (!p->d_local) {
+                p->bytes_local = 0;
+                set_error("device allocation failed (neighbourhood bitmaps)");
+                return PM_ENOMEM;
+            }
+        }
+        p->local_ready = true;
     }
     return PM_OK;
 }
@@ -626,18 +661,28 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
         D.tasks = tasks;
         D.passes = p->decomp_passes_active;
         D.t = p->d_tslot;
+        D.k4e = p->d_k4e;
+        D.local_blocks = p->local_blocks;
+        D.local.g = L.g;
+        D.local.low_off = tasks.off[TASKS_LOWER];
+        D.local.basis = p->d_basis;
+        D.local.ctl = p->d_ctl;
+        D.local.max_s = p->g->max_updeg;
+        D.local.grow_words = local_grow_words(p->g->max_updeg);
+        if (p->d_local) {
+            // per block: rows, then members, then per-member sums
+            D.local.grows = p->d_local;
+            D.local.gmem = reinterpret_cast<int32_t *>(p->d_local + size_t(p->local_blocks) * size_t(D.local.grow_words));
+            D.local.gts = reinterpret_cast<uint32_t *>(D.local.gmem) + size_t(p->local_blocks) * size_t(D.local.max_s);
+        }
         D.W = p->d_dW;
         D.touched = p->d_dtouched;
         D.path_blocks = p->dpath_blocks;
         D.basis = p->d_basis;
         D.ctl = p->d_ctl;
         p->launches += 3 + int((D.passes & DP_TRI2) != 0) + int((D.passes & DP_PATHS) != 0) +
-                       int((D.passes & DP_CLIQUE) != 0) + 1;
+                       2 * int((D.passes & DP_LOCAL) != 0) + 1;
         if (launch_decomp(D, s)) return PM_ECUDA;
-        if ((D.passes & DP_CLIQUE) &&
-            launch_clique(L.g, tasks, 4, DB_K4, p->d_basis, p->d_spill, p->spill_len, 1, p->d_ctl,
-                          nullptr, s, p->d_basis + 2 * DB_K4DEG))
-            return PM_ECUDA;
         if (launch_decomp_combine(p->d_basis, p->d_targets, nt, p->d_counters, s)) return PM_ECUDA;
         mark(first, 1);
         if (gate_flags && (p->launches++, launch_flag_targets(p->d_ctl, gate_flags, p->d_targets, nt, s)))
@@ -1415,6 +1460,119 @@ pm_status pm_count_instrumented(pm_query_plan *p, void *stream, uint64_t *counts
     return run_count(p, stream, 0.0, nullptr, 0, false, counts, nullptr, alg_bytes);
 }
 
+// The graph's caller-to-internal vertex map on the device (uploaded once).
+static pm_status ensure_new_id(const pm_graph *g) {
+    std::lock_guard<std::mutex> lk(g->new_id_mu);
+    if (g->d_new_id) return PM_OK;
+    g->d_new_id = (int32_t *)dev_alloc(sizeof(int32_t) * size_t(g->n), g->device);
+    if (!g->d_new_id) {
+        set_error("device allocation failed (vertex map)");
+        return PM_ENOMEM;
+    }
+    cudaError_t e = cudaMemcpy(g->d_new_id, g->new_id.data(), sizeof(int32_t) * size_t(g->n),
+                               cudaMemcpyHostToDevice);
+    if (e) return cuda_fail("vertex map upload", e);
+    return PM_OK;
+}
+
+pm_status pm_support_roots(pm_query_plan *p, void *stream, double timeout_s, const int32_t *roots,
+                           int64_t nroots, uint32_t *domains_dev) {
+    if (!p || !domains_dev || (!roots && nroots > 0) || nroots < 0) {
+        set_error("pm_support_roots: null argument or bad root list");
+        return PM_EINVAL;
+    }
+    if (p->op != PM_OP_SUPPORT || !p->g) {
+        set_error("pm_support_roots: needs a PM_OP_SUPPORT plan made on a graph");
+        return PM_EINVAL;
+    }
+    const pm_graph *g = p->g;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return PM_ECUDA;
+    pm_status st = ensure_device(p);
+    if (st == PM_OK) st = ensure_new_id(g);
+    if (st != PM_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    static const int32_t none = 0;
+    RootTasks rt;
+    DevTasks tasks;
+    st = root_tasks(g, roots ? roots : &none, nroots, s, rt, &tasks);
+    if (st != PM_OK) return st;
+    if (p->rooted_table.dirty) p->rooted_table.plans = p->rooted;
+    st = upload_table(p->rooted_table, g->device);
+    if (st != PM_OK) return st;
+    const size_t ncols = p->col_off.size() - 1;
+    cudaError_t e = cudaMemsetAsync(p->d_bitsets, 0, p->bytes_bitsets, s);
+    if (e) return cuda_fail("pm_support_roots: memset", e);
+    const uint64_t budget = timeout_s > 0 ? uint64_t(timeout_s * 1e9) : 0;
+    if (launch_arm(p->d_ctl, budget, s)) return PM_ECUDA;
+    st = launch_table(p, p->rooted_table, tasks, 1, true, nullptr, s);
+    if (st != PM_OK) return st;
+    if (launch_mni_domains(p->d_bitsets, p->words, p->d_col_off, p->d_col_src, int(ncols),
+                           g->d_new_id, g->n, domains_dev, s))
+        return PM_ECUDA;
+    Control ctl;
+    e = cudaMemcpyAsync(&ctl, p->d_ctl, sizeof(Control), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail("pm_support_roots: kernel or readback", e);
+    if (ctl.status == 1) {
+        set_error("pm_support_roots: deadline expired");
+        return PM_ETIMEOUT;
+    }
+    return PM_OK;
+}
+
+pm_status pm_domains_or(const uint32_t *parts_dev, int32_t n_parts, int64_t words, uint32_t *out_dev,
+                        void *stream) {
+    if (!parts_dev || !out_dev || n_parts < 1 || words < 0) {
+        set_error("pm_domains_or: null pointer or empty input");
+        return PM_EINVAL;
+    }
+    if (words == 0) return PM_OK;
+    if (launch_domains_or(parts_dev, n_parts, words, out_dev, stream)) {
+        set_error("pm_domains_or: launch failed");
+        return PM_ECUDA;
+    }
+    return PM_OK;
+}
+
+pm_status pm_support_from_domains(pm_query_plan *p, const uint32_t *domains_dev, void *stream,
+                                  uint64_t threshold, uint64_t *support, uint8_t *frequent) {
+    if (!p || !domains_dev || !support) {
+        set_error("pm_support_from_domains: null argument");
+        return PM_EINVAL;
+    }
+    if (p->op != PM_OP_SUPPORT || !p->g) {
+        set_error("pm_support_from_domains: needs a PM_OP_SUPPORT plan made on a graph");
+        return PM_EINVAL;
+    }
+    const pm_graph *g = p->g;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return PM_ECUDA;
+    pm_status st = ensure_device(p);
+    if (st != PM_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t ncols = p->col_off.size() - 1;
+    const int64_t words = (g->n + 31) / 32;
+    cudaError_t e = cudaMemsetAsync(p->d_popc, 0, sizeof(unsigned long long) * std::max<size_t>(ncols, 1), s);
+    if (e) return cuda_fail("pm_support_from_domains: memset", e);
+    if (launch_column_popc(domains_dev, words, int(ncols), p->d_popc, s)) return PM_ECUDA;
+    std::vector<unsigned long long> popc(ncols);
+    e = ncols ? cudaMemcpyAsync(popc.data(), p->d_popc, sizeof(unsigned long long) * ncols,
+                                cudaMemcpyDeviceToHost, s) : cudaSuccess;
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail("pm_support_from_domains: readback", e);
+    const size_t nq = p->morph.queries.size();
+    for (size_t i = 0; i < nq; i++) {
+        const int c0 = p->query_col_base[i];
+        const int c1 = (i + 1 < nq) ? p->query_col_base[i + 1] : int(ncols);
+        uint64_t best = UINT64_MAX;
+        for (int c = c0; c < c1; c++) best = std::min<uint64_t>(best, popc[c]);
+        support[i] = best == UINT64_MAX ? 0 : best;
+        if (frequent) frequent[i] = support[i] >= threshold ? 1 : 0;
+    }
+    return PM_OK;
+}
+
 pm_status pm_plan_query_columns(const pm_query_plan *p, int32_t *columns) {
     if (!p || !columns) return PM_EINVAL;
     if (p->op != PM_OP_SUPPORT) {
@@ -1466,19 +1624,8 @@ pm_status pm_support(pm_query_plan *p, void *stream, double timeout_s, uint64_t 
                           p->d_popc, s))
         return PM_ECUDA;
     if (domains_dev) {
-        {
-            std::lock_guard<std::mutex> lk(g->new_id_mu);
-            if (!g->d_new_id) {
-                g->d_new_id = (int32_t *)dev_alloc(sizeof(int32_t) * size_t(g->n), g->device);
-                if (!g->d_new_id) {
-                    set_error("pm_support: device allocation failed (vertex map)");
-                    return PM_ENOMEM;
-                }
-                e = cudaMemcpy(g->d_new_id, g->new_id.data(), sizeof(int32_t) * size_t(g->n),
-                               cudaMemcpyHostToDevice);
-                if (e) return cuda_fail("pm_support: vertex map upload", e);
-            }
-        }
+        st = ensure_new_id(g);
+        if (st != PM_OK) return st;
         if (launch_mni_domains(p->d_bitsets, p->words, p->d_col_off, p->d_col_src, int(ncols),
                                g->d_new_id, g->n, domains_dev, s))
             return PM_ECUDA;

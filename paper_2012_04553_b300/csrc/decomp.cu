@@ -208,12 +208,13 @@ __global__ void __launch_bounds__(DC_WARPS * 32) mirror_kernel(DevGraph g, int32
 // Sums over vertices and edges (each undirected edge once, from its higher
 // endpoint u towards x < u).
 __global__ void __launch_bounds__(DC_WARPS * 32) ve_kernel(DevGraph g, const int32_t *__restrict__ t,
+                                                          const uint32_t *__restrict__ k4e,
                                                           uint64_t *basis, Control *ctl) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = int64_t(gridDim.x) * DC_WARPS;
     u128 p4e = 0, bull = 0, lolli_e = 0, de = 0, kite = 0, dart_e = 0, book = 0;
     u128 star3 = 0, star4 = 0, tx3 = 0, paw = 0, fork = 0, p5a = 0, tvd = 0, cricket = 0,
-         lolli_v = 0, bowtie_v = 0;
+         lolli_v = 0, bowtie_v = 0, k5p3 = 0, k4deg3 = 0;
     for (int64_t u = int64_t(blockIdx.x) * DC_WARPS + (threadIdx.x >> 5); u < g.n; u += warps) {
         const int64_t row = __ldg(g.rowptr + u);
         const int64_t d = __ldg(g.rowptr + u + 1) - row;
@@ -226,6 +227,14 @@ __global__ void __launch_bounds__(DC_WARPS * 32) ve_kernel(DevGraph g, const int
             S += uint64_t(dx);
             S1 += uint64_t(dx - 1);
             S2 += uint64_t(dx - 1) * uint64_t(dx - 1);
+            if (k4e && x > u) {
+                // 4-cliques on the edge, kept at its slot in the lower endpoint's row
+                const uint64_t q = __ldg(k4e + row + j);
+                if (q) {
+                    k5p3 += u128(q) * uint64_t(tx - 2);
+                    k4deg3 += u128(q) * uint64_t(d + dx);
+                }
+            }
             if (x < u) {
                 p4e += u128(uint64_t((d - 1) * (dx - 1)));
                 if (tx > 0) {
@@ -278,6 +287,10 @@ __global__ void __launch_bounds__(DC_WARPS * 32) ve_kernel(DevGraph g, const int
     flush(basis, DB_CRICKET, cricket, lane);
     flush(basis, DB_LOLLI_V, lolli_v, lane);
     flush(basis, DB_BOWTIE_V, bowtie_v, lane);
+    if (k4e) {
+        flush(basis, DB_K5P3, k5p3, lane);
+        flush(basis, DB_K4DEG3, k4deg3, lane);
+    }
     (void)ctl;
 }
 
@@ -422,7 +435,10 @@ __global__ void combine_kernel(const uint64_t *basis, const int32_t *targets, in
             case DF_HOUSE: v = ld128(basis, DB_HOUSE) - 4 * DE; break;
             case DF_BOOK: v = ld128(basis, DB_BOOK); break;
             case DF_GEM: v = ld128(basis, DB_GEM_TRI) - 12 * K4; break;
-            case DF_K4PENDANT: v = ld128(basis, DB_K4DEG) - 12 * K4; break;
+            case DF_K4PENDANT: v = ld128(basis, DB_K4DEG3) / 3 - 12 * K4; break;
+            case DF_K4: v = K4; break;
+            case DF_K5: v = ld128(basis, DB_K5); break;
+            case DF_K5P3: v = ld128(basis, DB_K5P3); break;
             default: break;
         }
         const int slot = targets[2 * i + 1];
@@ -477,8 +493,16 @@ int launch_decomp(const DecompLaunch &L, void *stream) {
     cudaMemsetAsync(&L.ctl->work3, 0, sizeof(unsigned long long), s);
     tri_kernel<0><<<dc_blocks(device, (const void *)tri_kernel<0>), DC_WARPS * 32, 0, s>>>(A);
     mirror_kernel<<<dc_blocks(device, (const void *)mirror_kernel), DC_WARPS * 32, 0, s>>>(L.g, L.t);
-    ve_kernel<<<dc_blocks(device, (const void *)ve_kernel), DC_WARPS * 32, 0, s>>>(L.g, L.t, L.basis,
-                                                                                L.ctl);
+    if (L.passes & DP_LOCAL) {
+        if (L.k4e) cudaMemsetAsync(L.k4e, 0, sizeof(uint32_t) * size_t(L.g.nnz), s);
+        cudaMemsetAsync(&L.ctl->work3, 0, sizeof(unsigned long long), s);
+        LocalArgs la = L.local;
+        la.k4e = (L.passes & DP_K4E) ? L.k4e : nullptr;
+        la.want_k5 = (L.passes & DP_K5) ? 1 : 0;
+        if (launch_local(la, L.local_blocks, s)) return -1;
+    }
+    ve_kernel<<<dc_blocks(device, (const void *)ve_kernel), DC_WARPS * 32, 0, s>>>(
+        L.g, L.t, (L.passes & DP_K4E) ? L.k4e : nullptr, L.basis, L.ctl);
     if (L.passes & DP_TRI2) {
         cudaMemsetAsync(&L.ctl->work3, 0, sizeof(unsigned long long), s);
         tri_kernel<1><<<dc_blocks(device, (const void *)tri_kernel<1>), DC_WARPS * 32, 0, s>>>(A);

@@ -126,6 +126,7 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
             off[0][i + 1] = off[0][i] + g->lowdeg[r];
             off[1][i + 1] = off[1][i] + (d - g->lowdeg[r]);
             off[2][i + 1] = off[2][i] + d;
+            g->max_updeg = std::max<int64_t>(g->max_updeg, d - g->lowdeg[r]);
         }
         for (int sp = 0; sp < 3; sp++) g->ntasks[sp] = off[sp][n];
         if (nnz >= (int64_t(1) << 32)) {

@@ -18,6 +18,7 @@
 struct pm_graph {
     int device = 0;
     int64_t n = 0, m = 0, self_loops = 0, duplicates = 0, max_degree = 0;
+    int64_t max_updeg = 0;           // most neighbours ranked above one vertex
     bool labeled = false;
     std::vector<int32_t> new_id;     // caller id -> internal id
     std::vector<int32_t> lowdeg;     // internal id -> neighbours with smaller internal id
@@ -148,7 +149,7 @@ int launch_clique(const DevGraph &g, const DevTasks &tasks, int k, int counter,
 // Edge-induced counts from local statistics (decomp.cu).  Sums (128-bit,
 // 2 words each, DB_COUNT entries) accumulated by the passes:
 enum DecompSum : int {
-    DB_TRI, DB_K4, DB_K4DEG, DB_DE, DB_C4,
+    DB_TRI, DB_K4, DB_K5, DB_K4DEG3, DB_K5P3, DB_DE, DB_C4,
     DB_STAR3, DB_STAR4, DB_P4E, DB_TX3, DB_PAW, DB_FORK, DB_P5A, DB_TVD, DB_CRICKET,
     DB_LOLLI_V, DB_BOWTIE_V, DB_BULL, DB_LOLLI_E, DB_KITE, DB_DART_E, DB_BOOK,
     DB_C5TRI, DB_DART_TRI, DB_GEM_TRI, DB_BANNER2, DB_HOUSE, DB_C5Q, DB_C5CORR, DB_C5TM,
@@ -159,10 +160,33 @@ enum DecompFormula : int {
     DF_STAR3, DF_P4, DF_PAW, DF_DIAMOND,                       // 4 vertices
     DF_STAR4, DF_FORK, DF_P5, DF_CRICKET, DF_BULL, DF_LOLLIPOP, DF_BANNER, DF_C5, DF_KITE,
     DF_DART, DF_BOWTIE, DF_HOUSE, DF_BOOK, DF_GEM, DF_K4PENDANT,   // 5 vertices
+    DF_K4, DF_K5, DF_K5P3,                                         // cliques, K5 minus a 2-path
     DF_COUNT
 };
-// Passes beyond triangle pass 1, the mirror and the vertex/edge pass.
-enum DecompPass : int { DP_TRI2 = 1, DP_PATHS = 2, DP_C5 = 4, DP_CLIQUE = 8 };
+// Passes beyond triangle pass 1, the mirror and the vertex/edge pass:
+// triangle pass 2, 2-path pass (with the 5-cycle scan), out-neighbourhood
+// bitmaps (4-cliques; 5-cliques; 4-cliques per edge).
+enum DecompPass : int {
+    DP_TRI2 = 1, DP_PATHS = 2, DP_C5 = 4, DP_LOCAL = 8, DP_K5 = 16, DP_K4E = 32
+};
+// Out-neighbourhood bitmap pass (local.cu).
+struct LocalArgs {
+    DevGraph g;
+    const int64_t *low_off;   // lower-neighbour task offsets over the implicit roots n-1..0
+    uint32_t *k4e;            // 4-cliques per edge at its slot in the lower endpoint's row, or nullptr
+    uint64_t *basis;
+    Control *ctl;
+    uint32_t *grows;          // per block: rows of neighbourhoods above the shared-memory size
+    int32_t *gmem;            // per block: their members (max_s entries)
+    uint32_t *gts;            // per block: their per-member triangle sums (max_s entries)
+    int64_t grow_words;
+    int64_t max_s;
+    int want_k5;
+};
+size_t local_smem_bytes();
+int local_blocks(int device);
+int64_t local_grow_words(int64_t max_s);
+int launch_local(const LocalArgs &A, int blocks, void *stream);
 // formula of an unlabeled edge-induced pattern, or -1 (morph.cpp)
 int decomp_formula(const Pat &p);
 int decomp_passes(int formula);
@@ -171,6 +195,9 @@ struct DecompLaunch {
     DevTasks tasks;           // lower-neighbour tasks over every root
     int passes;
     int32_t *t;               // one int32 per CSR slot
+    uint32_t *k4e;            // one uint32 per CSR slot (DP_K4E), or nullptr
+    LocalArgs local;          // DP_LOCAL: scratch of the bitmap pass
+    int local_blocks;
     uint32_t *W;              // path_blocks x n (zero on entry and exit)
     int32_t *touched;         // path_blocks x n
     int path_blocks;
@@ -186,6 +213,9 @@ int launch_decomp_combine(const uint64_t *basis, const int32_t *targets, int n_t
 int launch_mni_reduce(const uint32_t *d_bitsets, int64_t words_per_bitset, const int32_t *d_src_off,
                       const int32_t *d_src, int n_columns, unsigned long long *d_popc,
                       void *stream);
+int launch_domains_or(const uint32_t *parts, int n_parts, int64_t words, uint32_t *out, void *stream);
+int launch_column_popc(const uint32_t *cols, int64_t words, int n_columns, unsigned long long *popc,
+                       void *stream);
 // Query columns as n-bit bitsets in caller vertex ids: bit v of column c of
 // out (words_per_bitset words each) = bit new_id[v] of the OR of c's sources.
 int launch_mni_domains(const uint32_t *d_bitsets, int64_t words_per_bitset,

@@ -1069,6 +1069,55 @@ int launch_mni_domains(const uint32_t *d_bitsets, int64_t words, const int32_t *
     return 0;
 }
 
+// OR of n_parts bitsets of `words` words each (the per-shard MNI columns of
+// a sharded support), and the popcount of each column of a set of columns.
+__global__ void domains_or_kernel(const uint32_t *__restrict__ parts, int n_parts, int64_t words,
+                                  uint32_t *__restrict__ out) {
+    for (int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; w < words;
+         w += int64_t(gridDim.x) * blockDim.x) {
+        uint32_t v = 0;
+        for (int p = 0; p < n_parts; p++) v |= __ldg(parts + int64_t(p) * words + w);
+        out[w] = v;
+    }
+}
+
+__global__ void column_popc_kernel(const uint32_t *__restrict__ cols, int64_t words, int n_columns,
+                                   unsigned long long *popc) {
+    const int c = blockIdx.y;
+    if (c >= n_columns) return;
+    unsigned long long local = 0;
+    for (int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; w < words;
+         w += int64_t(gridDim.x) * blockDim.x)
+        local += __popc(__ldg(cols + int64_t(c) * words + w));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(FULL, local, off);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(popc + c, local);
+}
+
+int launch_domains_or(const uint32_t *parts, int n_parts, int64_t words, uint32_t *out, void *stream) {
+    int device = 0;
+    cudaGetDevice(&device);
+    int64_t blocks = (words + 255) / 256;
+    const int64_t cap = 8 * int64_t(device_sm_count(device));
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    domains_or_kernel<<<unsigned(blocks), 256, 0, (cudaStream_t)stream>>>(parts, n_parts, words, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_column_popc(const uint32_t *cols, int64_t words, int n_columns, unsigned long long *popc,
+                       void *stream) {
+    if (n_columns == 0) return 0;
+    int device = 0;
+    cudaGetDevice(&device);
+    int64_t bx = (words + 255) / 256;
+    if (bx > 4 * device_sm_count(device)) bx = 4 * device_sm_count(device);
+    if (bx < 1) bx = 1;
+    dim3 grid{unsigned(bx), unsigned(n_columns), 1u};
+    column_popc_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(cols, words, n_columns, popc);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int launch_mni_reduce(const uint32_t *d_bitsets, int64_t words, const int32_t *d_src_off,
                       const int32_t *d_src, int n_columns, unsigned long long *d_popc,
                       void *stream) {

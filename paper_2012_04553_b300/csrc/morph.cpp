@@ -470,6 +470,7 @@ DevPlan compile_free_plan(const Pat &p, int counter, int dom_base,
 // lexicographic pair order.
 int decomp_formula(const Pat &p) {
     if ((p.vi && !p.is_clique()) || p.labeled() || (p.k != 4 && p.k != 5)) return -1;
+    // (a clique's edge- and vertex-induced counts coincide)
     static const std::map<Key, int> table = [] {
         const int8_t none[KMAX] = {-1, -1, -1, -1, -1, -1, -1, -1};
         const struct { int k; uint32_t mask; int f; } rows[] = {
@@ -477,7 +478,8 @@ int decomp_formula(const Pat &p) {
             {5, 15, DF_STAR4}, {5, 29, DF_FORK}, {5, 58, DF_P5}, {5, 31, DF_CRICKET},
             {5, 59, DF_BULL}, {5, 185, DF_LOLLIPOP}, {5, 62, DF_BANNER}, {5, 220, DF_C5},
             {5, 63, DF_KITE}, {5, 187, DF_DART}, {5, 207, DF_BOWTIE}, {5, 221, DF_HOUSE},
-            {5, 127, DF_BOOK}, {5, 223, DF_GEM}, {5, 191, DF_K4PENDANT}};
+            {5, 127, DF_BOOK}, {5, 223, DF_GEM}, {5, 191, DF_K4PENDANT},
+            {4, 63, DF_K4}, {5, 1023, DF_K5}, {5, 255, DF_K5P3}};
         std::map<Key, int> m;
         for (const auto &r : rows) m[canonical(Pat::from_mask(r.k, r.mask, none, false))] = r.f;
         return m;
@@ -492,8 +494,10 @@ int decomp_passes(int f) {
     switch (f) {
         case DF_P5: case DF_BANNER: case DF_HOUSE: return DP_PATHS;
         case DF_C5: return DP_PATHS | DP_C5;
-        case DF_DART: case DF_GEM: return DP_TRI2 | DP_CLIQUE;
-        case DF_K4PENDANT: return DP_CLIQUE;
+        case DF_DART: case DF_GEM: return DP_TRI2 | DP_LOCAL;
+        case DF_K4: return DP_LOCAL;
+        case DF_K5: return DP_LOCAL | DP_K5;
+        case DF_K4PENDANT: case DF_K5P3: return DP_LOCAL | DP_K4E;
         default: return 0;
     }
 }

@@ -12,6 +12,13 @@ partial and summing.
 
 The only exchange is one sum of n_matched 128-bit integers, carried out as
 16-bit limbs in int64 so that it is exact for any realistic world size.
+
+MNI support shards the same way: the columns of a query over all matches
+are the union of its columns over each process's roots, so each process
+fills its columns (pm_support_roots), the columns are gathered, ORed by
+the library (pm_domains_or) and the smallest column of each query is its
+support (pm_support_from_domains).  There is no OR reduction in NCCL, hence
+an all-gather followed by a local OR.
 """
 import numpy as np
 
@@ -80,3 +87,27 @@ def count_sharded(plan, graph, rank, world, stream=None, timeout_s=0.0, group=No
     _, matched = plan.count_roots(roots, stream=stream, timeout_s=timeout_s, with_matched=True)
     total = allreduce_counts(matched, group) if world > 1 else matched
     return plan.morph(total)
+
+
+def gather_columns(local, group=None):
+    """All processes' MNI column bitsets stacked: shape (world,) + local.shape.
+    CUDA tensors are gathered with the group's backend on the device; with a
+    CPU-only backend (gloo) they are staged through host memory."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    staged = local if dist.get_backend(group) == "nccl" else local.cpu()
+    parts = [torch.empty_like(staged) for _ in range(world)]
+    dist.all_gather(parts, staged.contiguous(), group=group)
+    return torch.stack(parts).to(local.device)
+
+
+def support_sharded(plan, graph, rank, world, threshold=0, stream=None, timeout_s=0.0, group=None):
+    """MNI supports of a PM_OP_SUPPORT plan with the roots split over `world`
+    processes: each fills the columns of its shard, the columns are gathered
+    and ORed on the device, and each process reads the supports."""
+    import paper_2012_04553_b300 as pm
+    roots = root_shard(graph.vertex_order(), rank, world)
+    local = plan.support_roots(roots, stream=stream, timeout_s=timeout_s)
+    cols = pm.domains_or(gather_columns(local, group), stream=stream) if world > 1 else local
+    return plan.support_from_domains(cols, threshold, stream=stream)

@@ -16,8 +16,8 @@ from pm_inputs import rmat_edges, gnp_edges, uniform_ints, cached_rmat
 pytestmark = pytest.mark.gpu
 
 # canonical masks (lexicographic pair order) of the decomposed patterns
-DECOMP4 = [7, 13, 15, 31]                                  # star, P4, tailed triangle, diamond
-DECOMP5 = [15, 29, 58, 31, 59, 62, 185, 220, 63, 187, 207, 221, 127, 223, 191]
+DECOMP4 = [7, 13, 15, 31, 63]                      # star, P4, tailed triangle, diamond, 4-clique
+DECOMP5 = [15, 29, 58, 31, 59, 62, 185, 220, 63, 187, 207, 221, 127, 223, 191, 255, 1023]
 
 
 def ei(k, m):
@@ -78,6 +78,26 @@ def test_decomposition_against_oracle(name, n, s, d):
     assert one == want                               # each pattern alone (its own passes only)
 
 
+@pytest.mark.parametrize("n", [24, 200, 800])
+def test_decomposition_closed_forms_on_cliques(n):
+    """On the complete graph K_n every connected k-vertex pattern occurs
+    C(n, k) k! / |Aut(p)| times edge-induced.  n = 24 keeps every
+    out-neighbourhood within one warp, n = 200 puts them in shared memory,
+    n = 800 (out-degrees up to 799) in the per-block global area."""
+    from math import comb, factorial
+    pairs = [(a, b) for a in range(n) for b in range(a + 1, n)]
+    s = np.array([a for a, _ in pairs], np.int32)
+    d = np.array([b for _, b in pairs], np.int32)
+    g = pm.Graph(n, s, d)
+    want = []
+    for k, masks in ((4, DECOMP4), (5, DECOMP5)):
+        for m in masks:
+            aut = len(algebra.automorphisms(algebra.Pattern.from_mask(k, m)))
+            want.append(comb(n, k) * factorial(k) // aut)
+    plan = pm.Plan(g, decomp_queries(), mode=pm.MORPH_NONE)
+    assert plan.count() == want
+
+
 def test_decomposition_equals_set_operations_scale11():
     """On R-MAT scale 11 (ef 8) the decomposition and the free-family set
     operations (two independent GPU algorithms) agree on every pattern."""
@@ -91,8 +111,8 @@ def test_decomposition_equals_set_operations_scale11():
 
 @pytest.mark.parametrize("scale,ef,seed", [(7, 6, 306), (8, 6, 307)])
 def test_five_motifs_morphed_with_decomposition(scale, ef, seed):
-    """Vertex-induced 5-motifs via naive morphing (15 edge-induced counts from
-    the decomposition, 6 from set operations) against the oracle's direct
+    """Vertex-induced 5-motifs via naive morphing (17 edge-induced counts from
+    the decomposition, 4 from set operations) against the oracle's direct
     vertex-induced counts."""
     n = 1 << scale
     s, d = rmat_edges(scale, ef, seed=seed)
@@ -124,11 +144,11 @@ def test_decomposition_deadline_flags_its_patterns():
 def test_decomposition_on_scale20_matches_free_plans():
     """On the bench's scale-20 graph, the decomposed patterns whose free
     set-operation plans finish in seconds (the 4-vertex star, path, tailed
-    triangle and diamond; the 5-vertex star, fork, cricket and book) get the
-    same counts both ways."""
+    triangle, diamond and 4-clique; the 5-vertex star, fork, cricket and
+    book) get the same counts both ways."""
     s, d = cached_rmat(20, 16, seed=2)
     g = pm.Graph(1 << 20, s, d)
-    qs = [ei(4, m) for m in DECOMP4] + [ei(5, m) for m in (15, 29, 31, 127)]
+    qs = [ei(4, m) for m in DECOMP4] + [ei(5, m) for m in (15, 29, 31, 127)]   # set operations finish
     auto = pm.Plan(g, qs, mode=pm.MORPH_NONE)
     got = auto.count()
     free = pm.Plan(g, qs, mode=pm.MORPH_NONE)

@@ -400,6 +400,39 @@ def test_mni_domains_returned_in_caller_ids():
             assert sup[i] == min(int(w.sum()) for w in want[i])
 
 
+def test_sharded_mni_support_on_one_gpu():
+    """Sharded MNI support (three root shards, their columns ORed by
+    pm_domains_or) equals pm_support's supports and columns, morphed and
+    direct; each shard's columns are the oracle's over its roots."""
+    from paper_2012_04553_b300 import shard
+    import torch
+    n = 512
+    s, d = rmat_edges(9, 8, seed=122)
+    labels = zipf_labels(n, 3, seed=123)
+    og = oracle.prepare_graph(n, s, d, labels)
+    g = load(n, s, d, labels)
+    qs = oracle.labeled_edge_patterns(3, [0, 1, 2])[::4]
+    cq = [pm.make_pattern(p.k, p.mask, pm.EDGE_INDUCED, p.labels) for p in qs]
+    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+        plan = pm.Plan(g, cq, op=pm.OP_SUPPORT, mode=mode)
+        sup, freq, doms = plan.support(threshold=10, domains=True)
+        parts = torch.stack([plan.support_roots(shard.root_shard(g.vertex_order(), r, 3)) for r in range(3)])
+        cols = pm.domains_or(parts)
+        assert torch.equal(cols, torch.cat(doms))
+        assert plan.support_from_domains(cols, threshold=10) == (sup, freq)
+        # shard 0's columns against the oracle's columns over its roots
+        r0 = shard.root_shard(g.vertex_order(), 0, 3)
+        at = 0
+        words = parts[0].cpu().numpy().view(np.uint32)
+        for p in qs:
+            _, dom = oracle.match_count(og, p, roots=r0, domains=True)
+            for orb in algebra.orbits(p):
+                want = np.logical_or.reduce([dom[u] for u in orb])
+                bits = ((words[at][:, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(-1)[:n]
+                assert (bits.astype(bool) == want).all()
+                at += 1
+
+
 def test_fsm_against_oracle():
     """Level-wise 3-edge FSM with MNI support (Section 2): the candidates of
     every level, their supports and the frequent sets, morphed and direct."""
