@@ -205,7 +205,7 @@ def traffic_record(kernel):
     return rec
 
 
-def cpu_oracle_sample(n, src, dst, ks, budget_s=12.0, seed=11, per_root_s=1.0, sample=4096,
+def cpu_oracle_sample(n, src, dst, ks, budget_s=12.0, seed=11, per_root_s=0.25, sample=4096,
                       all_core=True):
     """The oracle as it stands (direct vertex-induced counting) on a bounded
     sample of the same workload: roots drawn uniformly over all n vertices
@@ -216,6 +216,9 @@ def cpu_oracle_sample(n, src, dst, ks, budget_s=12.0, seed=11, per_root_s=1.0, s
     in one call on all host cores.  Returns the all-core matches/s, the
     single-thread matches/s, the roots and the per-root occurrence sums."""
     import oracle
+    # host cores this process may use (the oracle's single-thread calls pin
+    # OpenMP to one thread, so the all-core pass asks for them explicitly)
+    ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     og = oracle.prepare_graph(n, src, dst)
     order = uniform_ints(seed, 9, sample, 0, n)
     _, first = np.unique(order, return_index=True)
@@ -244,10 +247,10 @@ def cpu_oracle_sample(n, src, dst, ks, budget_s=12.0, seed=11, per_root_s=1.0, s
     value, cores = out["single_thread"]["value"], 1
     if all_core and len(roots):
         t1 = time.time()
-        c_all = sum(sum(oracle.motif_counts_direct(og, k, roots=roots)) for k in ks)
+        c_all = sum(sum(oracle.motif_counts_direct(og, k, roots=roots, threads=ncores)) for k in ks)
         t_all = time.time() - t1
         assert c_all == matches
-        value, cores = matches / t_all, oracle.max_threads()
+        value, cores = matches / t_all, ncores
         out["all_core"] = {"value": value, "cores": cores, "seconds": round(t_all, 3)}
     deg_done = og.degree[roots] if len(roots) else np.zeros(1, np.int64)
     out.update({"value": value, "cores": cores,

@@ -213,7 +213,8 @@ pm_status pm_plan_autotune(pm_query_plan *p, void *stream, int32_t *families);
  * last two levels are an independent pair counted as |A||B| - |A n B|, with
  * the merged constraints of A n B in level k), int32 pad;
  * then 8 levels of uint8 isect, diff, lt,
- * gt, neq, int8 label, uint8 column, pad.  For inspection and tests;
+ * gt, neq, int8 label, uint8 column, vertex (the pattern vertex the level
+ * binds).  For inspection and tests;
  * PM_EINVAL if cap is too small. */
 pm_status pm_plan_export(const pm_query_plan *p, int32_t family, void *out, int64_t cap);
 
@@ -305,6 +306,25 @@ pm_status pm_support(pm_query_plan *p, void *stream, double timeout_s, uint64_t 
  * Columns are the automorphism orbits numbered by their smallest vertex;
  * query i has 1 + max_u columns[i * PM_MAX_K + u] of them. */
 pm_status pm_plan_query_columns(const pm_query_plan *p, int32_t *columns);
+
+/* List every occurrence of every query of a counting plan (Section 3.2.1:
+ * materialising M(q^V) o phi(p^E, q^E), Theorem 3.1).  An edge-induced query
+ * planned with morphing is listed from the matches of its vertex-induced
+ * superpatterns, each composed with one map per distinct copy of the query
+ * it contains, so every distinct occurrence (edge subgraph) appears exactly
+ * once; queries matched as given (PM_MORPH_NONE, cliques) are listed
+ * directly.  A vertex-induced query morphed to edge-induced patterns cannot
+ * be listed (Corollary 3.1 subtracts): PM_EUNSUPPORTED.
+ * tuples: cap x PM_MAX_K int32 (host), occurrence r is tuples[r * PM_MAX_K
+ * + u] = the caller vertex that query vertex u maps to (-1 for u >= k);
+ * query_of (nullable): cap int32, the query of each occurrence.  Order is
+ * unspecified.  *n_out = number of occurrences; PM_EOVERFLOW (nothing
+ * written) when it exceeds cap.  Runs a count first to size the output;
+ * device memory of (PM_MAX_K + 1) x 4 bytes per listed match is taken
+ * through the allocator for the call.  Errors: PM_EINVAL, PM_EUNSUPPORTED,
+ * PM_EOVERFLOW, PM_ENOMEM, PM_ECUDA, PM_ETIMEOUT. */
+pm_status pm_enumerate(pm_query_plan *p, void *stream, double timeout_s, int32_t *tuples,
+                       int32_t *query_of, int64_t cap, int64_t *n_out);
 
 /* Sharded MNI support.  Every match has one highest-ranked vertex (rank =
  * (degree, caller id)), so the MNI columns of a query over all matches are

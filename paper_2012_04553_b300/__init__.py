@@ -109,6 +109,7 @@ def _load():
         "pm_support_roots": [vp, vp, dbl, vp, i64, vp],
         "pm_domains_or": [vp, i32, i64, vp, vp],
         "pm_support_from_domains": [vp, vp, vp, ctypes.c_uint64, vp, vp],
+        "pm_enumerate": [vp, vp, dbl, vp, vp, i64, ctypes.POINTER(i64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -139,7 +140,7 @@ ABI_SYMBOLS = [
     "pm_server_create", "pm_server_submit", "pm_server_wait", "pm_server_get_stats",
     "pm_server_destroy", "pm_plan_set_launch", "pm_count_each", "pm_plan_query_columns",
     "pm_plan_pattern_ms", "pm_plan_last_launches", "pm_support_roots", "pm_domains_or",
-    "pm_support_from_domains",
+    "pm_support_from_domains", "pm_enumerate",
 ]
 
 
@@ -341,7 +342,7 @@ class Plan:
     def export_plans(self, family=PLANS_ROOTED):
         """The compiled plans of one family as a numpy structured array (pm_plan_export)."""
         level = np.dtype([("isect", "u1"), ("diff", "u1"), ("lt", "u1"), ("gt", "u1"),
-                          ("neq", "u1"), ("label", "i1"), ("column", "u1"), ("pad", "u1")])
+                          ("neq", "u1"), ("label", "i1"), ("column", "u1"), ("vertex", "u1")])
         rec = np.dtype([("k", "<i4"), ("n_enum", "<i4"), ("tail", "<i4"), ("closed", "<i4"),
                         ("counter", "<i4"), ("dom_base", "<i4"), ("n_columns", "<i4"),
                         ("split", "<i4"), ("task_space", "<i4"), ("kind", "<i4"),
@@ -457,6 +458,21 @@ class Plan:
             per_query.append(dom[at:at + max(c) + 1])
             at += max(c) + 1
         return out + (per_query,)
+
+    def enumerate(self, cap=1 << 20, stream=None, timeout_s=0.0):
+        """Every occurrence of every query (pm_enumerate): a list of
+        (query index, tuple of caller vertex ids indexed by query vertex)."""
+        while True:
+            tup = np.zeros((max(cap, 1), MAX_K), dtype=np.int32)
+            qof = np.zeros(max(cap, 1), dtype=np.int32)
+            n = ctypes.c_int64(0)
+            st = _lib.pm_enumerate(self._h, _stream_handle(stream), float(timeout_s), _ptr(tup), _ptr(qof),
+                                   int(cap), ctypes.byref(n))
+            if st == PM_EOVERFLOW and n.value > cap:
+                cap = int(n.value)
+                continue
+            _check(st, "pm_enumerate")
+            return [(int(qof[r]), tuple(int(x) for x in tup[r] if x >= 0)) for r in range(n.value)]
 
     def _columns_tensor(self):
         import torch

@@ -1573,6 +1573,204 @@ pm_status pm_support_from_domains(pm_query_plan *p, const uint32_t *domains_dev,
     return PM_OK;
 }
 
+// Listing through Theorem 3.1 (Section 3.2.1): the edge-induced matches of
+// p are the vertex-induced matches of p and of its superpatterns q, each
+// composed with the maps phi(p^E, q^E); one map per distinct image edge set
+// (c(p, q) of them) lists every distinct occurrence of p exactly once, the
+// union over q being disjoint (Corollary 3.1).  A vertex-induced query is
+// listed directly.  Listing plans are the free plans with every level
+// enumerated (one match per occurrence, symmetry broken).
+pm_status pm_enumerate(pm_query_plan *p, void *stream, double timeout_s, int32_t *tuples,
+                       int32_t *query_of, int64_t cap, int64_t *n_out) {
+    if (!p || !n_out || (cap > 0 && !tuples) || cap < 0) {
+        set_error("pm_enumerate: null argument");
+        return PM_EINVAL;
+    }
+    if (p->op != PM_OP_COUNT || !p->g) {
+        set_error("pm_enumerate: needs a counting plan made on a graph");
+        return PM_EINVAL;
+    }
+    const pm_graph *g = p->g;
+    const size_t nq = p->morph.queries.size(), nm = p->morph.matched.size();
+    // maps per matched pattern: (query, f) with f[u] = vertex of the matched
+    // pattern that vertex u of the query goes to
+    std::vector<std::vector<std::pair<int, Perm>>> maps(nm);
+    for (size_t i = 0; i < nq; i++) {
+        Pat q = p->morph.queries[i];
+        if (q.is_clique()) q.vi = false;
+        for (const Term &t : p->morph.terms[i]) {
+            if (t.coef <= 0) {
+                set_error("pm_enumerate: a vertex-induced query morphed to edge-induced patterns "
+                          "(Corollary 3.1 subtracts) cannot be listed; plan it with PM_MORPH_NONE");
+                return PM_EUNSUPPORTED;
+            }
+            const Pat &mq = p->morph.matched[t.matched];
+            std::vector<Perm> fs;
+            if (q.vi) {
+                // a vertex-induced query is matched as itself (canonical numbering)
+                fs = embeddings(q, mq);
+                if (!fs.empty()) fs.resize(1);
+            } else {
+                Pat pe = q, me = mq;
+                pe.vi = me.vi = false;
+                std::vector<Perm> all = embeddings(pe, me);
+                std::vector<uint64_t> seen;
+                for (const Perm &f : all) {
+                    uint64_t img = 0;   // image edge set of the query's edges
+                    for (int a = 0; a < q.k; a++)
+                        for (int b = a + 1; b < q.k; b++)
+                            if (q.adjacent(a, b)) {
+                                const int x = std::min(f[a], f[b]), y = std::max(f[a], f[b]);
+                                img |= uint64_t(1) << (x * PM_MAX_K + y);
+                            }
+                    if (std::find(seen.begin(), seen.end(), img) == seen.end()) {
+                        seen.push_back(img);
+                        fs.push_back(f);
+                    }
+                }
+            }
+            if (int64_t(fs.size()) != t.coef) {
+                set_error("pm_enumerate: internal error (maps do not match the morph coefficient)");
+                return PM_EUNSUPPORTED;
+            }
+            for (const Perm &f : fs) maps[t.matched].push_back({int(i), f});
+        }
+    }
+    // exact sizes from a count
+    std::vector<uint64_t> req(2 * nq), mat(2 * nm);
+    pm_status st = run_count(p, stream, timeout_s, nullptr, 0, false, req.data(), mat.data());
+    if (st != PM_OK) return st;
+    int64_t listed = 0, needed = 0;
+    for (size_t j = 0; j < nm; j++) {
+        if (mat[2 * j + 1]) {
+            set_error("pm_enumerate: more matches than can be listed");
+            return PM_EOVERFLOW;
+        }
+        listed += int64_t(mat[2 * j]);
+        needed += int64_t(mat[2 * j]) * int64_t(maps[j].size());
+    }
+    *n_out = needed;
+    if (needed > cap) {
+        set_error("pm_enumerate: cap too small (*n_out holds the number of occurrences)");
+        return PM_EOVERFLOW;
+    }
+    if (needed == 0) return PM_OK;
+    DeviceGuard dg(g->device);
+    if (!dg.ok) return PM_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    // listing plans
+    PlanTable table;
+    for (size_t j = 0; j < nm; j++) {
+        DevPlan dp = compile_free_plan(p->morph.matched[j], int(j), 0, p->morph.matched_orbit[j], false);
+        if (dp.k >= 3) {
+            dp.tail = 1;
+            dp.n_enum = dp.k - 1;
+        }
+        dp.closed = 0;
+        dp.pair = 0;
+        table.plans.push_back(dp);
+    }
+    st = upload_table(table, g->device);
+    if (st != PM_OK) return st;
+    std::vector<int32_t> old_of(g->n), map_off(nm + 1, 0), map_query, query_k(nq);
+    std::vector<uint8_t> map_f;
+    for (int64_t v = 0; v < g->n; v++) old_of[g->new_id[v]] = int32_t(v);
+    for (size_t j = 0; j < nm; j++) {
+        for (auto &qf : maps[j]) {
+            map_query.push_back(qf.first);
+            for (int u = 0; u < PM_MAX_K; u++) map_f.push_back(qf.second[u]);
+        }
+        map_off[j + 1] = int32_t(map_query.size());
+    }
+    for (size_t i = 0; i < nq; i++) query_k[i] = p->morph.queries[i].k;
+    // device buffers: listed matches (tuple + tag), output (tuple + query),
+    // cursors, maps, the vertex map
+    const size_t b_q = sizeof(int32_t) * size_t(listed) * (PM_MAX_K + 1);
+    const size_t b_o = sizeof(int32_t) * size_t(needed) * (PM_MAX_K + 1);
+    const size_t b_aux = sizeof(int32_t) * (size_t(g->n) + map_off.size() + map_query.size() + nq) +
+                         map_f.size() + 64;
+    char *dq = (char *)dev_alloc(b_q, g->device);
+    char *dout = (char *)dev_alloc(b_o, g->device);
+    char *daux = (char *)dev_alloc(b_aux, g->device);
+    auto release = [&]() {
+        dev_free(dq, b_q, g->device);
+        dev_free(dout, b_o, g->device);
+        dev_free(daux, b_aux, g->device);
+        free_table(table, g->device);
+    };
+    if (!dq || !dout || !daux) {
+        release();
+        set_error("pm_enumerate: device allocation failed");
+        return PM_ENOMEM;
+    }
+    int32_t *q_t = (int32_t *)dq, *q_tag = q_t + size_t(listed) * PM_MAX_K;
+    int32_t *o_t = (int32_t *)dout, *o_q = o_t + size_t(needed) * PM_MAX_K;
+    unsigned long long *cur = (unsigned long long *)daux;               // two cursors
+    int32_t *d_old = (int32_t *)(daux + 16);
+    int32_t *d_moff = d_old + g->n;
+    int32_t *d_mq = d_moff + map_off.size();
+    int32_t *d_qk = d_mq + map_query.size();
+    uint8_t *d_mf = (uint8_t *)(d_qk + nq);
+    cudaError_t e = cudaMemsetAsync(cur, 0, 16, s);
+    if (!e) e = cudaMemcpyAsync(d_old, old_of.data(), sizeof(int32_t) * g->n, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(d_moff, map_off.data(), sizeof(int32_t) * map_off.size(), cudaMemcpyHostToDevice, s);
+    if (!e && !map_query.empty())
+        e = cudaMemcpyAsync(d_mq, map_query.data(), sizeof(int32_t) * map_query.size(), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(d_qk, query_k.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, s);
+    if (!e && !map_f.empty()) e = cudaMemcpyAsync(d_mf, map_f.data(), map_f.size(), cudaMemcpyHostToDevice, s);
+    if (e) {
+        release();
+        return cuda_fail("pm_enumerate: upload", e);
+    }
+    const uint64_t budget = timeout_s > 0 ? uint64_t(timeout_s * 1e9) : 0;
+    MatchLaunch L{};
+    const DevTasks tasks = all_tasks(g);
+    L.g = g->dev();
+    L.plans = table.d;
+    L.nplans = int(table.plans.size());
+    L.max_enum = table.max_enum;
+    L.tasks = tasks;
+    L.n_echunks = echunks_for(table.plans, tasks);
+    L.sample_stride = 1;
+    L.counters = p->d_counters;
+    L.ctl = p->d_ctl;
+    L.defer = p->d_defer;
+    L.defer_cap = p->defer_cap;
+    L.piece_off = p->d_piece_off;
+    L.list_out = q_t;
+    L.list_tag = q_tag;
+    L.list_cursor = cur;
+    L.list_cap = listed;
+    L.old_of = d_old;
+    int rc = launch_arm(p->d_ctl, budget, s);
+    if (!rc && L.n_echunks > 0) rc = launch_list(L, s);
+    if (!rc) rc = launch_compose(q_t, q_tag, listed, d_moff, d_mq, d_mf, d_qk, o_t, o_q, cur + 1, needed, s);
+    if (rc) {
+        release();
+        return PM_ECUDA;
+    }
+    unsigned long long cursors[2] = {0, 0};
+    Control ctl;
+    e = cudaMemcpyAsync(cursors, cur, 16, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(&ctl, p->d_ctl, sizeof(Control), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(tuples, o_t, sizeof(int32_t) * size_t(needed) * PM_MAX_K,
+                                cudaMemcpyDeviceToHost, s);
+    if (!e && query_of) e = cudaMemcpyAsync(query_of, o_q, sizeof(int32_t) * size_t(needed),
+                                            cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    release();
+    if (e) return cuda_fail("pm_enumerate: kernel or readback", e);
+    if (ctl.status == 1) {
+        set_error("pm_enumerate: deadline expired");
+        return PM_ETIMEOUT;
+    }
+    if (int64_t(cursors[0]) != listed || int64_t(cursors[1]) != needed) {
+        set_error("pm_enumerate: listed matches disagree with the count");
+        return PM_ECUDA;
+    }
+    return PM_OK;
+}
+
 pm_status pm_plan_query_columns(const pm_query_plan *p, int32_t *columns) {
     if (!p || !columns) return PM_EINVAL;
     if (p->op != PM_OP_SUPPORT) {

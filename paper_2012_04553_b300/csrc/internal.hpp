@@ -122,8 +122,19 @@ struct MatchLaunch {
     uint32_t defer_cap;
     uint32_t *piece_off;
     unsigned long long *stats;
+    // listing (launch_list): output tuples, their tags, the shared cursor,
+    // capacity in tuples, internal -> caller id map
+    int32_t *list_out;
+    int32_t *list_tag;
+    unsigned long long *list_cursor;
+    int64_t list_cap;
+    const int32_t *old_of;
 };
 int launch_count(const MatchLaunch &L, void *stream);
+int launch_list(const MatchLaunch &L, void *stream);
+int launch_compose(const int32_t *qt, const int32_t *qtag, int64_t n_listed, const int32_t *map_off,
+                   const int32_t *map_query, const uint8_t *map_f, const int32_t *query_k, int32_t *out,
+                   int32_t *out_query, unsigned long long *cursor, int64_t cap, void *stream);
 int launch_domains(const MatchLaunch &L, void *stream);
 // Wedge-pair kernels for one PLAN_WEDGE_PAIRS plan over the lower task space
 // of `tasks`: roots a >= heavy_from by the shared-memory heavy-root kernel

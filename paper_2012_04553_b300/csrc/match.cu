@@ -282,19 +282,45 @@ __device__ __forceinline__ bool deadline_hit(uint64_t deadline, int *status, int
     return __shfl_sync(FULL, hit, 0) != 0;
 }
 
+// Listing output (pm_enumerate): every match a listing plan reaches is
+// written as PLAN_KMAX caller vertex ids indexed by pattern vertex, with the
+// matched pattern's index as its tag, at a slot taken from a shared cursor
+// (matches past `cap` are counted but not written).
+struct ListOut {
+    int32_t *out;
+    int32_t *tag;
+    unsigned long long *cursor;
+    int64_t cap;
+    const int32_t *old_of;    // internal id -> caller id
+};
+
+__device__ __forceinline__ void emit_match(const ListOut &lo, const DevPlan &P, const Bound &m, int L,
+                                           int32_t x, bool with_x) {
+    const unsigned long long pos = atomicAdd(lo.cursor, 1ull);
+    if (pos >= (unsigned long long)lo.cap) return;
+    int32_t *t = lo.out + int64_t(pos) * PLAN_KMAX;
+#pragma unroll
+    for (int l = 0; l < PLAN_KMAX; l++)
+        if (l <= L) t[P.lv[l].vertex] = __ldg(lo.old_of + m.v[l]);
+    if (with_x) t[P.lv[L + 1].vertex] = __ldg(lo.old_of + x);
+    lo.tag[pos] = P.counter;
+}
+
 // Final stage over the prefixes of buffer L: levels n_enum .. k-1 counted.
 // For the flattened (scanned) stage only candidates [t_begin, t_end) are
 // visited; a range narrower than the whole buffer is used only when
 // tail == 1 in counting mode, where partial counts add up.
-template <bool DOMAINS, bool STATS>
+template <bool DOMAINS, bool STATS, bool LIST>
 __device__ bool final_stage(const DevGraph &g, const DevPlan &P, LevelBuf *B, WarpTail &T, int L,
                             int32_t t_begin, int32_t t_end, int lane, u128 &acc, uint64_t &stat,
                             uint32_t *bitsets, int64_t words, uint64_t deadline, int *status,
-                            uint32_t &tick) {
+                            uint32_t &tick, const ListOut &lo) {
     LevelBuf &b = B[L];
     const int cnt = b.cnt;
     if (P.tail == 0) {   // k == 2: each prefix is a match
-        if (DOMAINS) {
+        if (LIST) {
+            for (int p = lane; p < cnt; p += 32) emit_match(lo, P, tuple_of(B, L, p), L, 0, false);
+        } else if (DOMAINS) {
             for (int p = lane; p < cnt; p += 32) {
                 const Bound m = tuple_of(B, L, p);
 #pragma unroll
@@ -364,7 +390,9 @@ __device__ bool final_stage(const DevGraph &g, const DevPlan &P, LevelBuf *B, Wa
                 const Bound m = tuple_of(B, L, p);
                 ok = admissible(g, lv, b.src[p], m, x);
             }
-            if (!DOMAINS && P.tail == 1) {
+            if (LIST) {
+                if (ok) emit_match(lo, P, tuple_of(B, L, p), L, x, true);
+            } else if (!DOMAINS && P.tail == 1) {
                 if (ok) acc += 1;
             } else if (counting) {
                 if (ok) atomicAdd(&T.fcount[p], 1);
@@ -418,13 +446,14 @@ struct KernelArgs {
     uint32_t defer_cap;
     const uint32_t *piece_off;  // exclusive scan of pieces per deferred chunk
     unsigned long long *stats;
+    ListOut list;               // listing instance only
 };
 
 // One chunk (plan c % nplans, oriented edges (c / nplans) * 32 + 0..31),
 // restricted to flattened second-level candidates [t_begin, t_end).  In the
 // first pass (may_defer) a range larger than the plan's split is cut to the
 // split and the remainder deferred.  Returns false once the deadline expired.
-template <bool DOMAINS, bool STATS>
+template <bool DOMAINS, bool STATS, bool LIST>
 __device__ bool process_chunk(const KernelArgs &A, LevelBuf *B, WarpTail &T, unsigned long long c,
                               int32_t t_begin, int32_t t_end, bool may_defer, int lane,
                               uint64_t deadline, uint32_t &tick, uint64_t &stat) {
@@ -476,8 +505,8 @@ __device__ bool process_chunk(const KernelArgs &A, LevelBuf *B, WarpTail &T, uns
     const bool splittable =
         P.n_enum > 2 || (!DOMAINS && ((!P.closed && P.tail == 1) || P.pair));
     if (!splittable) {
-        alive = final_stage<DOMAINS, STATS>(g, P, B, T, 1, 0, INT_MAX, lane, acc, stat, A.bitsets,
-                                           A.words, deadline, status, tick);
+        alive = final_stage<DOMAINS, STATS, LIST>(g, P, B, T, 1, 0, INT_MAX, lane, acc, stat, A.bitsets,
+                                                 A.words, deadline, status, tick, A.list);
     } else {
         uint64_t resetup = 0;
         // the split range is over the second level's candidates, or, for a
@@ -498,8 +527,8 @@ __device__ bool process_chunk(const KernelArgs &A, LevelBuf *B, WarpTail &T, uns
             t_end_eff = __shfl_sync(FULL, t_end_eff, 0);
         }
         if (P.n_enum == 2) {
-            alive = final_stage<DOMAINS, STATS>(g, P, B, T, 1, t_begin, t_end_eff, lane, acc, stat,
-                                               A.bitsets, A.words, deadline, status, tick);
+            alive = final_stage<DOMAINS, STATS, LIST>(g, P, B, T, 1, t_begin, t_end_eff, lane, acc, stat,
+                                                     A.bitsets, A.words, deadline, status, tick, A.list);
         } else {
             if (lane == 0) {
                 B[1].t = t_begin;
@@ -509,8 +538,9 @@ __device__ bool process_chunk(const KernelArgs &A, LevelBuf *B, WarpTail &T, uns
             int L = 1;
             while (alive) {
                 if (L + 1 == P.n_enum) {
-                    alive = final_stage<DOMAINS, STATS>(g, P, B, T, L, 0, INT_MAX, lane, acc, stat,
-                                                       A.bitsets, A.words, deadline, status, tick);
+                    alive = final_stage<DOMAINS, STATS, LIST>(g, P, B, T, L, 0, INT_MAX, lane, acc,
+                                                             stat, A.bitsets, A.words, deadline,
+                                                             status, tick, A.list);
                     if (lane == 0) B[L].cnt = 0;
                     __syncwarp();
                     L--;
@@ -558,7 +588,7 @@ __device__ bool process_chunk(const KernelArgs &A, LevelBuf *B, WarpTail &T, uns
             }
         }
     }
-    if (!DOMAINS) {
+    if (!DOMAINS && !LIST) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) acc += shfl_xor_u128(acc, off);
         if (lane == 0 && acc != 0) add_u128(A.counters + 2 * int64_t(P.counter), acc);
@@ -568,7 +598,7 @@ __device__ bool process_chunk(const KernelArgs &A, LevelBuf *B, WarpTail &T, uns
 
 // pass 0: chunks from the shared counter (deferring oversized ranges);
 // pass 1: split-sized pieces of the deferred chunks.
-template <bool DOMAINS, bool STATS>
+template <bool DOMAINS, bool STATS, bool LIST>
 __global__ void __launch_bounds__(WARPS * 32)
 match_kernel(KernelArgs A, int pass) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -606,8 +636,8 @@ match_kernel(KernelArgs A, int pass) {
         bool alive;
         if (pass == 0) {
             const unsigned long long c = (w / A.nplans) * stride * A.nplans + w % A.nplans;
-            alive = process_chunk<DOMAINS, STATS>(A, B, T, c, 0, INT_MAX, true, lane, deadline,
-                                                 tick, stat);
+            alive = process_chunk<DOMAINS, STATS, LIST>(A, B, T, c, 0, INT_MAX, true, lane, deadline,
+                                                       tick, stat);
         } else {
             // piece w: deferred chunk i with piece_off[i] <= w < piece_off[i+1]
             uint32_t lo = 0, hi = n_def;
@@ -622,8 +652,8 @@ match_kernel(KernelArgs A, int pass) {
             const int32_t j = int32_t(w - __ldg(A.piece_off + lo)) + 1;   // piece 0 ran in pass 0
             const int32_t tb = j * P.split;
             const int32_t te = min(int32_t(tot), tb + P.split);
-            alive = process_chunk<DOMAINS, STATS>(A, B, T, chunk, tb, te, false, lane, deadline,
-                                                 tick, stat);
+            alive = process_chunk<DOMAINS, STATS, LIST>(A, B, T, chunk, tb, te, false, lane, deadline,
+                                                       tick, stat);
         }
         if (!alive) break;
     }
@@ -992,14 +1022,14 @@ int launch_arm(Control *d_ctl, uint64_t budget_ns, void *stream) {
     return 0;
 }
 
-template <bool DOMAINS, bool STATS>
+template <bool DOMAINS, bool STATS, bool LIST = false>
 static int launch_match(const MatchLaunch &L, void *stream) {
     int device = 0;
     cudaGetDevice(&device);
     const int sms = device_sm_count(device);
     const int n_buf = L.max_enum < 2 ? 2 : L.max_enum;
     const size_t smem = (sizeof(LevelBuf) * n_buf + sizeof(WarpTail)) * WARPS;
-    auto kern = match_kernel<DOMAINS, STATS>;
+    auto kern = match_kernel<DOMAINS, STATS, LIST>;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     int per_sm = 0;
@@ -1026,6 +1056,7 @@ static int launch_match(const MatchLaunch &L, void *stream) {
     A.defer_cap = L.defer_cap;
     A.piece_off = L.piece_off;
     A.stats = L.stats;
+    A.list = ListOut{L.list_out, L.list_tag, L.list_cursor, L.list_cap, L.old_of};
     cudaStream_t s = (cudaStream_t)stream;
     kern<<<unsigned(blocks0), WARPS * 32, smem, s>>>(A, 0);
     piece_scan_kernel<<<1, 1024, 0, s>>>(L.defer, L.defer_cap, L.plans, L.nplans, L.piece_off,
@@ -1046,6 +1077,48 @@ int launch_count(const MatchLaunch &L, void *stream) {
 
 int launch_domains(const MatchLaunch &L, void *stream) {
     return launch_match<true, false>(L, stream);
+}
+
+int launch_list(const MatchLaunch &L, void *stream) {
+    return launch_match<false, false, true>(L, stream);
+}
+
+// Theorem 3.1 on listed matches: every listed match t of a matched pattern
+// j, composed with each map f of j's list (query i, f: vertex of i -> vertex
+// of j), gives the match u -> t[f[u]] of query i.
+__global__ void compose_kernel(const int32_t *__restrict__ qt, const int32_t *__restrict__ qtag,
+                               int64_t n_listed, const int32_t *__restrict__ map_off,
+                               const int32_t *__restrict__ map_query, const uint8_t *__restrict__ map_f,
+                               const int32_t *__restrict__ query_k, int32_t *out, int32_t *out_query,
+                               unsigned long long *cursor, int64_t cap) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n_listed;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int j = qtag[i];
+        const int32_t *t = qt + i * PLAN_KMAX;
+        for (int m = map_off[j]; m < map_off[j + 1]; m++) {
+            const unsigned long long pos = atomicAdd(cursor, 1ull);
+            if (pos >= (unsigned long long)cap) continue;
+            const int q = map_query[m];
+            const int k = query_k[q];
+            int32_t *o = out + int64_t(pos) * PLAN_KMAX;
+#pragma unroll
+            for (int u = 0; u < PLAN_KMAX; u++) o[u] = u < k ? t[map_f[m * PLAN_KMAX + u]] : -1;
+            out_query[pos] = q;
+        }
+    }
+}
+
+int launch_compose(const int32_t *qt, const int32_t *qtag, int64_t n_listed, const int32_t *map_off,
+                   const int32_t *map_query, const uint8_t *map_f, const int32_t *query_k, int32_t *out,
+                   int32_t *out_query, unsigned long long *cursor, int64_t cap, void *stream) {
+    if (n_listed == 0) return 0;
+    int device = 0;
+    cudaGetDevice(&device);
+    int64_t blocks = (n_listed + 255) / 256;
+    if (blocks > 8 * int64_t(device_sm_count(device))) blocks = 8 * int64_t(device_sm_count(device));
+    compose_kernel<<<unsigned(blocks), 256, 0, (cudaStream_t)stream>>>(
+        qt, qtag, n_listed, map_off, map_query, map_f, query_k, out, out_query, cursor, cap);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int launch_mni_domains(const uint32_t *d_bitsets, int64_t words, const int32_t *d_src_off,

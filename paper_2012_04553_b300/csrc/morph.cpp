@@ -334,6 +334,7 @@ static DevPlan build_plan(const Pat &p, const std::vector<int> &order, std::vect
     for (int i = 0; i < p.k; i++) {
         int u = order[i];
         DevLevel &lv = plan.lv[i];
+        lv.vertex = uint8_t(u);
         lv.label = p.lab[u];
         lv.column = uint8_t(column_of_vertex.empty() ? 0 : column_of_vertex[u]);
         if (i == 0) continue;

@@ -50,7 +50,7 @@ struct DevLevel {
     uint8_t neq;
     int8_t label;
     uint8_t column;   // MNI column (orbit index) of the pattern vertex bound here
-    uint8_t pad;
+    uint8_t vertex;   // the pattern vertex bound here (listing output)
 };
 
 // Which oriented edges (root, v) a plan's tasks range over.

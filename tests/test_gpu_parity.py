@@ -533,3 +533,47 @@ def test_deadline_returns_timeout_and_context_survives():
     small = pm.Plan(g, motif_queries(3), mode=pm.MORPH_NAIVE)
     a = small.count()
     assert small.count(timeout_s=60.0) == a
+
+
+def _occurrences(n, es, p, labels=None):
+    """Distinct occurrences (edge sets) of p by brute force over injective maps."""
+    out = set()
+    for m in algebra.brute_force_matches(n, es, p, labels):
+        out.add(frozenset(frozenset((m[a], m[b])) for a, b in p.edges) |
+                frozenset([frozenset(m)]))
+    return out
+
+
+def test_enumerate_through_theorem_3_1():
+    """pm_enumerate lists every occurrence exactly once: edge-induced queries
+    from their vertex-induced superpatterns' matches composed with phi
+    (Theorem 3.1), vertex-induced and clique queries directly; the listed
+    edge sets equal brute force, with no repeats."""
+    n = 20
+    s, d = gnp_edges(n, 0.35, 124)
+    og = oracle.prepare_graph(n, s, d)
+    es = og.edge_set()
+    g = load(n, s, d)
+    qs = [algebra.Pattern.from_mask(4, m) for m in algebra.connected_classes(4)] + \
+         [algebra.Pattern.from_mask(3, 0b011, vertex_induced=True),
+          algebra.Pattern.from_mask(5, algebra.connected_classes(5)[7])]
+    cq = [pm.make_pattern(p.k, p.mask, int(p.vertex_induced)) for p in qs]
+    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
+        plan = pm.Plan(g, cq, mode=mode)
+        listed = plan.enumerate(cap=16)                    # grows the buffer once
+        for i, p in enumerate(qs):
+            got = [t for q, t in listed if q == i]
+            occ = []
+            for t in got:
+                assert len(t) == p.k and len(set(t)) == p.k
+                assert all((min(t[a], t[b]), max(t[a], t[b])) in es for a, b in p.edges)
+                if p.vertex_induced:
+                    assert all((min(t[a], t[b]), max(t[a], t[b])) not in es for a, b in p.anti_edges)
+                occ.append(frozenset(frozenset((t[a], t[b])) for a, b in p.edges) | frozenset([frozenset(t)]))
+            assert len(occ) == len(set(occ)), (mode, i)
+            assert set(occ) == _occurrences(n, es, p), (mode, i)
+    vi = pm.Plan(g, [pm.make_pattern(4, algebra.connected_classes(4)[0], pm.VERTEX_INDUCED)],
+                 mode=pm.MORPH_NAIVE)
+    with pytest.raises(pm.PMError) as e:
+        vi.enumerate()
+    assert e.value.status == pm.PM_EUNSUPPORTED
