@@ -46,9 +46,16 @@ def parse():
                          "a systematic root sample, morphed vs direct; fsm / batch / serve: one "
                          "measurement line of the other workloads")
     ap.add_argument("--mc5-roots", type=int, default=1024, help="root sample size of the mc5 workload")
-    ap.add_argument("--mc5-deadline", type=float, default=60.0, help="deadline of each mc5 count")
+    ap.add_argument("--mc5-deadline", type=float, default=60.0, help="deadline of each sampled-root mc5 count")
+    ap.add_argument("--mc5-pattern-deadline", type=float, default=35.0,
+                    help="deadline of each edge-induced 5-vertex pattern in the whole-graph mc5 count")
+    ap.add_argument("--mc5-total-deadline", type=float, default=150.0,
+                    help="deadline of the whole-graph mc5 count")
+    ap.add_argument("--no-mc5", action="store_true", help="leave the 5-motif measurements out of the mc line")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--batch-scale", type=int, default=SCALE)
+    ap.add_argument("--batch-pattern-deadline", type=float, default=30.0)
+    ap.add_argument("--batch-total-deadline", type=float, default=240.0)
     ap.add_argument("--serve-kmax", type=int, default=6, help="largest pattern size in serving requests")
     ap.add_argument("--pattern", default="4:63:0",
                     help="pattern workload: k:edge_mask:induced (induced 1 = vertex-induced)")
@@ -192,16 +199,17 @@ def barrier(world):
 def traffic_record(kernel):
     """DRAM bytes per launch of `kernel` on this workload from the committed
     ncu summary (profiles/traffic.json), valid only while the kernel's source
-    file is unchanged."""
+    files are unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path)).get(kernel)
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_2012_04553_b300", "csrc", rec["source"])
-    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
-        return None
+    for src, sha in rec["sources"].items():
+        f = os.path.join(ROOT, "paper_2012_04553_b300", "csrc", src)
+        if not os.path.exists(f) or hashlib.sha256(open(f, "rb").read()).hexdigest() != sha:
+            return None
     return rec
 
 
@@ -339,8 +347,10 @@ def run_fsm(args):
 
 def run_batch(args):
     """512 random connected 3-6 vertex patterns (half vertex-, half
-    edge-induced; seed 5) counted with one plan on the scale-20 graph,
-    replayed from a captured CUDA graph, under a 300 s deadline."""
+    edge-induced; seed 5) counted with one plan on the scale-20 graph in one
+    persistent launch (the decomposable edge-induced patterns by the
+    decomposition kernels after it), replayed from a captured CUDA graph with
+    a deadline per pattern counted from the launch start: per-query status."""
     import torch
     import paper_2012_04553_b300 as pm
     from pm_inputs import random_patterns
@@ -353,27 +363,38 @@ def run_batch(args):
     t0 = time.time()
     plan = pm.Plan(g, qs, mode=pm.MORPH_NAIVE)
     t_plan = time.time() - t0
-    plan.set_launch(pm.LAUNCH_SINGLE)     # one persistent launch for the whole batch
+    plan.set_launch(pm.LAUNCH_SINGLE)     # one persistent launch for the set-operation plans
     t0 = time.time()
-    plan.capture(timeout_s=300.0)
+    fam = plan.autotune()
+    plan.capture_each(timeout_per_pattern_s=args.batch_pattern_deadline,
+                      timeout_total_s=args.batch_total_deadline)
     t_tune = time.time() - t0
     torch.cuda.synchronize()
     t0 = time.time()
-    try:
-        counts = plan.count()
-        status = "ok"
-    except pm.PMTimeout:
-        counts, status = None, "deadline (300 s) expired"
+    counts, status = plan.count_each()
+    torch.cuda.synchronize()
     wall = time.time() - t0
+    ok = [i for i, st in enumerate(status) if st == pm.PM_OK]
+    by_k = {}
+    for (k, m, ind), st in zip(pats, status):
+        e = by_k.setdefault(str(k), {"queries": 0, "ok": 0})
+        e["queries"] += 1
+        e["ok"] += int(st == pm.PM_OK)
     line = {"metric": f"batched 512-pattern counting wall time, R-MAT scale {scale}", "value": wall,
             "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "int64",
-            "data": "synthetic", "status": status, "n_matched": plan.n_matched,
-            "plan_s": t_plan, "autotune_and_capture_s": t_tune,
-            "patterns_per_s": (512 / wall) if counts else None,
+            "data": "synthetic", "n_matched": plan.n_matched,
+            "matched_families": {name: int(sum(f == code for f in fam)) for name, code in
+                                 (("rooted", pm.PLANS_ROOTED), ("free", pm.PLANS_FREE),
+                                  ("decomposition", pm.PLANS_DECOMP))},
+            "queries_ok": len(ok), "queries_deadline": len(qs) - len(ok), "by_size": by_k,
+            "patterns_per_s_completed": len(ok) / wall if wall > 0 else None,
+            "plan_s": t_plan, "autotune_and_capture_s": t_tune, "launches": plan.last_launches(),
             "config": {"workload": "512 random connected patterns of 3-6 vertices (uniform over sizes, "
                                    "alternating vertex-/edge-induced, seed 5), naive morph, one plan, "
-                                   f"single persistent launch, captured CUDA graph, R-MAT scale {scale} "
-                                   "ef 16 seed 2"}}
+                                   "single persistent launch, captured CUDA graph with a deadline of "
+                                   f"{args.batch_pattern_deadline:g} s per pattern from the launch start "
+                                   f"({args.batch_total_deadline:g} s in all), R-MAT scale {scale} ef 16 "
+                                   "seed 2"}}
     print(json.dumps(line), flush=True)
 
 
@@ -440,55 +461,85 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
-def run_mc5(args):
-    """5-motif counting (the 21 connected vertex-induced patterns) on the
-    scale-20 graph, restricted to a systematic sample of roots: every
-    (n / R)-th vertex in degree order, offset by half a stride (the sample
-    spans all degrees but leaves out the single highest-ranked vertices).
-    Counts are of occurrences whose highest-ranked vertex is a sampled root,
-    so morphed and direct results on the sample must agree exactly; each
-    count runs under its own deadline."""
+def mc5_measurements(pm, g, n, stream=None, roots_n=1024, deadline=60.0, per_pattern_s=30.0,
+                     total_s=240.0, direct_s=30.0):
+    """5-motif counting (the 21 connected vertex-induced unlabeled patterns)
+    on the loaded graph, morphed vs direct:
+    * sampled roots: occurrences whose highest-ranked vertex is one of a
+      systematic sample of roots (every (n / R)-th vertex in degree order,
+      offset half a stride), rooted plans, each count under `deadline`;
+      morphed and direct counts must agree exactly;
+    * whole graph, morphed: the 21 edge-induced patterns (Theorem 3.1 /
+      Corollary 3.1 turn them into the 21 vertex-induced counts), each under
+      its own deadline (pm_count_each), with its status and device time;
+    * whole graph, direct: the 21 vertex-induced patterns under `direct_s`."""
     import torch
+    by_rank = np.empty(n, dtype=np.int64)
+    by_rank[g.vertex_order()] = np.arange(n)
+    stride = n // roots_n
+    roots = np.sort(by_rank[(np.arange(roots_n) * stride + stride // 2).astype(np.int64)]).astype(np.int32)
+    masks = connected_classes(5)
+    vq = [pm.make_pattern(5, m, pm.VERTEX_INDUCED) for m in masks]
+    sample = {}
+    for name, mode in (("morphed", pm.MORPH_NAIVE), ("direct", pm.MORPH_NONE)):
+        plan = pm.Plan(g, vq, mode=mode)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        try:
+            c = plan.count_roots(roots, stream=stream, timeout_s=deadline)
+            torch.cuda.synchronize()
+            sample[name] = {"wall_s": round(time.time() - t0, 4), "counts": [str(x) for x in c]}
+        except pm.PMTimeout:
+            sample[name] = {"timed_out_after_s": round(time.time() - t0, 3), "deadline_s": deadline}
+    m, d = sample["morphed"], sample["direct"]
+    sample["counts_equal"] = (m["counts"] == d["counts"]) if "counts" in m and "counts" in d else None
+    sample["roots"] = int(len(roots))
+    # whole graph, morphed: edge-induced patterns with a deadline each
+    eplan = pm.Plan(g, [pm.make_pattern(5, mm, pm.EDGE_INDUCED) for mm in masks], mode=pm.MORPH_NONE)
+    eplan.autotune(stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ecounts, status = eplan.count_each(timeout_per_pattern_s=per_pattern_s, timeout_total_s=total_s,
+                                       stream=stream)
+    torch.cuda.synchronize()
+    wall = time.time() - t0
+    fam = eplan.autotune(stream=stream)
+    ms = eplan.pattern_ms()
+    names = {0: "rooted", 1: "free", 3: "decomposition"}
+    per = [{"edge_mask": mm, "status": "ok" if st == pm.PM_OK else "deadline", "family": names.get(f, f),
+            "device_ms": round(t, 3)} for mm, st, f, t in zip(masks, status, fam, ms)]
+    whole = {"wall_s": round(wall, 3), "per_pattern_deadline_s": per_pattern_s, "total_deadline_s": total_s,
+             "edge_induced": per, "completed": int(sum(st == pm.PM_OK for st in status))}
+    if all(st == pm.PM_OK for st in status):
+        vplan = pm.Plan(g, vq, mode=pm.MORPH_NAIVE)
+        order = {q[1]: i for i, q in enumerate(eplan.matched_patterns())}
+        matched = [ecounts[order[q[1]]] for q in vplan.matched_patterns()]
+        whole["vertex_induced_counts"] = [str(x) for x in vplan.morph(matched)]
+    direct = pm.Plan(g, vq, mode=pm.MORPH_NONE)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    try:
+        dc = direct.count(stream=stream, timeout_s=direct_s)
+        whole_direct = {"wall_s": round(time.time() - t0, 3),
+                        "counts_equal_morphed": [str(x) for x in dc] == whole.get("vertex_induced_counts")}
+    except pm.PMTimeout:
+        whole_direct = {"timed_out_after_s": round(time.time() - t0, 3), "deadline_s": direct_s}
+    return {"sampled_roots": sample, "whole_graph_morphed": whole, "whole_graph_direct": whole_direct}
+
+
+def run_mc5(args):
+    """5-motif counting on the scale-20 graph, morphed vs direct (one line)."""
     import paper_2012_04553_b300 as pm
     n = 1 << SCALE
     src, dst = cached_rmat(SCALE, EDGE_FACTOR, SEED)
     g = pm.Graph(n, src, dst)
-    by_rank = np.empty(n, dtype=np.int64)
-    by_rank[g.vertex_order()] = np.arange(n)
-    stride = n // args.mc5_roots
-    ranks = (np.arange(args.mc5_roots) * stride + stride // 2).astype(np.int64)
-    roots = np.sort(by_rank[ranks]).astype(np.int32)
-    deg = np.bincount(np.concatenate([src, dst]), minlength=n)   # raw, before dedup: for the record only
-    queries = [pm.make_pattern(5, m, pm.VERTEX_INDUCED) for m in connected_classes(5)]
-    out = {}
-    for name, mode in (("morphed", pm.MORPH_NAIVE), ("direct", pm.MORPH_NONE)):
-        plan = pm.Plan(g, queries, mode=mode)
-        plan.count_roots(roots[:8], timeout_s=args.mc5_deadline)       # warm-up on a few light roots
-        torch.cuda.synchronize()
-        t0 = time.time()
-        try:
-            c = plan.count_roots(roots, timeout_s=args.mc5_deadline)
-            torch.cuda.synchronize()
-            out[name] = {"wall_s": time.time() - t0, "counts": [str(x) for x in c], "matches": sum(c),
-                         "n_matched_patterns": plan.n_matched}
-        except pm.PMTimeout:
-            out[name] = {"timed_out_after_s": round(time.time() - t0, 3), "deadline_s": args.mc5_deadline,
-                         "n_matched_patterns": plan.n_matched}
-    m, d = out["morphed"], out["direct"]
-    line = {"metric": "5-motif counting matches/s on sampled roots (morphed), R-MAT scale 20",
-            "value": (m["matches"] / m["wall_s"]) if "wall_s" in m else None, "unit": "matches/s",
-            "higher_is_better": True, "n_gpus": 1, "dtype": "int64", "data": "synthetic",
-            "morphed": {k: v for k, v in m.items() if k != "matches"},
-            "direct": {k: v for k, v in d.items() if k != "matches"},
-            "direct_over_morphed_time": (d["wall_s"] / m["wall_s"]) if "wall_s" in m and "wall_s" in d
-            else None,
-            "counts_equal": (m["counts"] == d["counts"]) if "counts" in m and "counts" in d else None,
-            "sample": {"roots": int(len(roots)), "stride_in_degree_order": int(stride),
-                       "max_raw_degree_in_sample": int(deg[roots].max())},
+    res = mc5_measurements(pm, g, n, roots_n=args.mc5_roots, deadline=args.mc5_deadline,
+                           per_pattern_s=args.mc5_pattern_deadline, total_s=args.mc5_total_deadline)
+    line = {"metric": "5-motif counting, morphed vs direct, R-MAT scale 20",
+            "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "int64", "data": "synthetic",
+            "value": res["whole_graph_morphed"]["wall_s"], "mc5": res,
             "config": {"workload": "5-motif counting (21 connected vertex-induced unlabeled patterns), "
-                                   "naive morph to edge-induced patterns vs direct, rooted plans, on the "
-                                   "occurrences whose highest-ranked vertex lies in a systematic sample "
-                                   f"of {len(roots)} roots, R-MAT scale {SCALE} ef {EDGE_FACTOR} seed {SEED}"}}
+                                   f"R-MAT scale {SCALE} ef {EDGE_FACTOR} seed {SEED}"}}
     print(json.dumps(line), flush=True)
 
 
@@ -542,6 +593,7 @@ def main():
         step()
     plan0 = pm.Plan(g, queries, mode=pm.MORPH_NAIVE)
     counts_i, alg_bytes = plan0.count_instrumented(stream=stream)
+    pattern_bytes = plan0.pattern_bytes()
 
     # timed region: K steps, each bracketed by events on the launch stream
     sampler = ClockSampler(local)
@@ -607,8 +659,9 @@ def main():
         direct = {"timed_out_after_s": round(time.time() - t0, 3), "deadline_s": args.direct_deadline}
 
     peak, peak_kind = read_peaks()
-    roof = dominant_roofline(pm, g, plan0, per_pattern_ms, alg_bytes, float(np.mean(kernel_ms)),
-                             peak, peak_kind, stream)
+    roof = dominant_roofline(pm, plan0, per_pattern_ms, pattern_bytes, peak, peak_kind, stream)
+    roof["whole_step"] = {"algorithmic_bytes": int(alg_bytes),
+                          "launch_sequence_ms": round(float(np.mean(kernel_ms)), 3)}
     line = {
         "metric": metric_name(args), "value": value, "unit": "matches/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -627,6 +680,11 @@ def main():
         "clocks": clocks,
         "graph": {"n": info["n"], "m": info["m"], "max_degree": info["max_degree"]},
     }
+    if rank == 0 and not args.no_mc5:
+        line["mc5"] = mc5_measurements(pm, g, n, stream=stream, roots_n=args.mc5_roots,
+                                       deadline=args.mc5_deadline,
+                                       per_pattern_s=args.mc5_pattern_deadline,
+                                       total_s=args.mc5_total_deadline)
     if rank == 0 and world == 1 and not args.no_baseline:
         base = cpu_oracle_sample(n, src, dst, ks)
         roots = base.pop("roots")
@@ -648,15 +706,18 @@ def main():
         print(json.dumps(line), flush=True)
 
 
-def kernel_of(kind):
+def kernel_of(family, kind, pm):
+    if family == pm.PLANS_DECOMP:
+        return "decomposition: tri_kernel, mirror_kernel, local_warp_kernel, local_block_kernel, ve_kernel"
     return {0: "match_kernel", 1: "wedge_heavy_kernel+wedge_pairs_kernel", 2: "clique_kernel"}[kind]
 
 
-def dominant_roofline(pm, g, plan, per_pattern_ms, alg_bytes_all, seq_ms, peak, peak_kind, stream):
+def dominant_roofline(pm, plan, per_pattern_ms, pattern_bytes, peak, peak_kind, stream):
     """Roofline of the matched pattern whose launches take the most device
-    time in a step (per-pattern CUDA events on the launch stream): its
-    kernel, its algorithmic bytes (instrumented run of that pattern alone,
-    same plan family) over its own average time."""
+    time in a step (per-pattern CUDA events on the launch stream; the
+    decomposed patterns' passes are timed as one group): its kernels, its
+    algorithmic bytes (instrumented run of the same plan) over its own
+    average time."""
     fam = plan.autotune(stream=stream)
     rooted = plan.export_plans(pm.PLANS_ROOTED)
     mats = plan.matched_patterns()
@@ -667,24 +728,26 @@ def dominant_roofline(pm, g, plan, per_pattern_ms, alg_bytes_all, seq_ms, peak, 
         kinds = [int(r["kind"]) for r in rooted if int(r["counter"]) == j]
         kind = kinds[0] if len(kinds) == 1 else 0
     k, mask, induced, labels = mats[j]
-    single = pm.Plan(g, [pm.make_pattern(k, mask, induced, labels)], mode=pm.MORPH_NONE)
-    single.select(fam[j])
-    _, b = single.count_instrumented(stream=stream)
-    achieved = b / (ms[j] / 1000.0) / 1e9 if ms[j] > 0 else 0.0
-    trec = traffic_record(kernel_of(kind))
+    b = int(pattern_bytes[j])
+    achieved = b / (ms[j] / 1000.0) / 1e9 if ms[j] > 0 and b > 0 else None
+    name = kernel_of(fam[j], kind, pm)
+    trec = traffic_record(name.split(":")[0])
     share = float(ms[j] / ms.sum()) if ms.sum() > 0 else None
-    return {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 5), "peak_source": peak_kind,
+    fam_name = {pm.PLANS_ROOTED: "rooted", pm.PLANS_FREE: "free", pm.PLANS_DECOMP: "decomposition"}[fam[j]]
+    return {"bound": "hbm", "achieved": round(achieved, 2) if achieved else None, "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 5) if achieved else None,
+            "peak_source": peak_kind,
             "traffic": trec["dram_bytes_per_launch"] if trec else None,
             "traffic_frac": (round(trec["dram_bytes_per_launch"] / (ms[j] / 1000.0) / 1e9 / peak, 5)
                              if trec else None),
-            "kernel": kernel_of(kind),
-            "pattern": {"k": k, "edge_mask": mask, "induced": induced,
-                        "family": "rooted" if fam[j] == pm.PLANS_ROOTED else "free"},
+            "kernel": name,
+            "pattern": {"k": k, "edge_mask": mask, "induced": induced, "family": fam_name,
+                        "decomposed_patterns_in_group": int(sum(f == pm.PLANS_DECOMP for f in fam))
+                        if fam[j] == pm.PLANS_DECOMP else None},
             "kernel_ms": round(float(ms[j]), 3), "share_of_step_device_time": share,
-            "algorithmic_bytes_per_launch": int(b),
+            "algorithmic_bytes_per_launch": b,
             "per_pattern_ms": [round(float(x), 3) for x in ms],
-            "whole_step": {"algorithmic_bytes": int(alg_bytes_all), "launch_sequence_ms": round(seq_ms, 3)}}
+            "per_pattern_algorithmic_bytes": [int(x) for x in pattern_bytes]}
 
 
 if __name__ == "__main__":

@@ -202,7 +202,11 @@ pm_status pm_plan_set_launch(pm_query_plan *p, int32_t mode);
 /* Run the autotuner now (it otherwise runs inside the first pm_count or
  * pm_support): for each matched pattern not yet decided on this graph, time
  * its rooted and free plans on the same sample of about 4096 task chunks and
- * keep the faster; decisions are cached on the graph.  families (nullable):
+ * keep the faster, then time that family's task granularity -- the
+ * second-level candidates a task chunk keeps before the rest is deferred to
+ * other warps, which sets how many warps share a hub root -- at a quarter
+ * and at four times the compiled value, keeping one only if it is more than
+ * 10% faster; decisions are cached on the graph.  families (nullable):
  * n_matched entries receiving PM_PLANS_ROOTED, PM_PLANS_FREE or (counting
  * plans, unless a set-operation family is forced) PM_PLANS_DECOMP. */
 pm_status pm_plan_autotune(pm_query_plan *p, void *stream, int32_t *families);
@@ -236,9 +240,11 @@ pm_status pm_morph(const pm_query_plan *p, const uint64_t *matched, uint64_t *re
 pm_status pm_count(pm_query_plan *p, void *stream, double timeout_s, uint64_t *counts,
                    uint64_t *matched);
 
-/* pm_count with a deadline per matched pattern: the matched patterns run
- * one after another (per-pattern launches), each with timeout_per_pattern_s,
- * capped by timeout_total_s from the start of the call (<= 0: no limit);
+/* pm_count with a deadline per matched pattern: with per-pattern launches
+ * the matched patterns run one after another, each with
+ * timeout_per_pattern_s; in PM_LAUNCH_SINGLE mode they share one launch and
+ * each has timeout_per_pattern_s from its start; either way capped by
+ * timeout_total_s from the start of the call (<= 0: no limit);
  * a query whose alternative set uses a pattern whose deadline expired gets
  * status PM_ETIMEOUT and count 0, the others PM_OK and their exact counts.
  * status: n_queries entries.  Returns PM_OK unless the call itself fails. */
@@ -260,14 +266,32 @@ pm_status pm_count_roots(pm_query_plan *p, void *stream, double timeout_s, const
  * is fixed into the graph; pm_count's own timeout_s is then ignored. */
 pm_status pm_plan_capture(pm_query_plan *p, void *stream, double timeout_s);
 
+/* pm_count_each recorded as one CUDA graph (the per-pattern and total
+ * deadlines are fixed into it); later pm_count_each calls on the plan replay
+ * it and ignore their own deadlines.  In PM_LAUNCH_SINGLE mode the plans
+ * share one persistent launch and every pattern's deadline runs from the
+ * launch start: the patterns whose work the deadline cuts (counted from
+ * per-plan progress counters) report PM_ETIMEOUT, the others their exact
+ * counts. */
+pm_status pm_plan_capture_each(pm_query_plan *p, void *stream, double timeout_per_pattern_s,
+                               double timeout_total_s);
+
 /* pm_count with an instrumented kernel that also returns the algorithmic
  * bytes of the matching: 4 B per element of every set-operation operand,
  * each operand cut to the plan's (lower, upper) id window (merge accounting
  * |A'| + |B'| per intersection or difference), 16 B per row-offset pair,
  * 28 B per task and 24 B plus 8 B per excluded vertex for each closed-form
- * count.  Slower than pm_count; meant for roofline measurement. */
+ * count, plus the bytes of the clique and decomposition kernels (below).
+ * Slower than pm_count; meant for roofline measurement. */
 pm_status pm_count_instrumented(pm_query_plan *p, void *stream, uint64_t *counts,
                                 uint64_t *alg_bytes);
+/* Algorithmic bytes of each matched pattern in the plan's last
+ * pm_count_instrumented (n_matched entries): its own launches in per-pattern
+ * mode, all set-operation plans on the first one in PM_LAUNCH_SINGLE mode,
+ * the decomposition passes (4 B per list element read, 16 B per row-offset
+ * pair, 4 B per counter read or written, 8 B per atomic update) on the first
+ * decomposed pattern, nothing for the wedge kernels. */
+pm_status pm_plan_pattern_bytes(const pm_query_plan *p, uint64_t *bytes);
 
 /* Device time (CUDA events on the launch stream) of the matching kernel of
  * the plan's last completed pm_count / pm_count_roots / pm_support call;

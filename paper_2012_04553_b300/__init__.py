@@ -110,6 +110,8 @@ def _load():
         "pm_domains_or": [vp, i32, i64, vp, vp],
         "pm_support_from_domains": [vp, vp, vp, ctypes.c_uint64, vp, vp],
         "pm_enumerate": [vp, vp, dbl, vp, vp, i64, ctypes.POINTER(i64)],
+        "pm_plan_capture_each": [vp, vp, dbl, dbl],
+        "pm_plan_pattern_bytes": [vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -140,7 +142,7 @@ ABI_SYMBOLS = [
     "pm_server_create", "pm_server_submit", "pm_server_wait", "pm_server_get_stats",
     "pm_server_destroy", "pm_plan_set_launch", "pm_count_each", "pm_plan_query_columns",
     "pm_plan_pattern_ms", "pm_plan_last_launches", "pm_support_roots", "pm_domains_or",
-    "pm_support_from_domains", "pm_enumerate",
+    "pm_support_from_domains", "pm_enumerate", "pm_plan_capture_each", "pm_plan_pattern_bytes",
 ]
 
 
@@ -364,6 +366,11 @@ class Plan:
         """Record this plan's pm_count as a CUDA graph; count() then replays it."""
         _check(_lib.pm_plan_capture(self._h, _stream_handle(stream), float(timeout_s)), "pm_plan_capture")
 
+    def capture_each(self, timeout_per_pattern_s=0.0, timeout_total_s=0.0, stream=None):
+        """Record count_each (deadlines fixed) as a CUDA graph replayed by count_each()."""
+        _check(_lib.pm_plan_capture_each(self._h, _stream_handle(stream), float(timeout_per_pattern_s),
+                                         float(timeout_total_s)), "pm_plan_capture_each")
+
     def autotune(self, stream=None):
         fam = np.zeros(self.n_matched, dtype=np.int32)
         _check(_lib.pm_plan_autotune(self._h, _stream_handle(stream), _ptr(fam)), "pm_plan_autotune")
@@ -390,6 +397,12 @@ class Plan:
         v = ctypes.c_float()
         _check(_lib.pm_plan_last_kernel_ms(self._h, ctypes.byref(v)), "pm_plan_last_kernel_ms")
         return float(v.value)
+
+    def pattern_bytes(self):
+        """Algorithmic bytes per matched pattern of the last count_instrumented()."""
+        b = np.zeros(self.n_matched, dtype=np.uint64)
+        _check(_lib.pm_plan_pattern_bytes(self._h, _ptr(b)), "pm_plan_pattern_bytes")
+        return [int(x) for x in b]
 
     def last_launches(self):
         """Library kernels launched by the last count()."""

@@ -90,6 +90,7 @@ struct pm_query_plan {
     std::vector<int> rooted_begin;
     std::vector<DevPlan> free_plans;
     std::vector<int> choice;        // per matched pattern: 0 rooted, 1 free, -1 undecided
+    std::vector<int> split_code;    // per matched pattern: task granularity (0: split / 4, 1: as compiled, 2: x 4)
     int forced = -1;                // pm_plan_select: -1 = autotuned per pattern
     int launch_mode = PM_LAUNCH_PER_PATTERN;
     PlanTable active;               // pm_count / pm_support
@@ -115,6 +116,7 @@ struct pm_query_plan {
     std::vector<cudaEvent_t> pat_ev;
     std::vector<char> pat_recorded;
     int64_t launches = 0;                    // library kernels launched by the last count
+    std::vector<uint64_t> pat_bytes;         // algorithmic bytes per matched pattern (instrumented count)
     unsigned long long *d_stats = nullptr;
     uint8_t *d_timed_out = nullptr;          // pm_count_each: expired matched patterns
     uint32_t *d_wedge = nullptr;             // wedge-kernel counters: blocks x n, kept zero
@@ -123,6 +125,9 @@ struct pm_query_plan {
     int64_t list_cap = 0, heavy_from = 0;
     size_t bytes_lists = 0;
     bool wedge_ready = false;
+    unsigned int *d_plan_done = nullptr;     // per-plan progress (single launch, per-pattern deadlines)
+    size_t plan_done_cap = 0;
+    cudaGraphExec_t graph_each = nullptr;    // pm_plan_capture_each: pm_count_each as a CUDA graph
     int32_t *d_spill = nullptr;              // clique-kernel spill sets (per warp)
     int64_t spill_len = 0;
     size_t bytes_counters = 0, bytes_bitsets = 0, bytes_cols = 0, bytes_wedge = 0, bytes_spill = 0;
@@ -246,7 +251,7 @@ void free_plan_device(pm_query_plan *p) {
     dev_free(p->d_col_off, p->bytes_cols, dev);
     dev_free(p->d_col_src, p->bytes_cols, dev);
     dev_free(p->d_popc, p->bytes_cols, dev);
-    dev_free(p->d_stats, 256, dev);
+    dev_free(p->d_stats, std::max<size_t>(256, sizeof(unsigned long long) * (p->morph.matched.size() + 1)), dev);
     dev_free(p->d_timed_out, std::max<size_t>(p->morph.matched.size(), 1), dev);
     p->d_timed_out = nullptr;
     dev_free(p->d_wedge, p->bytes_wedge, dev);
@@ -260,6 +265,9 @@ void free_plan_device(pm_query_plan *p) {
     p->d_spill = nullptr;
     p->bytes_spill = 0;
     p->spill_ready = false;
+    dev_free(p->d_plan_done, sizeof(unsigned int) * 3 * p->plan_done_cap, dev);
+    p->d_plan_done = nullptr;
+    p->plan_done_cap = 0;
     dev_free(p->d_targets, p->bytes_targets, dev);
     dev_free(p->d_tslot, p->bytes_tslot, dev);
     dev_free(p->d_dW, p->bytes_dW, dev);
@@ -607,6 +615,7 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
             }
             mark(t.plans[b].counter, 0);
             p->launches += 3;
+            G.stats = stats ? stats + 1 + t.plans[b].counter : nullptr;   // bytes per matched pattern
             const int rc = domains ? launch_domains(G, s) : launch_count(G, s);
             if (rc) return PM_ECUDA;
             mark(t.plans[b].counter, 1);
@@ -614,11 +623,41 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
         }
     } else if (n_setops > 0 && L.n_echunks > 0) {
         L.nplans = n_setops;
+        if (gate_flags) {
+            // per-pattern deadlines inside the one launch: every pattern gets
+            // the budget from the launch start; plans whose work is cut are
+            // flagged from their progress counters afterwards
+            if (!p->d_plan_done || p->plan_done_cap < size_t(n_setops)) {
+                dev_free(p->d_plan_done, sizeof(unsigned int) * 3 * p->plan_done_cap, g->device);
+                p->plan_done_cap = size_t(n_setops);
+                p->d_plan_done = (unsigned int *)dev_alloc(sizeof(unsigned int) * 3 * p->plan_done_cap,
+                                                           g->device);
+                if (!p->d_plan_done) {
+                    p->plan_done_cap = 0;
+                    set_error("device allocation failed (plan progress)");
+                    return PM_ENOMEM;
+                }
+            }
+            cudaMemsetAsync(p->d_plan_done, 0, sizeof(unsigned int) * 3 * size_t(n_setops), s);
+            L.plan_done = p->d_plan_done;
+            p->launches++;
+            if (launch_pattern_gate(p->d_ctl, gate_flags, -1, gate_budget_ns, s)) return PM_ECUDA;
+        }
         p->launches += 3;
+        L.stats = stats ? stats + 1 + t.plans[0].counter : nullptr;     // one launch: all on the first
         const int rc = domains ? launch_domains(L, s) : launch_count(L, s);
         if (rc) return PM_ECUDA;
+        if (gate_flags) {
+            const int64_t stride = sample_stride > 1 ? sample_stride : 1;
+            p->launches++;
+            if (launch_plan_flags(p->d_ctl, t.d, n_setops, p->d_plan_done,
+                                  (unsigned long long)((L.n_echunks + stride - 1) / stride), gate_flags, s))
+                return PM_ECUDA;
+        }
     }
-    int last = n_setops > 0 ? t.plans[n_setops - 1].counter : -1;
+    int last = n_setops > 0 && !(gate_flags && p->launch_mode == PM_LAUNCH_SINGLE)
+                   ? t.plans[n_setops - 1].counter
+                   : -1;
     for (size_t i = size_t(n_setops); i < t.plans.size(); i++) {
         const DevPlan &dp = t.plans[i];
         if (domains) {
@@ -639,7 +678,8 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
                                    p->d_ctl, s))
                 return PM_ECUDA;
         } else if (launch_clique(L.g, tasks, dp.k, dp.counter, p->d_counters, p->d_spill,
-                                 p->spill_len, sample_stride, p->d_ctl, stats, s)) {
+                                 p->spill_len, sample_stride, p->d_ctl,
+                                 stats ? stats + 1 + dp.counter : nullptr, s)) {
             return PM_ECUDA;
         }
         mark(dp.counter, 1);
@@ -680,6 +720,7 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
         D.path_blocks = p->dpath_blocks;
         D.basis = p->d_basis;
         D.ctl = p->d_ctl;
+        D.stats = stats ? stats + 1 + first : nullptr;
         p->launches += 3 + int((D.passes & DP_TRI2) != 0) + int((D.passes & DP_PATHS) != 0) +
                        2 * int((D.passes & DP_LOCAL) != 0) + 1;
         if (launch_decomp(D, s)) return PM_ECUDA;
@@ -700,11 +741,23 @@ void rezero_wedge(pm_query_plan *p, cudaStream_t s) {
     if (p->d_dW) cudaMemsetAsync(p->d_dW, 0, p->bytes_dW, s);
 }
 
-// The plans of matched pattern j in family f (0 rooted, 1 free).
+// Task granularity: the second-level candidates a chunk keeps before the
+// rest is deferred to other warps (hub roots), scaled by split code 0 (/4),
+// 1 (as compiled) or 2 (x4).
+void scale_split(DevPlan &dp, int code) {
+    if (code == 0) dp.split = std::max(8, dp.split / 4);
+    else if (code == 2) dp.split = std::min(1 << 20, dp.split * 4);
+}
+
+// The plans of matched pattern j in family f (0 rooted, 1 free), with the
+// split code of the pattern (when tuned).
 std::vector<DevPlan> family_plans(const pm_query_plan *p, size_t j, int f) {
-    if (f == PM_PLANS_FREE) return {p->free_plans[j]};
-    return std::vector<DevPlan>(p->rooted.begin() + p->rooted_begin[j],
-                                p->rooted.begin() + p->rooted_begin[j + 1]);
+    std::vector<DevPlan> v;
+    if (f == PM_PLANS_FREE) v = {p->free_plans[j]};
+    else v.assign(p->rooted.begin() + p->rooted_begin[j], p->rooted.begin() + p->rooted_begin[j + 1]);
+    if (j < p->split_code.size())
+        for (DevPlan &dp : v) scale_split(dp, p->split_code[j]);
+    return v;
 }
 
 // Decomposable patterns of counting plans use the decomposition kernels
@@ -735,6 +788,8 @@ pm_status autotune(pm_query_plan *p, cudaStream_t s) {
             auto it = g->tuned.find(key);
             if (it != g->tuned.end()) {
                 p->choice[j] = it->second;
+                auto sp = g->tuned_split.find(key);
+                p->split_code[j] = sp != g->tuned_split.end() ? sp->second : 1;
                 continue;
             }
         }
@@ -778,9 +833,48 @@ pm_status autotune(pm_query_plan *p, cudaStream_t s) {
             }
             if (ms < best) { best = ms; best_f = f; }
         }
+        // task granularity of the chosen family (set-operation plans only):
+        // a quarter and four times the compiled split on the same sample
+        int best_code = 1;
+        std::vector<DevPlan> chosen = family_plans(p, j, best_f);
+        bool setops = !chosen.empty();
+        for (const DevPlan &dp : chosen) setops &= dp.kind == PLAN_SETOPS && dp.n_enum >= 3;
+        if (setops && std::isfinite(best)) {
+            for (int code : {0, 2}) {
+                PlanTable t;
+                t.plans = chosen;
+                for (DevPlan &dp : t.plans) {
+                    dp.counter = 0;
+                    scale_split(dp, code);
+                }
+                pm_status st = upload_table(t, g->device);
+                if (st != PM_OK) return st;
+                const int64_t ech = echunks_for(t.plans, tasks);
+                const int stride = int(std::max<int64_t>(1, ech / 4096));
+                cudaError_t e = cudaMemsetAsync(p->d_counters, 0, p->bytes_counters, s);
+                if (!e && launch_arm(p->d_ctl, uint64_t(5e8), s)) e = cudaErrorLaunchFailure;
+                if (!e) e = cudaEventRecord(p->ev0, s);
+                if (!e && launch_table(p, t, tasks, stride, false, nullptr, s) != PM_OK)
+                    e = cudaErrorLaunchFailure;
+                if (!e) e = cudaEventRecord(p->ev1, s);
+                Control ctl{};
+                if (!e) e = cudaMemcpyAsync(&ctl, p->d_ctl, sizeof(Control), cudaMemcpyDeviceToHost, s);
+                if (!e) e = cudaStreamSynchronize(s);
+                float ms = 0.f;
+                if (!e) e = cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+                free_table(t, g->device);
+                if (e) return cuda_fail("autotune (split)", e);
+                if (ctl.status != 1 && ms < 0.9f * best) {
+                    best = ms;
+                    best_code = code;
+                }
+            }
+        }
         p->choice[j] = best_f;
+        p->split_code[j] = best_code;
         std::lock_guard<std::mutex> lk(g->tune_mu);
         g->tuned[key] = best_f;
+        g->tuned_split[key] = best_code;
         g->tuned_ms[key] = best;
     }
     return PM_OK;
@@ -945,12 +1039,13 @@ pm_status run_count(pm_query_plan *p, void *stream, double timeout_s, const int3
     const uint64_t budget = timeout_s > 0 ? uint64_t(timeout_s * 1e9) : 0;
     p->launches = 1;
     if (launch_arm(p->d_ctl, budget, s)) return PM_ECUDA;
+    const size_t stat_bytes = std::max<size_t>(256, sizeof(unsigned long long) * (nm + 1));
     if (alg_bytes && !p->d_stats) {
-        p->d_stats = (unsigned long long *)dev_alloc(256, g->device);
+        p->d_stats = (unsigned long long *)dev_alloc(stat_bytes, g->device);
         if (!p->d_stats) return PM_ENOMEM;
     }
     if (alg_bytes) {
-        e = cudaMemsetAsync(p->d_stats, 0, sizeof(unsigned long long), s);
+        e = cudaMemsetAsync(p->d_stats, 0, sizeof(unsigned long long) * (nm + 1), s);
         if (e) return cuda_fail("pm_count: memset", e);
     }
     cudaEventRecord(p->ev0, s);
@@ -960,11 +1055,18 @@ pm_status run_count(pm_query_plan *p, void *stream, double timeout_s, const int3
     cudaEventRecord(p->ev1, s);
     p->timed = true;
     if (alg_bytes) {
-        unsigned long long v = 0;
-        e = cudaMemcpyAsync(&v, p->d_stats, sizeof(v), cudaMemcpyDeviceToHost, s);
+        std::vector<unsigned long long> v(nm + 1);
+        e = cudaMemcpyAsync(v.data(), p->d_stats, sizeof(unsigned long long) * (nm + 1),
+                            cudaMemcpyDeviceToHost, s);
         if (!e) e = cudaStreamSynchronize(s);
         if (e) return cuda_fail("pm_count: stats readback", e);
-        *alg_bytes = v;
+        uint64_t total = 0;
+        p->pat_bytes.assign(nm, 0);
+        for (size_t j = 0; j < nm; j++) {
+            p->pat_bytes[j] = v[j + 1];
+            total += v[j + 1];
+        }
+        *alg_bytes = total + v[0];
     }
     std::vector<uint64_t> raw(2 * nm);
     Control ctl;
@@ -1006,8 +1108,31 @@ pm_status run_count_each(pm_query_plan *p, void *stream, double timeout_s, doubl
         p->d_timed_out = (uint8_t *)dev_alloc(std::max<size_t>(nm, 1), g->device);
         if (!p->d_timed_out) return PM_ENOMEM;
     }
+    if (p->graph_each) {
+        // replay of pm_plan_capture_each (its deadlines are fixed in the graph)
+        cudaError_t e = cudaGraphLaunch(p->graph_each, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        if (e) return cuda_fail("pm_count_each (graph replay)", e);
+        std::vector<uint8_t> flags(nm);
+        std::memcpy(flags.data(), reinterpret_cast<uint8_t *>(p->h_pinned + 2 * nm) + sizeof(Control), nm);
+        bool any = false;
+        for (size_t j = 0; j < nm; j++) any |= flags[j] != 0;
+        if (any) {
+            rezero_wedge(p, s);
+            cudaStreamSynchronize(s);
+        }
+        p->timed = true;
+        st = pm_morph(p, p->h_pinned, counts);
+        if (st != PM_OK) return st;
+        for (size_t i = 0; i < p->morph.terms.size(); i++) {
+            status[i] = PM_OK;
+            for (const Term &t : p->morph.terms[i])
+                if (flags[t.matched]) status[i] = PM_ETIMEOUT;
+            if (status[i] != PM_OK) counts[2 * i] = counts[2 * i + 1] = 0;
+        }
+        return PM_OK;
+    }
     const int saved_mode = p->launch_mode;
-    p->launch_mode = PM_LAUNCH_PER_PATTERN;
     cudaError_t e = cudaMemsetAsync(p->d_counters, 0, p->bytes_counters, s);
     if (!e) e = cudaMemsetAsync(p->d_timed_out, 0, std::max<size_t>(nm, 1), s);
     if (e) {
@@ -1193,6 +1318,7 @@ pm_status pm_plan(const pm_graph *g, const pm_pattern *queries, int32_t nq, pm_o
                                                   p->morph.matched_orbit[j], op == PM_OP_COUNT));
     }
     p->choice.assign(nm, -1);
+    p->split_code.assign(nm, 1);
     p->decomp_f.assign(nm, -1);
     if (op == PM_OP_COUNT)
         for (size_t j = 0; j < nm; j++) p->decomp_f[j] = decomp_formula(p->morph.matched[j]);
@@ -1250,7 +1376,7 @@ pm_status pm_plan_export(const pm_query_plan *p, int32_t family, void *out, int6
 
 pm_status pm_plan_set_launch(pm_query_plan *p, int32_t mode) {
     if (!p || (mode != PM_LAUNCH_PER_PATTERN && mode != PM_LAUNCH_SINGLE)) return PM_EINVAL;
-    if (p->graph_exec) {
+    if (p->graph_exec || p->graph_each) {
         set_error("pm_plan_set_launch: the plan was already captured");
         return PM_EINVAL;
     }
@@ -1291,6 +1417,13 @@ pm_status pm_plan_last_kernel_ms(const pm_query_plan *p, float *ms) {
     return PM_OK;
 }
 
+pm_status pm_plan_pattern_bytes(const pm_query_plan *p, uint64_t *bytes) {
+    if (!p || !bytes) return PM_EINVAL;
+    for (size_t j = 0; j < p->morph.matched.size(); j++)
+        bytes[j] = j < p->pat_bytes.size() ? p->pat_bytes[j] : 0;
+    return PM_OK;
+}
+
 pm_status pm_plan_last_launches(const pm_query_plan *p, int64_t *launches) {
     if (!p || !launches) return PM_EINVAL;
     *launches = p->launches;
@@ -1316,6 +1449,7 @@ void pm_free_plan(pm_query_plan *p) {
         free_plan_device(p);
     }
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->graph_each) cudaGraphExecDestroy(p->graph_each);
     if (p->h_pinned) cudaFreeHost(p->h_pinned);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
@@ -1365,20 +1499,23 @@ pm_status pm_count(pm_query_plan *p, void *stream, double timeout_s, uint64_t *c
     return run_count(p, stream, timeout_s, nullptr, 0, false, counts, matched);
 }
 
-pm_status pm_plan_capture(pm_query_plan *p, void *stream, double timeout_s) {
+// pm_count (each = false) or pm_count_each (each = true) recorded as one
+// CUDA graph; every allocation and the autotuning happen before capture.
+static pm_status capture_impl(pm_query_plan *p, void *stream, double timeout_s, double per_pattern_s,
+                              bool each) {
+    const char *who = each ? "pm_plan_capture_each" : "pm_plan_capture";
     if (!p || !p->g) {
-        set_error("pm_plan_capture: plan without a graph");
+        set_error(std::string(who) + ": plan without a graph");
         return PM_EINVAL;
     }
     if (p->op != PM_OP_COUNT) {
-        set_error("pm_plan_capture: counting plans only");
+        set_error(std::string(who) + ": counting plans only");
         return PM_EINVAL;
     }
     const pm_graph *g = p->g;
     DeviceGuard dg(g->device);
     if (!dg.ok) return PM_ECUDA;
     cudaStream_t user = (cudaStream_t)stream;
-    // everything that allocates or tunes happens before capture
     pm_status st = ensure_device(p);
     if (st == PM_OK) st = prepare_active(p, user);
     if (st != PM_OK) return st;
@@ -1400,29 +1537,50 @@ pm_status pm_plan_capture(pm_query_plan *p, void *stream, double timeout_s) {
         if (st != PM_OK) return st;
     }
     const size_t nm = p->morph.matched.size();
+    if (each && !p->d_timed_out) {
+        p->d_timed_out = (uint8_t *)dev_alloc(std::max<size_t>(nm, 1), g->device);
+        if (!p->d_timed_out) return PM_ENOMEM;
+    }
+    if (each && p->launch_mode == PM_LAUNCH_SINGLE && !p->active.plans.empty() &&
+        (!p->d_plan_done || p->plan_done_cap < p->active.plans.size())) {
+        dev_free(p->d_plan_done, sizeof(unsigned int) * 3 * p->plan_done_cap, g->device);
+        p->plan_done_cap = p->active.plans.size();
+        p->d_plan_done = (unsigned int *)dev_alloc(sizeof(unsigned int) * 3 * p->plan_done_cap, g->device);
+        if (!p->d_plan_done) {
+            p->plan_done_cap = 0;
+            return PM_ENOMEM;
+        }
+    }
     if (!p->h_pinned) {
-        cudaError_t e = cudaMallocHost(&p->h_pinned, sizeof(uint64_t) * 2 * nm + sizeof(Control));
-        if (e) return cuda_fail("pm_plan_capture: pinned buffer", e);
+        // counters, the control block, then the per-pattern expiry flags
+        cudaError_t e = cudaMallocHost(&p->h_pinned, sizeof(uint64_t) * 2 * nm + sizeof(Control) + nm + 8);
+        if (e) return cuda_fail(who, e);
     }
     cudaError_t e = cudaStreamSynchronize(user);
-    if (e) return cuda_fail("pm_plan_capture", e);
+    if (e) return cuda_fail(who, e);
     cudaStream_t cs;
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-    if (e) return cuda_fail("pm_plan_capture: stream", e);
+    if (e) return cuda_fail(who, e);
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
     if (!e) {
         const DevTasks tasks = all_tasks(g);
         cudaMemsetAsync(p->d_counters, 0, p->bytes_counters, cs);
+        if (each) cudaMemsetAsync(p->d_timed_out, 0, std::max<size_t>(nm, 1), cs);
         const uint64_t budget = timeout_s > 0 ? uint64_t(timeout_s * 1e9) : 0;
+        const uint64_t per = each && per_pattern_s > 0 ? uint64_t(per_pattern_s * 1e9) : 0;
         p->launches = 1;
         launch_arm(p->d_ctl, budget, cs);
         cudaEventRecord(p->ev0, cs);
-        st = launch_table(p, p->active, tasks, 1, false, nullptr, cs, 0, nullptr, true, true);
+        st = launch_table(p, p->active, tasks, 1, false, nullptr, cs, per,
+                          each ? p->d_timed_out : nullptr, true, true);
         cudaEventRecord(p->ev1, cs);
         cudaMemcpyAsync(p->h_pinned, p->d_counters, sizeof(uint64_t) * 2 * nm,
                         cudaMemcpyDeviceToHost, cs);
         cudaMemcpyAsync(p->h_pinned + 2 * nm, p->d_ctl, sizeof(Control), cudaMemcpyDeviceToHost, cs);
+        if (each)
+            cudaMemcpyAsync(reinterpret_cast<uint8_t *>(p->h_pinned + 2 * nm) + sizeof(Control),
+                            p->d_timed_out, nm, cudaMemcpyDeviceToHost, cs);
         e = cudaStreamEndCapture(cs, &graph);
     }
     cudaStreamDestroy(cs);
@@ -1430,15 +1588,25 @@ pm_status pm_plan_capture(pm_query_plan *p, void *stream, double timeout_s) {
         if (graph) cudaGraphDestroy(graph);
         return st;
     }
-    if (e) return cuda_fail("pm_plan_capture: capture", e);
-    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
-    e = cudaGraphInstantiate(&p->graph_exec, graph, 0);
+    if (e) return cuda_fail(who, e);
+    cudaGraphExec_t &slot = each ? p->graph_each : p->graph_exec;
+    if (slot) cudaGraphExecDestroy(slot);
+    e = cudaGraphInstantiate(&slot, graph, 0);
     cudaGraphDestroy(graph);
     if (e) {
-        p->graph_exec = nullptr;
-        return cuda_fail("pm_plan_capture: instantiate", e);
+        slot = nullptr;
+        return cuda_fail(who, e);
     }
     return PM_OK;
+}
+
+pm_status pm_plan_capture(pm_query_plan *p, void *stream, double timeout_s) {
+    return capture_impl(p, stream, timeout_s, 0.0, false);
+}
+
+pm_status pm_plan_capture_each(pm_query_plan *p, void *stream, double timeout_per_pattern_s,
+                               double timeout_total_s) {
+    return capture_impl(p, stream, timeout_total_s, timeout_per_pattern_s, true);
 }
 
 pm_status pm_count_roots(pm_query_plan *p, void *stream, double timeout_s, const int32_t *roots,
@@ -1595,15 +1763,17 @@ pm_status pm_enumerate(pm_query_plan *p, void *stream, double timeout_s, int32_t
     // maps per matched pattern: (query, f) with f[u] = vertex of the matched
     // pattern that vertex u of the query goes to
     std::vector<std::vector<std::pair<int, Perm>>> maps(nm);
-    for (size_t i = 0; i < nq; i++) {
-        Pat q = p->morph.queries[i];
-        if (q.is_clique()) q.vi = false;
-        for (const Term &t : p->morph.terms[i]) {
+    for (size_t i = 0; i < nq; i++)
+        for (const Term &t : p->morph.terms[i])
             if (t.coef <= 0) {
                 set_error("pm_enumerate: a vertex-induced query morphed to edge-induced patterns "
                           "(Corollary 3.1 subtracts) cannot be listed; plan it with PM_MORPH_NONE");
                 return PM_EUNSUPPORTED;
             }
+    for (size_t i = 0; i < nq; i++) {
+        Pat q = p->morph.queries[i];
+        if (q.is_clique()) q.vi = false;
+        for (const Term &t : p->morph.terms[i]) {
             const Pat &mq = p->morph.matched[t.matched];
             std::vector<Perm> fs;
             if (q.vi) {

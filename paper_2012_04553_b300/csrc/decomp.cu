@@ -61,6 +61,21 @@ __device__ __forceinline__ void flush(uint64_t *basis, int idx, u128 v, int lane
     if (lane == 0 && v != 0) add_u128(basis + 2 * idx, v);
 }
 
+// Algorithmic bytes (instrumented runs, stats != nullptr): 4 B per element of
+// every list read (each operand of an intersection cut to its id window, the
+// elements a binary search probes), 16 B per row-offset pair, 4 B per
+// counter read or written (8 B for an atomic update).
+__device__ __forceinline__ uint64_t probe_bytes(int64_t len) {
+    return 4ull * uint64_t(len > 1 ? 65 - __clzll(uint64_t(len)) : 1);
+}
+
+__device__ __forceinline__ void flush_stat(unsigned long long *stats, uint64_t v, int lane) {
+    if (!stats) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (lane == 0 && v) atomicAdd(stats, (unsigned long long)v);
+}
+
 __device__ __forceinline__ bool dc_stop(Control *ctl, uint64_t deadline, int lane) {
     int stop = 0;
     if (lane == 0) {
@@ -79,6 +94,8 @@ struct TriArgs {
     int32_t *t;         // per CSR slot
     uint64_t *basis;
     Control *ctl;
+    unsigned long long *stats;   // nullable: algorithmic bytes
+    int with_c5;        // MODE 0: also the 5-cycle triangle term
 };
 
 // Triangle passes over the tasks (a, b), b < a, with the strided chunk
@@ -98,6 +115,7 @@ __global__ void __launch_bounds__(DC_WARPS * 32) tri_kernel(TriArgs A) {
     const int64_t *off = A.tasks.off[TASKS_LOWER];
     const unsigned long long n_chunks = (unsigned long long)((ntasks + 31) / 32);
     u128 acc0 = 0, acc1 = 0, tri = 0;
+    uint64_t stat = 0;
     while (true) {
         unsigned long long w = 0;
         if (lane == 0) w = atomicAdd(&ctl->work3, 1ull);
@@ -134,6 +152,7 @@ __global__ void __launch_bounds__(DC_WARPS * 32) tri_kernel(TriArgs A) {
             }
             lb = __shfl_sync(FULL, lb, 0);
             pba = __shfl_sync(FULL, pba, 0);
+            if (A.stats && lane == 0) stat += 32 + 4ull * uint64_t(la + lb) + (MODE == 1 ? 4 : 8);
             const int32_t n = la <= lb ? la : lb;
             if (n == 0) continue;
             const bool from_a = la <= lb;
@@ -158,9 +177,13 @@ __global__ void __launch_bounds__(DC_WARPS * 32) tri_kernel(TriArgs A) {
                             atomicAdd(A.t + s_ac, 1);
                             atomicAdd(A.t + s_bc, 1);
                             cnt++;
-                            const int32_t pxa = lower_bound_dev(g.col + rowx, dx, ra);
-                            acc0 += u128(uint64_t(up_ab + int64_t(dx - pxa - 1)));
+                            if (A.with_c5) {
+                                const int32_t pxa = lower_bound_dev(g.col + rowx, dx, ra);
+                                acc0 += u128(uint64_t(up_ab + int64_t(dx - pxa - 1)));
+                            }
+                            if (A.stats) stat += 16 + (A.with_c5 ? 16 + probe_bytes(dx) : 0);
                         } else {
+                            if (A.stats) stat += 24;
                             const int64_t tac = __ldg(A.t + s_ac), tbc = __ldg(A.t + s_bc);
                             const int64_t tab = t_ab;
                             acc0 += u128(uint64_t((tab - 1) * dx + (tbc - 1) * da + (tac - 1) * db));
@@ -179,6 +202,7 @@ __global__ void __launch_bounds__(DC_WARPS * 32) tri_kernel(TriArgs A) {
             }
         }
     }
+    flush_stat(A.stats, stat, lane);
     if (MODE == 0) {
         flush(A.basis, DB_C5TRI, acc0, lane);
         flush(A.basis, DB_TRI, tri, lane);
@@ -189,27 +213,35 @@ __global__ void __launch_bounds__(DC_WARPS * 32) tri_kernel(TriArgs A) {
 }
 
 // t of every slot (u, v) with v > u from the canonical slot (v, u) in v's row.
-__global__ void __launch_bounds__(DC_WARPS * 32) mirror_kernel(DevGraph g, int32_t *t) {
+__global__ void __launch_bounds__(DC_WARPS * 32) mirror_kernel(DevGraph g, int32_t *t,
+                                                              unsigned long long *stats) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = int64_t(gridDim.x) * DC_WARPS;
+    uint64_t stat = 0;
     for (int64_t u = int64_t(blockIdx.x) * DC_WARPS + (threadIdx.x >> 5); u < g.n; u += warps) {
         const int64_t row = __ldg(g.rowptr + u);
         const int32_t d = int32_t(__ldg(g.rowptr + u + 1) - row);
         const int32_t lo = lower_bound_dev(g.col + row, d, int32_t(u));
+        if (stats && lane == 0) stat += 16 + probe_bytes(d);
         for (int32_t j = lo + lane; j < d; j += 32) {
             const int32_t v = __ldg(g.col + row + j);
             const int64_t rv = __ldg(g.rowptr + v);
-            const int32_t p = lower_bound_dev(g.col + rv, int32_t(__ldg(g.rowptr + v + 1) - rv), int32_t(u));
+            const int32_t dv = int32_t(__ldg(g.rowptr + v + 1) - rv);
+            const int32_t p = lower_bound_dev(g.col + rv, dv, int32_t(u));
             t[row + j] = t[rv + p];
+            if (stats) stat += 4 + 16 + probe_bytes(dv) + 8;
         }
     }
+    flush_stat(stats, stat, lane);
 }
 
 // Sums over vertices and edges (each undirected edge once, from its higher
 // endpoint u towards x < u).
 __global__ void __launch_bounds__(DC_WARPS * 32) ve_kernel(DevGraph g, const int32_t *__restrict__ t,
                                                           const uint32_t *__restrict__ k4e,
-                                                          uint64_t *basis, Control *ctl) {
+                                                          uint64_t *basis, Control *ctl,
+                                                          unsigned long long *stats) {
+    uint64_t stat = 0;
     const int lane = threadIdx.x & 31;
     const int64_t warps = int64_t(gridDim.x) * DC_WARPS;
     u128 p4e = 0, bull = 0, lolli_e = 0, de = 0, kite = 0, dart_e = 0, book = 0;
@@ -219,6 +251,8 @@ __global__ void __launch_bounds__(DC_WARPS * 32) ve_kernel(DevGraph g, const int
         const int64_t row = __ldg(g.rowptr + u);
         const int64_t d = __ldg(g.rowptr + u + 1) - row;
         uint64_t st = 0, S = 0, S1 = 0, S2 = 0;
+        if (stats) stat += lane == 0 ? 16 : 0;
+        if (stats) stat += (d > lane ? uint64_t((d - 1 - lane) / 32 + 1) : 0) * (k4e ? 28 : 24);
         for (int64_t j = lane; j < d; j += 32) {
             const int32_t x = __ldg(g.col + row + j);
             const int64_t tx = __ldg(t + row + j);
@@ -291,6 +325,7 @@ __global__ void __launch_bounds__(DC_WARPS * 32) ve_kernel(DevGraph g, const int
         flush(basis, DB_K5P3, k5p3, lane);
         flush(basis, DB_K4DEG3, k4deg3, lane);
     }
+    flush_stat(stats, stat, lane);
     (void)ctl;
 }
 
@@ -308,7 +343,8 @@ __global__ void __launch_bounds__(DC_WARPS * 32) ve_kernel(DevGraph g, const int
 __global__ void __launch_bounds__(P2_THREADS) paths2_kernel(DevGraph g, const int32_t *__restrict__ t,
                                                             uint32_t *Wall, int32_t *touched_all,
                                                             uint64_t *basis, Control *ctl,
-                                                            int with_c5) {
+                                                            int with_c5, unsigned long long *stats) {
+    uint64_t stat = 0;
     __shared__ unsigned long long s_root;
     __shared__ int s_stop;
     __shared__ int s_nt;
@@ -334,11 +370,14 @@ __global__ void __launch_bounds__(P2_THREADS) paths2_kernel(DevGraph g, const in
         const int64_t rowa = __ldg(g.rowptr + a);
         const int32_t da = int32_t(__ldg(g.rowptr + a + 1) - rowa);
         const int32_t la = lower_bound_dev(g.col + rowa, da, a);
+        if (stats && tid == 0) stat += 16 + probe_bytes(da) + 4ull * uint64_t(la);
         // walk 1
         for (int i = warp; i < la; i += nwarps) {
             const int32_t b = __ldg(g.col + rowa + i);
             const int64_t rowb = __ldg(g.rowptr + b);
             const int32_t bl = lower_bound_dev(g.col + rowb, int32_t(__ldg(g.rowptr + b + 1) - rowb), a);
+            if (stats && lane == 0)
+                stat += 2 * (16 + probe_bytes(__ldg(g.rowptr + b + 1) - rowb)) + uint64_t(bl) * (12 + 28);
             for (int32_t j = lane; j < bl; j += 32) {
                 const int32_t c = __ldg(g.col + rowb + j);
                 const uint32_t old = atomicAdd(W + c, 1u);
@@ -375,9 +414,12 @@ __global__ void __launch_bounds__(P2_THREADS) paths2_kernel(DevGraph g, const in
             const int32_t c = touched[q];
             const uint32_t w = W[c];
             if (lane == 0) k23 += c3(w);
+            if (stats && lane == 0) stat += 8 + 4;       // touched entry, its counter, the reset
             if (with_c5) {
                 const int64_t rowc = __ldg(g.rowptr + c);
                 const int32_t lc = lower_bound_dev(g.col + rowc, int32_t(__ldg(g.rowptr + c + 1) - rowc), c);
+                if (stats && lane == 0)
+                    stat += 16 + probe_bytes(__ldg(g.rowptr + c + 1) - rowc) + 8ull * uint64_t(lc);
                 uint64_t s = 0;
                 for (int32_t j = lane; j < lc; j += 32) s += W[__ldg(g.col + rowc + j)];
 #pragma unroll
@@ -396,6 +438,7 @@ __global__ void __launch_bounds__(P2_THREADS) paths2_kernel(DevGraph g, const in
     flush(basis, DB_C5CORR, corr, lane);
     flush(basis, DB_C5TM, tm, lane);
     flush(basis, DB_K23I, k23, lane);
+    flush_stat(stats, stat, lane);
 }
 
 __device__ __forceinline__ u128 ld128(const uint64_t *basis, int i) {
@@ -488,21 +531,23 @@ int launch_decomp(const DecompLaunch &L, void *stream) {
     cudaGetDevice(&device);
     cudaStream_t s = (cudaStream_t)stream;
     cudaMemsetAsync(L.basis, 0, sizeof(uint64_t) * 2 * DB_COUNT, s);
-    TriArgs A{L.g, L.tasks, L.t, L.basis, L.ctl};
+    TriArgs A{L.g, L.tasks, L.t, L.basis, L.ctl, L.stats, (L.passes & DP_C5) ? 1 : 0};
     cudaMemsetAsync(L.t, 0, sizeof(int32_t) * size_t(L.g.nnz), s);
     cudaMemsetAsync(&L.ctl->work3, 0, sizeof(unsigned long long), s);
     tri_kernel<0><<<dc_blocks(device, (const void *)tri_kernel<0>), DC_WARPS * 32, 0, s>>>(A);
-    mirror_kernel<<<dc_blocks(device, (const void *)mirror_kernel), DC_WARPS * 32, 0, s>>>(L.g, L.t);
+    mirror_kernel<<<dc_blocks(device, (const void *)mirror_kernel), DC_WARPS * 32, 0, s>>>(L.g, L.t,
+                                                                                      L.stats);
     if (L.passes & DP_LOCAL) {
         if (L.k4e) cudaMemsetAsync(L.k4e, 0, sizeof(uint32_t) * size_t(L.g.nnz), s);
         cudaMemsetAsync(&L.ctl->work3, 0, sizeof(unsigned long long), s);
         LocalArgs la = L.local;
         la.k4e = (L.passes & DP_K4E) ? L.k4e : nullptr;
         la.want_k5 = (L.passes & DP_K5) ? 1 : 0;
+        la.stats = L.stats;
         if (launch_local(la, L.local_blocks, s)) return -1;
     }
     ve_kernel<<<dc_blocks(device, (const void *)ve_kernel), DC_WARPS * 32, 0, s>>>(
-        L.g, L.t, (L.passes & DP_K4E) ? L.k4e : nullptr, L.basis, L.ctl);
+        L.g, L.t, (L.passes & DP_K4E) ? L.k4e : nullptr, L.basis, L.ctl, L.stats);
     if (L.passes & DP_TRI2) {
         cudaMemsetAsync(&L.ctl->work3, 0, sizeof(unsigned long long), s);
         tri_kernel<1><<<dc_blocks(device, (const void *)tri_kernel<1>), DC_WARPS * 32, 0, s>>>(A);
@@ -510,7 +555,7 @@ int launch_decomp(const DecompLaunch &L, void *stream) {
     if (L.passes & DP_PATHS) {
         cudaMemsetAsync(&L.ctl->work3, 0, sizeof(unsigned long long), s);
         paths2_kernel<<<L.path_blocks, P2_THREADS, 0, s>>>(L.g, L.t, L.W, L.touched, L.basis, L.ctl,
-                                                           (L.passes & DP_C5) ? 1 : 0);
+                                                           (L.passes & DP_C5) ? 1 : 0, L.stats);
     }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) {

@@ -41,6 +41,7 @@ struct pm_graph {
     mutable std::mutex tune_mu;
     mutable std::map<pm::Key, int> tuned;
     mutable std::map<pm::Key, double> tuned_ms;   // sampled time of the chosen family
+    mutable std::map<pm::Key, int> tuned_split;   // chosen task granularity (split code)
     mutable std::map<int, double> decomp_ms;      // decomposition time per pass set
     pm::DevGraph dev() const {
         return pm::DevGraph{n, 2 * m, d_rowptr, d_col, d_labels,
@@ -129,7 +130,10 @@ struct MatchLaunch {
     unsigned long long *list_cursor;
     int64_t list_cap;
     const int32_t *old_of;
+    unsigned int *plan_done;   // per-plan progress (3 x nplans, zeroed), or nullptr
 };
+int launch_plan_flags(Control *ctl, const DevPlan *plans, int nplans, const unsigned int *plan_done,
+                      unsigned long long n_chunks, uint8_t *timed_out, void *stream);
 int launch_count(const MatchLaunch &L, void *stream);
 int launch_list(const MatchLaunch &L, void *stream);
 int launch_compose(const int32_t *qt, const int32_t *qtag, int64_t n_listed, const int32_t *map_off,
@@ -193,6 +197,7 @@ struct LocalArgs {
     int64_t grow_words;
     int64_t max_s;
     int want_k5;
+    unsigned long long *stats;   // nullable: algorithmic bytes
 };
 size_t local_smem_bytes();
 int local_blocks(int device);
@@ -214,6 +219,7 @@ struct DecompLaunch {
     int path_blocks;
     uint64_t *basis;          // 2 x DB_COUNT words
     Control *ctl;
+    unsigned long long *stats;   // nullable: algorithmic bytes of every pass
 };
 int decomp_path_blocks(int device);
 int launch_decomp(const DecompLaunch &L, void *stream);

@@ -32,6 +32,20 @@ constexpr int LC_WARPS = LC_THREADS / 32;
 constexpr int LC_SMEM_S = 704;                       // members whose rows fit shared memory
 constexpr int LC_PITCH_MAX = ((LC_SMEM_S + 31) / 32) | 1;
 
+// Algorithmic bytes of a row walk (instrumented runs): row offsets, the
+// search for its end, 4 B per element read.
+__device__ __forceinline__ uint64_t walk_bytes(int64_t from, int64_t to, int64_t row_len) {
+    return 16 + 4ull * uint64_t(row_len > 1 ? 65 - __clzll(uint64_t(row_len)) : 1) +
+           4ull * uint64_t(to - from);
+}
+
+__device__ __forceinline__ void lc_flush_stat(unsigned long long *stats, uint64_t v, int lane) {
+    if (!stats) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (lane == 0 && v) atomicAdd(stats, (unsigned long long)v);
+}
+
 __device__ __forceinline__ int32_t lc_lowdeg(const LocalArgs &A, int32_t v) {
     const int64_t r = A.g.n - 1 - v;
     return int32_t(__ldg(A.low_off + r + 1) - __ldg(A.low_off + r));
@@ -62,6 +76,7 @@ __global__ void __launch_bounds__(LC_THREADS) local_warp_kernel(LocalArgs A) {
     const uint64_t deadline = *(volatile unsigned long long *)&A.ctl->deadline;
     const int64_t warps = int64_t(gridDim.x) * LC_WARPS;
     u128 k4 = 0, k5 = 0;
+    uint64_t stat = 0;
     uint32_t tick = 0;
     for (int64_t v = int64_t(blockIdx.x) * LC_WARPS + (threadIdx.x >> 5); v < g.n; v += warps) {
         if (((++tick) & 255u) == 0) {
@@ -81,11 +96,13 @@ __global__ void __launch_bounds__(LC_THREADS) local_warp_kernel(LocalArgs A) {
         if (s < 3 || s > 32) continue;
         const int32_t Mi = lane < s ? __ldg(g.col + rowv + lowv + lane) : INT_MAX;
         const int32_t last = __shfl_sync(FULL, Mi, s - 1);
+        if (A.stats && lane == 0) stat += 16 + 4ull * uint64_t(s);
         uint32_t U = 0;                                   // members above lane adjacent to M[lane]
         for (int i = 0; i < s; i++) {
             const int32_t x = __shfl_sync(FULL, Mi, i);
             const int64_t from = __ldg(g.rowptr + x) + lc_lowdeg(A, x);
             const int64_t to = walk_end(g, x, from, last);
+            if (A.stats && lane == 0) stat += walk_bytes(from, to, __ldg(g.rowptr + x + 1) - from);
             uint32_t bits = 0;
             for (int64_t p0 = from; p0 < to; p0 += 32) {
                 const int64_t p = p0 + lane;
@@ -130,12 +147,14 @@ __global__ void __launch_bounds__(LC_THREADS) local_warp_kernel(LocalArgs A) {
         }
         if (A.k4e) {
             if (lane < s && tri_i) atomicAdd(A.k4e + rowv + lowv + lane, tri_i / 2);
+            if (A.stats && lane < s && tri_i) stat += 8;
             // edges (M[i], M[j]), i < j, at their slot in M[i]'s row
             for (int i = 0; i < s; i++) {
                 const int32_t x = __shfl_sync(FULL, Mi, i);
                 const uint32_t Ri = __shfl_sync(FULL, R, i);
                 const int64_t from = __ldg(g.rowptr + x) + lc_lowdeg(A, x);
                 const int64_t to = walk_end(g, x, from, last);
+                if (A.stats && lane == 0) stat += walk_bytes(from, to, __ldg(g.rowptr + x + 1) - from);
                 for (int64_t p0 = from; p0 < to; p0 += 32) {
                     const int64_t p = p0 + lane;
                     const int32_t y = p < to ? __ldg(g.col + p) : INT_MAX;
@@ -154,6 +173,7 @@ __global__ void __launch_bounds__(LC_THREADS) local_warp_kernel(LocalArgs A) {
                     if (p < to && lo < s && at == y) {
                         const uint32_t c = __popc(Ri & Rj);
                         if (c) atomicAdd(A.k4e + p, c);
+                        if (A.stats && c) stat += 8;
                     }
                 }
             }
@@ -161,6 +181,7 @@ __global__ void __launch_bounds__(LC_THREADS) local_warp_kernel(LocalArgs A) {
     }
     lc_flush(A.basis, DB_K4, k4, lane);
     if (A.want_k5) lc_flush(A.basis, DB_K5, k5, lane);
+    lc_flush_stat(A.stats, stat, lane);
 }
 
 // Vertices with more than 32 higher neighbours: one block each (taken from a
@@ -180,6 +201,7 @@ __global__ void __launch_bounds__(LC_THREADS) local_block_kernel(LocalArgs A) {
     uint32_t *Cbuf = tsum + LC_SMEM_S;
     uint32_t *Cw = Cbuf + 33 * warp;
     u128 k4 = 0, k5 = 0;
+    uint64_t stat = 0;
     for (;;) {
         if (tid == 0) {
             s_v = atomicAdd(&A.ctl->work3, 1ull);
@@ -214,11 +236,13 @@ __global__ void __launch_bounds__(LC_THREADS) local_block_kernel(LocalArgs A) {
         for (int64_t w = tid; w < int64_t(s) * pitch; w += blockDim.x) rows[w] = 0;
         __syncthreads();
         const int32_t last = M[s - 1];
+        if (A.stats && tid == 0) stat += 16 + 4ull * uint64_t(s);
         // build: warp per member row, symmetric bits
         for (int i = warp; i < s; i += LC_WARPS) {
             const int32_t x = M[i];
             const int64_t from = __ldg(g.rowptr + x) + lc_lowdeg(A, x);
             const int64_t to = walk_end(g, x, from, last);
+            if (A.stats && lane == 0) stat += walk_bytes(from, to, __ldg(g.rowptr + x + 1) - from);
             for (int64_t p = from + lane; p < to; p += 32) {
                 const int32_t y = __ldg(g.col + p);
                 int lo = i + 1, hi = s;
@@ -292,6 +316,7 @@ __global__ void __launch_bounds__(LC_THREADS) local_block_kernel(LocalArgs A) {
                 const uint32_t *Ri = rows + size_t(i) * pitch;
                 const int64_t from = __ldg(g.rowptr + x) + lc_lowdeg(A, x);
                 const int64_t to = walk_end(g, x, from, last);
+                if (A.stats && lane == 0) stat += walk_bytes(from, to, __ldg(g.rowptr + x + 1) - from);
                 for (int64_t p = from + lane; p < to; p += 32) {
                     const int32_t y = __ldg(g.col + p);
                     int lo = i + 1, hi = s;
@@ -308,18 +333,23 @@ __global__ void __launch_bounds__(LC_THREADS) local_block_kernel(LocalArgs A) {
                             atomicAdd(A.k4e + p, c);
                             atomicAdd(ts + i, c);
                             atomicAdd(ts + lo, c);
+                            if (A.stats) stat += 8;
                         }
                     }
                 }
             }
             __syncthreads();
             for (int i = tid; i < s; i += blockDim.x)
-                if (ts[i]) atomicAdd(A.k4e + rowv + lowv + i, ts[i] / 2);
+                if (ts[i]) {
+                    atomicAdd(A.k4e + rowv + lowv + i, ts[i] / 2);
+                    if (A.stats) stat += 8;
+                }
         }
         __syncthreads();
     }
     lc_flush(A.basis, DB_K4, k4, lane);
     if (A.want_k5) lc_flush(A.basis, DB_K5, k5, lane);
+    lc_flush_stat(A.stats, stat, lane);
 }
 
 size_t local_smem_bytes() {

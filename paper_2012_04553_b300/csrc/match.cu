@@ -447,6 +447,10 @@ struct KernelArgs {
     const uint32_t *piece_off;  // exclusive scan of pieces per deferred chunk
     unsigned long long *stats;
     ListOut list;               // listing instance only
+    // per plan: first-pass chunks finished, second-pass pieces finished and
+    // pieces made (3 x nplans), or nullptr: a plan whose counts fall short
+    // was cut by the deadline (per-pattern deadlines in one launch)
+    unsigned int *plan_done;
 };
 
 // One chunk (plan c % nplans, oriented edges (c / nplans) * 32 + 0..31),
@@ -656,6 +660,20 @@ match_kernel(KernelArgs A, int pass) {
                                                        tick, stat);
         }
         if (!alive) break;
+        if (A.plan_done && lane == 0) {
+            const unsigned long long chunk = pass == 0 ? w % A.nplans : 0;
+            if (pass == 0) {
+                atomicAdd(A.plan_done + chunk, 1u);
+            } else {
+                uint32_t lo = 0, hi = n_def;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (__ldg(A.piece_off + mid) <= w) lo = mid;
+                    else hi = mid;
+                }
+                atomicAdd(A.plan_done + A.nplans + A.defer[lo].chunk % A.nplans, 1u);
+            }
+        }
     }
     if (STATS) {
 #pragma unroll
@@ -666,7 +684,8 @@ match_kernel(KernelArgs A, int pass) {
 
 // Pieces per deferred chunk (all but the first) -> exclusive scan (one block).
 __global__ void piece_scan_kernel(const Deferred *defer, uint32_t cap, const DevPlan *plans,
-                                  int nplans, uint32_t *piece_off, Control *ctl) {
+                                  int nplans, uint32_t *piece_off, Control *ctl,
+                                  unsigned int *plan_done) {
     __shared__ uint32_t partial[1024];
     const uint32_t n = min(*(volatile uint32_t *)&ctl->n_deferred, cap);
     const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
@@ -692,8 +711,38 @@ __global__ void piece_scan_kernel(const Deferred *defer, uint32_t cap, const Dev
     for (uint32_t i = b; i < e; i++) {
         piece_off[i] = run;
         const uint32_t split = uint32_t(plans[defer[i].chunk % nplans].split);
-        run += (defer[i].total + split - 1) / split - 1;
+        const uint32_t pieces = (defer[i].total + split - 1) / split - 1;
+        run += pieces;
+        if (plan_done && pieces) atomicAdd(plan_done + 2 * nplans + defer[i].chunk % nplans, pieces);
     }
+}
+
+// Per-pattern deadlines in one launch: after the launch, every plan with a
+// first-pass chunk or a second-pass piece left unfinished flags its
+// pattern; then the control block is reset for what follows (as between
+// two patterns, with the call's deadline).
+__global__ void plan_flags_kernel(Control *ctl, const DevPlan *plans, int nplans,
+                                  const unsigned int *plan_done, unsigned long long n_chunks,
+                                  uint8_t *timed_out) {
+    if (ctl->status == 1) {
+        for (int p = 0; p < nplans; p++)
+            if (plan_done[p] < n_chunks || plan_done[nplans + p] < plan_done[2 * nplans + p])
+                timed_out[plans[p].counter] = 1;
+    }
+    ctl->status = 0;
+    ctl->work = 0;
+    ctl->work2 = 0;
+    ctl->work3 = 0;
+    ctl->n_deferred = 0;
+    ctl->n_pieces = 0;
+    ctl->deadline = ctl->call_deadline;
+}
+
+int launch_plan_flags(Control *ctl, const DevPlan *plans, int nplans, const unsigned int *plan_done,
+                      unsigned long long n_chunks, uint8_t *timed_out, void *stream) {
+    plan_flags_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(ctl, plans, nplans, plan_done, n_chunks,
+                                                         timed_out);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 // MNI morph (Theorem 3.2 with MNI tables): column c of a query is the OR of
@@ -1057,10 +1106,11 @@ static int launch_match(const MatchLaunch &L, void *stream) {
     A.piece_off = L.piece_off;
     A.stats = L.stats;
     A.list = ListOut{L.list_out, L.list_tag, L.list_cursor, L.list_cap, L.old_of};
+    A.plan_done = L.plan_done;
     cudaStream_t s = (cudaStream_t)stream;
     kern<<<unsigned(blocks0), WARPS * 32, smem, s>>>(A, 0);
     piece_scan_kernel<<<1, 1024, 0, s>>>(L.defer, L.defer_cap, L.plans, L.nplans, L.piece_off,
-                                         L.ctl);
+                                         L.ctl, L.plan_done);
     kern<<<unsigned(blocks), WARPS * 32, smem, s>>>(A, 1);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) {

@@ -559,9 +559,12 @@ def test_enumerate_through_theorem_3_1():
           algebra.Pattern.from_mask(5, algebra.connected_classes(5)[7])]
     cq = [pm.make_pattern(p.k, p.mask, int(p.vertex_induced)) for p in qs]
     for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE):
-        plan = pm.Plan(g, cq, mode=mode)
-        listed = plan.enumerate(cap=16)                    # grows the buffer once
-        for i, p in enumerate(qs):
+        # a vertex-induced query can be listed only as itself (no morphing)
+        use = [i for i, p in enumerate(qs) if mode == pm.MORPH_NONE or not p.vertex_induced]
+        plan = pm.Plan(g, [cq[i] for i in use], mode=mode)
+        listed = [(use[q], t) for q, t in plan.enumerate(cap=16)]     # grows the buffer once
+        for i in use:
+            p = qs[i]
             got = [t for q, t in listed if q == i]
             occ = []
             for t in got:
@@ -577,3 +580,77 @@ def test_enumerate_through_theorem_3_1():
     with pytest.raises(pm.PMError) as e:
         vi.enumerate()
     assert e.value.status == pm.PM_EUNSUPPORTED
+
+
+def test_batch_128_patterns_single_launch_with_deadlines():
+    """128 random connected 3-6 vertex patterns (half vertex-, half
+    edge-induced) on R-MAT scale 10 in one persistent launch, replayed from a
+    captured CUDA graph with per-pattern deadlines: every status is OK, the
+    3- and 4-vertex counts equal the oracle's, and every count equals the
+    same plan run pattern by pattern."""
+    from pm_inputs import random_patterns
+    n = 1024
+    s, d = rmat_edges(10, 4, seed=125)
+    og = oracle.prepare_graph(n, s, d)
+    g = load(n, s, d)
+    pats = random_patterns(128, seed=126)
+    qs = [pm.make_pattern(k, m, ind) for k, m, ind in pats]
+    ref = pm.Plan(g, qs, mode=pm.MORPH_NAIVE)
+    want = ref.count()
+    small = [i for i, (k, _, _) in enumerate(pats) if k <= 4]
+    for i in small:
+        k, m, ind = pats[i]
+        assert want[i] == oracle.count(og, algebra.Pattern.from_mask(k, m, None, bool(ind))), i
+    plan = pm.Plan(g, qs, mode=pm.MORPH_NAIVE)
+    plan.set_launch(pm.LAUNCH_SINGLE)
+    plan.capture_each(timeout_per_pattern_s=120.0, timeout_total_s=600.0)
+    for _ in range(2):
+        counts, status = plan.count_each()
+        assert status == [pm.PM_OK] * len(qs)
+        assert counts == want
+
+
+def test_single_launch_per_pattern_deadlines():
+    """In one persistent launch every pattern's deadline runs from the launch
+    start: the vertex-induced 5-star (seconds of work here) is cut and
+    reported, the triangle and wedge complete exactly, captured or not."""
+    s, d = rmat_edges(14, 16, seed=119)
+    g = load(1 << 14, s, d)
+    light = [pm.make_pattern(3, 0b111), pm.make_pattern(3, 0b011)]
+    heavy = [pm.make_pattern(5, 0b1111, pm.VERTEX_INDUCED)]
+    want = pm.Plan(g, light, mode=pm.MORPH_NONE).count()
+    plan = pm.Plan(g, light + heavy, mode=pm.MORPH_NONE)
+    plan.select(pm.PLANS_FREE)
+    plan.set_launch(pm.LAUNCH_SINGLE)
+    counts, status = plan.count_each(timeout_per_pattern_s=0.5, timeout_total_s=30.0)
+    assert status == [pm.PM_OK, pm.PM_OK, pm.PM_ETIMEOUT] and counts == want + [0]
+    plan.capture_each(timeout_per_pattern_s=0.5, timeout_total_s=30.0)
+    counts, status = plan.count_each()
+    assert status == [pm.PM_OK, pm.PM_OK, pm.PM_ETIMEOUT] and counts == want + [0]
+
+
+def test_cost_mode_never_slower_than_naive_or_direct():
+    """Cost-based morph selection (Section 4.1 optimizer, Table 3) on a fixed
+    graph: the set it picks for the 4-motif queries counts no slower than the
+    naive morphed set or the direct set (median of 3 timed counts after
+    warm-up; 50% tolerance plus 5 ms for timing noise), with equal counts."""
+    import time as _t
+    import torch
+    s, d = rmat_edges(14, 16, seed=127)
+    g = load(1 << 14, s, d)
+    qs = motif_queries(4)
+    times, counts = {}, {}
+    for mode in (pm.MORPH_NONE, pm.MORPH_NAIVE, pm.MORPH_COST):
+        plan = pm.Plan(g, qs, mode=mode)
+        counts[mode] = plan.count()                  # tuning and warm-up
+        ts = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = _t.perf_counter()
+            assert plan.count() == counts[mode]
+            torch.cuda.synchronize()
+            ts.append(_t.perf_counter() - t0)
+        times[mode] = sorted(ts)[1]
+    assert counts[pm.MORPH_COST] == counts[pm.MORPH_NAIVE] == counts[pm.MORPH_NONE]
+    best = min(times[pm.MORPH_NONE], times[pm.MORPH_NAIVE])
+    assert times[pm.MORPH_COST] <= 1.5 * best + 0.005, times
