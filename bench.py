@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--scale", type=int, default=18, help="R-MAT scale of the pattern workload")
     ap.add_argument("--seed", type=int, default=7, help="R-MAT seed of the pattern workload")
     ap.add_argument("--family", choices=["auto", "rooted", "free"], default="auto")
+    ap.add_argument("--labels", type=int, default=0, help="pattern workload: Zipf(1.2) vertex labels")
+    ap.add_argument("--pattern-labels", default="", help="pattern workload: comma-separated vertex labels")
+    ap.add_argument("--op", choices=["count", "support"], default="count")
     return ap.parse_args()
 
 
@@ -461,23 +464,37 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
-def mc5_measurements(pm, g, n, stream=None, roots_n=1024, deadline=60.0, per_pattern_s=30.0,
-                     total_s=240.0, direct_s=30.0):
+def simple_degrees(n, src, dst):
+    """Degree of every vertex of the simple graph of an edge list (self-loops
+    and duplicate edges dropped, either direction), by caller id."""
+    a = np.minimum(src, dst).astype(np.int64)
+    b = np.maximum(src, dst).astype(np.int64)
+    keep = a != b
+    key = np.unique(a[keep] * n + b[keep])
+    return np.bincount(key // n, minlength=n) + np.bincount(key % n, minlength=n)
+
+
+def mc5_measurements(pm, g, n, degrees, stream=None, roots_n=1024, deadline=60.0, per_pattern_s=30.0,
+                     total_s=240.0, direct_s=30.0, max_root_degree=48):
     """5-motif counting (the 21 connected vertex-induced unlabeled patterns)
     on the loaded graph, morphed vs direct:
     * sampled roots: occurrences whose highest-ranked vertex is one of a
-      systematic sample of roots (every (n / R)-th vertex in degree order,
-      offset half a stride), rooted plans, each count under `deadline`;
-      morphed and direct counts must agree exactly;
+      systematic sample of R roots (evenly spaced, in degree order, over the
+      vertices of degree <= max_root_degree), rooted plans, each count under
+      `deadline`; morphed and direct counts must agree exactly;
     * whole graph, morphed: the 21 edge-induced patterns (Theorem 3.1 /
       Corollary 3.1 turn them into the 21 vertex-induced counts), each under
       its own deadline (pm_count_each), with its status and device time;
     * whole graph, direct: the 21 vertex-induced patterns under `direct_s`."""
     import torch
+    # sampled roots: every stride-th vertex, in degree order, among those of
+    # degree <= max_root_degree (rooted plans enumerate about degree^4 maps
+    # per root for the vertex-induced 5-star)
     by_rank = np.empty(n, dtype=np.int64)
     by_rank[g.vertex_order()] = np.arange(n)
-    stride = n // roots_n
-    roots = np.sort(by_rank[(np.arange(roots_n) * stride + stride // 2).astype(np.int64)]).astype(np.int32)
+    eligible = by_rank[degrees[by_rank] <= max_root_degree]  # ascending degree order
+    stride = max(1, len(eligible) // roots_n)
+    roots = np.sort(eligible[stride // 2::stride][:roots_n]).astype(np.int32)
     masks = connected_classes(5)
     vq = [pm.make_pattern(5, m, pm.VERTEX_INDUCED) for m in masks]
     sample = {}
@@ -494,6 +511,7 @@ def mc5_measurements(pm, g, n, stream=None, roots_n=1024, deadline=60.0, per_pat
     m, d = sample["morphed"], sample["direct"]
     sample["counts_equal"] = (m["counts"] == d["counts"]) if "counts" in m and "counts" in d else None
     sample["roots"] = int(len(roots))
+    sample["max_root_degree"] = int(degrees[roots].max()) if len(roots) else 0
     # whole graph, morphed: edge-induced patterns with a deadline each
     eplan = pm.Plan(g, [pm.make_pattern(5, mm, pm.EDGE_INDUCED) for mm in masks], mode=pm.MORPH_NONE)
     eplan.autotune(stream=stream)
@@ -533,8 +551,9 @@ def run_mc5(args):
     n = 1 << SCALE
     src, dst = cached_rmat(SCALE, EDGE_FACTOR, SEED)
     g = pm.Graph(n, src, dst)
-    res = mc5_measurements(pm, g, n, roots_n=args.mc5_roots, deadline=args.mc5_deadline,
-                           per_pattern_s=args.mc5_pattern_deadline, total_s=args.mc5_total_deadline)
+    res = mc5_measurements(pm, g, n, simple_degrees(n, src, dst), roots_n=args.mc5_roots,
+                           deadline=args.mc5_deadline, per_pattern_s=args.mc5_pattern_deadline,
+                           total_s=args.mc5_total_deadline)
     line = {"metric": "5-motif counting, morphed vs direct, R-MAT scale 20",
             "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "int64", "data": "synthetic",
             "value": res["whole_graph_morphed"]["wall_s"], "mc5": res,
@@ -545,15 +564,22 @@ def run_mc5(args):
 
 def run_pattern(args):
     """One pattern on R-MAT (scale, ef 16, seed), matched as given: device
-    time of the matching kernels (profiling target)."""
+    time of the matching kernels (profiling target).  With --labels L the
+    graph carries L Zipf(1.2) labels (seed + 1) and the pattern's vertices
+    take labels from --pattern-labels; --op support collects MNI domains."""
     import torch
     import paper_2012_04553_b300 as pm
+    from pm_inputs import zipf_labels
     k, mask, ind = (int(x) for x in args.pattern.split(":"))
     src, dst = cached_rmat(args.scale, 16, args.seed)
-    g = pm.Graph(1 << args.scale, src, dst)
-    plan = pm.Plan(g, [pm.make_pattern(k, mask, ind)], mode=pm.MORPH_NONE)
+    n = 1 << args.scale
+    labels = zipf_labels(n, args.labels, s=1.2, seed=args.seed + 1) if args.labels else None
+    plab = [int(x) for x in args.pattern_labels.split(",")] if args.pattern_labels else None
+    g = pm.Graph(n, src, dst, labels)
+    op = pm.OP_SUPPORT if args.op == "support" else pm.OP_COUNT
+    plan = pm.Plan(g, [pm.make_pattern(k, mask, ind, plab)], op=op, mode=pm.MORPH_NONE)
     plan.select({"auto": pm.PLANS_AUTO, "rooted": pm.PLANS_ROOTED, "free": pm.PLANS_FREE}[args.family])
-    counts = plan.count()
+    counts = plan.support(threshold=0)[0] if op == pm.OP_SUPPORT else plan.count()
     print(json.dumps({"metric": "single-pattern count, kernel time", "value": plan.last_kernel_ms(),
                       "unit": "ms", "count": str(counts[0]), "pattern": args.pattern,
                       "scale": args.scale, "seed": args.seed, "family": args.family}), flush=True)
@@ -681,8 +707,8 @@ def main():
         "graph": {"n": info["n"], "m": info["m"], "max_degree": info["max_degree"]},
     }
     if rank == 0 and not args.no_mc5:
-        line["mc5"] = mc5_measurements(pm, g, n, stream=stream, roots_n=args.mc5_roots,
-                                       deadline=args.mc5_deadline,
+        line["mc5"] = mc5_measurements(pm, g, n, simple_degrees(n, src, dst), stream=stream,
+                                       roots_n=args.mc5_roots, deadline=args.mc5_deadline,
                                        per_pattern_s=args.mc5_pattern_deadline,
                                        total_s=args.mc5_total_deadline)
     if rank == 0 and world == 1 and not args.no_baseline:

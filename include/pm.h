@@ -201,7 +201,8 @@ pm_status pm_plan_select(pm_query_plan *p, int32_t family);
 pm_status pm_plan_set_launch(pm_query_plan *p, int32_t mode);
 /* Run the autotuner now (it otherwise runs inside the first pm_count or
  * pm_support): for each matched pattern not yet decided on this graph, time
- * its rooted and free plans on the same sample of about 4096 task chunks and
+ * its rooted and free plans on the same sample of about 4096 task chunks
+ * (0.5 s deadline; an 8x, then 64x sparser sample when both run past it) and
  * keep the faster, then time that family's task granularity -- the
  * second-level candidates a task chunk keeps before the rest is deferred to
  * other warps, which sets how many warps share a hub root -- at a quarter
@@ -302,7 +303,8 @@ pm_status pm_plan_last_kernel_ms(const pm_query_plan *p, float *ms);
  * launch sequence in the plan's last completed pm_count (or its captured
  * replay), in per-pattern launch mode: ms[j] for matched pattern j
  * (n_matched entries), 0 for patterns that did not run on their own
- * (single-launch mode, pm_count_roots, pm_count_instrumented). */
+ * (single-launch mode, pm_count_roots, pm_count_instrumented).  Also
+ * filled by pm_count_each. */
 pm_status pm_plan_pattern_ms(const pm_query_plan *p, float *ms);
 /* Number of the library's kernels launched by the plan's last pm_count
  * (or pm_count_each, or captured into its CUDA graph), counting the arming

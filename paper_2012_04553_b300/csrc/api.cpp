@@ -796,6 +796,9 @@ pm_status autotune(pm_query_plan *p, cudaStream_t s) {
         const DevTasks tasks = all_tasks(g);
         float best = std::numeric_limits<float>::infinity();
         int best_f = PM_PLANS_ROOTED;
+        // the sample: about 4096 chunks, or 8x (64x) sparser when every
+        // family ran past its deadline on the denser one
+        for (int sparse = 1; sparse <= 64 && !std::isfinite(best); sparse *= 8)
         for (int f = PM_PLANS_ROOTED; f <= PM_PLANS_FREE; f++) {
             PlanTable t;
             t.plans = family_plans(p, j, f);
@@ -813,7 +816,7 @@ pm_status autotune(pm_query_plan *p, cudaStream_t s) {
             pm_status st = upload_table(t, g->device);
             if (st != PM_OK) return st;
             const int64_t ech = echunks_for(t.plans, tasks);
-            const int stride = int(std::max<int64_t>(1, ech / 4096));
+            const int stride = int(std::max<int64_t>(1, ech / 4096) * sparse);
             cudaError_t e = cudaMemsetAsync(p->d_counters, 0, p->bytes_counters, s);
             if (!e && launch_arm(p->d_ctl, uint64_t(5e8), s)) e = cudaErrorLaunchFailure;
             if (!e) e = cudaEventRecord(p->ev0, s);
@@ -830,6 +833,8 @@ pm_status autotune(pm_query_plan *p, cudaStream_t s) {
             if (ctl.status == 1) {
                 ms = std::numeric_limits<float>::infinity();
                 rezero_wedge(p, s);
+            } else {
+                ms *= float(sparse);    // comparable with the denser sample
             }
             if (ms < best) { best = ms; best_f = f; }
         }
@@ -1147,7 +1152,7 @@ pm_status run_count_each(pm_query_plan *p, void *stream, double timeout_s, doubl
     }
     cudaEventRecord(p->ev0, s);
     st = launch_table(p, p->active, all_tasks(g), 1, false, nullptr, s, budget,
-                      p->d_timed_out, false, true);
+                      p->d_timed_out, true, true);
     p->launch_mode = saved_mode;
     if (st != PM_OK) return st;
     cudaEventRecord(p->ev1, s);

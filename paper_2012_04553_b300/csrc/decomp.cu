@@ -152,13 +152,21 @@ __global__ void __launch_bounds__(DC_WARPS * 32) tri_kernel(TriArgs A) {
             }
             lb = __shfl_sync(FULL, lb, 0);
             pba = __shfl_sync(FULL, pba, 0);
-            if (A.stats && lane == 0) stat += 32 + 4ull * uint64_t(la + lb) + (MODE == 1 ? 4 : 8);
+            if (A.stats && lane == 0) stat += 32 + 4ull * uint64_t(la <= lb ? la : lb) + (MODE == 1 ? 4 : 8);
             const int32_t n = la <= lb ? la : lb;
             if (n == 0) continue;
             const bool from_a = la <= lb;
             const int64_t src = from_a ? rowa : rowb;
             const int64_t oth = from_a ? rowb : rowa;
             const int32_t olen = from_a ? lb : la;
+            // membership in the other row: one bit read when it has a hub
+            // bitmap (the binary search then runs only for the triangles,
+            // whose slot it finds), else the binary search itself
+            const uint32_t *obits = nullptr;
+            if (g.hub) {
+                const int32_t h = __ldg(g.hub + (from_a ? rb : ra));
+                if (h >= 0) obits = g.bits + int64_t(h) * g.words;
+            }
             const int64_t up_ab = int64_t(da - lowra) + int64_t(db - pba - 1);
             int32_t t_ab = 0;
             if (MODE == 1) t_ab = __ldg(A.t + rowa + la);
@@ -167,7 +175,9 @@ __global__ void __launch_bounds__(DC_WARPS * 32) tri_kernel(TriArgs A) {
                 const int32_t j = j0 + lane;
                 if (j < n) {
                     const int32_t x = __ldg(g.col + src + j);
-                    const int32_t p = lower_bound_dev(g.col + oth, olen, x);
+                    const bool maybe = !obits || ((__ldg(obits + (x >> 5)) >> (x & 31)) & 1u);
+                    const int32_t p = maybe ? lower_bound_dev(g.col + oth, olen, x) : olen;
+                    if (A.stats) stat += obits ? 4 : probe_bytes(olen);   // membership test
                     if (p < olen && __ldg(g.col + oth + p) == x) {
                         const int64_t s_ac = from_a ? src + j : oth + p;
                         const int64_t s_bc = from_a ? oth + p : src + j;
@@ -181,9 +191,10 @@ __global__ void __launch_bounds__(DC_WARPS * 32) tri_kernel(TriArgs A) {
                                 const int32_t pxa = lower_bound_dev(g.col + rowx, dx, ra);
                                 acc0 += u128(uint64_t(up_ab + int64_t(dx - pxa - 1)));
                             }
-                            if (A.stats) stat += 16 + (A.with_c5 ? 16 + probe_bytes(dx) : 0);
+                            if (A.stats)
+                                stat += 16 + (obits ? probe_bytes(olen) : 0) + (A.with_c5 ? 16 + probe_bytes(dx) : 0);
                         } else {
-                            if (A.stats) stat += 24;
+                            if (A.stats) stat += 24 + (obits ? probe_bytes(olen) : 0);
                             const int64_t tac = __ldg(A.t + s_ac), tbc = __ldg(A.t + s_bc);
                             const int64_t tab = t_ab;
                             acc0 += u128(uint64_t((tab - 1) * dx + (tbc - 1) * da + (tac - 1) * db));
