@@ -14,6 +14,11 @@
  *
  * Conventions for every entry point:
  *  - Status codes are returned; the library never aborts the process.
+ *  - Fault injection on the host, for testing error paths: the environment
+ *    variable PM_FAULT, read at each call, makes every device allocation
+ *    fail ("alloc": PM_ENOMEM from the call that needed it), every
+ *    pm_load_graph fail ("load": PM_EINVAL) or every pm_plan fail ("plan":
+ *    PM_EUNSUPPORTED), each with a pm_last_error() text saying so.
  *  - The plan handle type is pm_query_plan (the C name pm_plan is the
  *    function that makes one).
  *  - Host input arrays are read during the call only and never retained;

@@ -31,7 +31,16 @@ void *g_alloc_ctx = nullptr;
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
+// Host-side fault injection (environment variable PM_FAULT, read at each
+// call): "alloc" fails every device allocation, "load" every graph load,
+// "plan" every plan, so error paths are exercised without a GPU fault.
+bool fault_injected(const char *what) {
+    const char *f = std::getenv("PM_FAULT");
+    return f && std::strcmp(f, what) == 0;
+}
+
 void *dev_alloc(size_t bytes, int device) {
+    if (fault_injected("alloc")) return nullptr;
     if (bytes == 0) bytes = 256;
     pm_alloc_fn a;
     void *ctx;
@@ -1233,6 +1242,10 @@ pm_status pm_set_allocator(pm_alloc_fn alloc, pm_free_fn release, void *ctx) {
 
 pm_status pm_load_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_t *dst,
                         const uint8_t *labels, int device, void *stream, pm_graph **out) {
+    if (fault_injected("load")) {
+        set_error("pm_load_graph: fault injected (PM_FAULT=load)");
+        return PM_EINVAL;
+    }
     return build_graph(n, m_raw, src, dst, labels, device, stream, out);
 }
 
@@ -1271,6 +1284,10 @@ void pm_free_graph(pm_graph *g) {
 
 pm_status pm_plan(const pm_graph *g, const pm_pattern *queries, int32_t nq, pm_op op,
                   pm_morph_mode mode, pm_query_plan **out) {
+    if (fault_injected("plan")) {
+        set_error("pm_plan: fault injected (PM_FAULT=plan)");
+        return PM_EUNSUPPORTED;
+    }
     if (!queries || nq < 1 || !out) {
         set_error("pm_plan: null argument or empty query set");
         return PM_EINVAL;

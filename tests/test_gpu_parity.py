@@ -654,3 +654,21 @@ def test_cost_mode_never_slower_than_naive_or_direct():
     assert counts[pm.MORPH_COST] == counts[pm.MORPH_NAIVE] == counts[pm.MORPH_NONE]
     best = min(times[pm.MORPH_NONE], times[pm.MORPH_NAIVE])
     assert times[pm.MORPH_COST] <= 1.5 * best + 0.005, times
+
+
+def test_injected_allocation_failure_is_a_status(monkeypatch):
+    """PM_FAULT=alloc: every device allocation fails on the host side; loading
+    and counting report PM_ENOMEM and the library stays usable afterwards."""
+    s, d = rmat_edges(7, 6, seed=128)
+    g = load(128, s, d)
+    monkeypatch.setenv("PM_FAULT", "alloc")
+    with pytest.raises(pm.PMError) as e:
+        pm.Graph(128, s, d)
+    assert e.value.status == pm.PM_ENOMEM
+    plan = pm.Plan(g, motif_queries(3), mode=pm.MORPH_NAIVE)
+    with pytest.raises(pm.PMError) as e:
+        plan.count()
+    assert e.value.status == pm.PM_ENOMEM
+    monkeypatch.delenv("PM_FAULT")
+    og = oracle.prepare_graph(128, s, d)
+    assert pm.Plan(g, motif_queries(3), mode=pm.MORPH_NAIVE).count() == oracle.motif_counts_direct(og, 3)

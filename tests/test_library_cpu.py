@@ -218,3 +218,18 @@ def test_canonical_labelling_is_a_class_function():
         # a clique's vertex- and edge-induced forms are one pattern
         keys.add(algebra.canonical(op.with_induced(False) if op.is_clique else op))
     assert pm.Plan(None, lib_q, mode=pm.MORPH_NONE).n_matched == len(keys)
+
+
+def test_host_fault_injection(monkeypatch):
+    """PM_FAULT makes graph loading and planning fail with their statuses and
+    an explanatory error text, before any device work."""
+    monkeypatch.setenv("PM_FAULT", "plan")
+    with pytest.raises(pm.PMError) as e:
+        pm.Plan(None, [pm.make_pattern(3, 0b111)])
+    assert e.value.status == pm.PM_EUNSUPPORTED and "fault injected" in str(e.value)
+    monkeypatch.setenv("PM_FAULT", "load")
+    with pytest.raises(pm.PMError) as e:
+        pm.Graph(4, np.array([0, 1], np.int32), np.array([1, 2], np.int32))
+    assert e.value.status == pm.PM_EINVAL and "fault injected" in str(e.value)
+    monkeypatch.delenv("PM_FAULT")
+    assert pm.Plan(None, [pm.make_pattern(3, 0b111)]).n_matched == 1
