@@ -162,12 +162,49 @@ struct pm_query_plan {
     size_t bytes_local = 0;
     int local_blocks = 0;
     bool local_ready = false;
+    // neighbourhood-graph pass (wheel.cu): list offsets, common-neighbour
+    // lists, scan scratch, hub rank index, mirror positions, counters
+    struct {
+        int64_t *toff = nullptr;
+        int32_t *T = nullptr;
+        int64_t *bsum = nullptr;
+        int32_t *rank = nullptr;
+        int32_t *mpos = nullptr;
+        uint32_t *gcnt = nullptr;
+        uint32_t *kW = nullptr;
+        unsigned long long *kE = nullptr;
+        int32_t *ktouched = nullptr;
+        size_t b_toff = 0, b_T = 0, b_bsum = 0, b_rank = 0, b_mpos = 0, b_gcnt = 0, b_kW = 0, b_kE = 0;
+        int64_t gcnt_words = 0;
+        int w4_blocks = 0, k23_blocks = 0;
+    } wh;
     // CUDA graph of a whole pm_count (pm_plan_capture): replayed by pm_count
     cudaGraphExec_t graph_exec = nullptr;
     uint64_t *h_pinned = nullptr;            // counters (2 per matched) then the Control block
 };
 
 namespace {
+
+// A pass found its inputs inconsistent (common-neighbour lists whose
+// lengths differ from the per-edge triangle counts): an internal error.
+pm_status list_fault(const char *who) {
+    set_error(std::string(who) + ": common-neighbour lists disagree with the per-edge triangle counts");
+    return PM_ECUDA;
+}
+
+void free_wheel(pm_query_plan *p, int dev) {
+    auto &w = p->wh;
+    dev_free(w.toff, w.b_toff, dev);
+    dev_free(w.T, w.b_T, dev);
+    dev_free(w.bsum, w.b_bsum, dev);
+    dev_free(w.rank, w.b_rank, dev);
+    dev_free(w.mpos, w.b_mpos, dev);
+    dev_free(w.gcnt, w.b_gcnt, dev);
+    dev_free(w.kW, w.b_kW, dev);
+    dev_free(w.kE, w.b_kE, dev);
+    dev_free(w.ktouched, w.b_kW, dev);
+    p->wh = {};
+}
 
 struct DeviceGuard {
     int prev = 0;
@@ -284,6 +321,7 @@ void free_plan_device(pm_query_plan *p) {
     dev_free(p->d_basis, sizeof(uint64_t) * 2 * DB_COUNT, dev);
     dev_free(p->d_k4e, p->bytes_k4e, dev);
     dev_free(p->d_local, p->bytes_local, dev);
+    free_wheel(p, dev);
     p->d_k4e = nullptr;
     p->bytes_k4e = 0;
     p->d_local = nullptr;
@@ -547,6 +585,87 @@ pm_status ensure_decomp(pm_query_plan *p, cudaStream_t s) {
             return PM_ENOMEM;
         }
     }
+    if ((passes & (DP_W4 | DP_K23E)) && !p->wh.T) {
+        auto &w = p->wh;
+        const int64_t nnz = 2 * g->m;
+        auto fail = [&](const char *what) {
+            free_wheel(p, g->device);
+            set_error(std::string("device allocation failed (") + what + ")");
+            return PM_ENOMEM;
+        };
+        w.b_toff = sizeof(int64_t) * size_t(nnz + 1);
+        w.toff = (int64_t *)dev_alloc(w.b_toff, g->device);
+        w.b_bsum = sizeof(int64_t) * size_t(std::max<int64_t>(tscan_blocks(nnz), 1));
+        w.bsum = (int64_t *)dev_alloc(w.b_bsum, g->device);
+        if (!w.toff || !w.bsum) return fail("common-neighbour list offsets");
+        if (g->n_hubs > 0) {
+            w.b_rank = sizeof(int32_t) * size_t(g->n_hubs) * size_t(g->hub_words);
+            w.rank = (int32_t *)dev_alloc(w.b_rank, g->device);
+            if (!w.rank) return fail("hub rank index");
+        }
+        // the lists' total length: one triangle pass (own control block, no
+        // deadline) and the offset scan
+        int64_t total = 0;
+        if (nnz > 0) {
+            Control *ctl = (Control *)dev_alloc(sizeof(Control), g->device);
+            if (!ctl) return fail("control block");
+            cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(Control), s);
+            DecompLaunch D{};
+            D.g = g->dev();
+            D.tasks = all_tasks(g);
+            D.t = p->d_tslot;
+            D.basis = p->d_basis;
+            D.ctl = ctl;
+            WheelArgs A{};
+            A.g = D.g;
+            A.t = p->d_tslot;
+            A.toff = w.toff;
+            A.bsum = w.bsum;
+            int bad = e != cudaSuccess;
+            if (!bad) bad = launch_decomp_triangles(D, s) || launch_list_offsets(A, s);
+            if (!bad) e = cudaMemcpyAsync(&total, w.toff + nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+            if (!bad && !e) e = cudaStreamSynchronize(s);
+            dev_free(ctl, sizeof(Control), g->device);
+            if (bad) return PM_ECUDA;
+            if (e) return cuda_fail("common-neighbour list sizes", e);
+        }
+        w.b_T = sizeof(int32_t) * size_t(std::max<int64_t>(total, 1));
+        w.T = (int32_t *)dev_alloc(w.b_T, g->device);
+        if (!w.T) return fail("common-neighbour lists");
+    }
+    if ((passes & DP_K23E) && !p->wh.kW) {
+        auto &w = p->wh;
+        w.k23_blocks = k23_blocks(g->device);
+        w.b_mpos = sizeof(int32_t) * size_t(std::max<int64_t>(2 * g->m, 1));
+        w.b_kW = sizeof(uint32_t) * size_t(g->n) * size_t(w.k23_blocks);
+        w.b_kE = sizeof(unsigned long long) * size_t(g->n) * size_t(w.k23_blocks);
+        w.mpos = (int32_t *)dev_alloc(w.b_mpos, g->device);
+        w.kW = (uint32_t *)dev_alloc(w.b_kW, g->device);
+        w.kE = (unsigned long long *)dev_alloc(w.b_kE, g->device);
+        w.ktouched = (int32_t *)dev_alloc(w.b_kW, g->device);
+        if (!w.mpos || !w.kW || !w.kE || !w.ktouched) {
+            free_wheel(p, g->device);
+            set_error("device allocation failed (K2,3 root counters)");
+            return PM_ENOMEM;
+        }
+        cudaError_t e = cudaMemsetAsync(w.kW, 0, w.b_kW, s);
+        if (!e) e = cudaMemsetAsync(w.kE, 0, w.b_kE, s);
+        if (e) return cuda_fail("K2,3 root counters", e);
+    }
+    if ((passes & DP_W4) && !p->wh.w4_blocks) {
+        auto &w = p->wh;
+        w.w4_blocks = w4_blocks(g->device);
+        w.gcnt_words = w4_global_words(g->max_degree);
+        if (w.gcnt_words) {
+            w.b_gcnt = sizeof(uint32_t) * size_t(w.gcnt_words) * size_t(w.w4_blocks);
+            w.gcnt = (uint32_t *)dev_alloc(w.b_gcnt, g->device);
+            if (!w.gcnt) {
+                free_wheel(p, g->device);
+                set_error("device allocation failed (4-wheel counters)");
+                return PM_ENOMEM;
+            }
+        }
+    }
     if ((passes & DP_LOCAL) && !p->local_ready) {
         p->local_blocks = local_blocks(g->device);
         const int64_t gw = local_grow_words(g->max_updeg);
@@ -724,6 +843,20 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
             D.local.gmem = reinterpret_cast<int32_t *>(p->d_local + size_t(p->local_blocks) * size_t(D.local.grow_words));
             D.local.gts = reinterpret_cast<uint32_t *>(D.local.gmem) + size_t(p->local_blocks) * size_t(D.local.max_s);
         }
+        D.wheel.toff = p->wh.toff;
+        D.wheel.T = p->wh.T;
+        D.wheel.bsum = p->wh.bsum;
+        D.wheel.hub_rank = p->wh.rank;
+        D.wheel.n_hubs = p->wh.rank ? g->n_hubs : 0;
+        D.wheel.mpos = p->wh.mpos;
+        D.wheel.gcnt = p->wh.gcnt;
+        D.wheel.gcnt_words = p->wh.gcnt_words;
+        D.wheel.w4_blocks = p->wh.w4_blocks;
+        D.wheel.kW = p->wh.kW;
+        D.wheel.kE = p->wh.kE;
+        D.wheel.ktouched = p->wh.ktouched;
+        D.wheel.k23_blocks = p->wh.k23_blocks;
+        D.wheel.g = L.g;
         D.W = p->d_dW;
         D.touched = p->d_dtouched;
         D.path_blocks = p->dpath_blocks;
@@ -731,7 +864,8 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
         D.ctl = p->d_ctl;
         D.stats = stats ? stats + 1 + first : nullptr;
         p->launches += 3 + int((D.passes & DP_TRI2) != 0) + int((D.passes & DP_PATHS) != 0) +
-                       2 * int((D.passes & DP_LOCAL) != 0) + 1;
+                       2 * int((D.passes & DP_LOCAL) != 0) + 1 +
+                       ((D.passes & (DP_W4 | DP_K23E)) ? wheel_launches(D.wheel, D.passes) : 0);
         if (launch_decomp(D, s)) return PM_ECUDA;
         if (launch_decomp_combine(p->d_basis, p->d_targets, nt, p->d_counters, s)) return PM_ECUDA;
         mark(first, 1);
@@ -748,6 +882,8 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
 void rezero_wedge(pm_query_plan *p, cudaStream_t s) {
     if (p->d_wedge) cudaMemsetAsync(p->d_wedge, 0, p->bytes_wedge, s);
     if (p->d_dW) cudaMemsetAsync(p->d_dW, 0, p->bytes_dW, s);
+    if (p->wh.kW) cudaMemsetAsync(p->wh.kW, 0, p->wh.b_kW, s);
+    if (p->wh.kE) cudaMemsetAsync(p->wh.kE, 0, p->wh.b_kE, s);
 }
 
 // Task granularity: the second-level candidates a chunk keeps before the
@@ -1095,6 +1231,7 @@ pm_status run_count(pm_query_plan *p, void *stream, double timeout_s, const int3
         set_error("pm_count: deadline expired");
         return PM_ETIMEOUT;
     }
+    if (ctl.fault) return list_fault("pm_count");
     if (matched) std::memcpy(matched, raw.data(), sizeof(uint64_t) * 2 * nm);
     return pm_morph(p, raw.data(), counts);
 }
@@ -1129,6 +1266,9 @@ pm_status run_count_each(pm_query_plan *p, void *stream, double timeout_s, doubl
         if (e) return cuda_fail("pm_count_each (graph replay)", e);
         std::vector<uint8_t> flags(nm);
         std::memcpy(flags.data(), reinterpret_cast<uint8_t *>(p->h_pinned + 2 * nm) + sizeof(Control), nm);
+        Control ctl;
+        std::memcpy(&ctl, p->h_pinned + 2 * nm, sizeof(Control));
+        if (ctl.fault) return list_fault("pm_count_each (graph replay)");
         bool any = false;
         for (size_t j = 0; j < nm; j++) any |= flags[j] != 0;
         if (any) {
@@ -1171,8 +1311,11 @@ pm_status run_count_each(pm_query_plan *p, void *stream, double timeout_s, doubl
     e = cudaMemcpyAsync(raw.data(), p->d_counters, sizeof(uint64_t) * 2 * nm,
                         cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaMemcpyAsync(flags.data(), p->d_timed_out, nm, cudaMemcpyDeviceToHost, s);
+    Control ctl;
+    if (!e) e = cudaMemcpyAsync(&ctl, p->d_ctl, sizeof(Control), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return cuda_fail("pm_count_each: kernel or readback", e);
+    if (ctl.fault) return list_fault("pm_count_each");
     bool any = false;
     for (size_t j = 0; j < nm; j++) any |= flags[j] != 0;
     if (any) {
@@ -1513,6 +1656,7 @@ pm_status pm_count(pm_query_plan *p, void *stream, double timeout_s, uint64_t *c
             set_error("pm_count: deadline expired");
             return PM_ETIMEOUT;
         }
+        if (ctl.fault) return list_fault("pm_count (graph replay)");
         p->timed = true;
         if (matched) std::memcpy(matched, p->h_pinned, sizeof(uint64_t) * 2 * nm);
         (void)timeout_s;

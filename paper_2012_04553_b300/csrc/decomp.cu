@@ -493,6 +493,9 @@ __global__ void combine_kernel(const uint64_t *basis, const int32_t *targets, in
             case DF_K4: v = K4; break;
             case DF_K5: v = ld128(basis, DB_K5); break;
             case DF_K5P3: v = ld128(basis, DB_K5P3); break;
+            case DF_W4: v = ld128(basis, DB_W4); break;
+            case DF_K23: v = ld128(basis, DB_K23); break;
+            case DF_K23E: v = ld128(basis, DB_K23E); break;
             default: break;
         }
         const int slot = targets[2 * i + 1];
@@ -548,6 +551,15 @@ int launch_decomp(const DecompLaunch &L, void *stream) {
     tri_kernel<0><<<dc_blocks(device, (const void *)tri_kernel<0>), DC_WARPS * 32, 0, s>>>(A);
     mirror_kernel<<<dc_blocks(device, (const void *)mirror_kernel), DC_WARPS * 32, 0, s>>>(L.g, L.t,
                                                                                       L.stats);
+    if (L.passes & (DP_W4 | DP_K23E)) {
+        WheelArgs w = L.wheel;
+        w.g = L.g;
+        w.t = L.t;
+        w.basis = L.basis;
+        w.ctl = L.ctl;
+        w.stats = L.stats;
+        if (launch_wheel(w, L.passes, s)) return -1;
+    }
     if (L.passes & DP_LOCAL) {
         if (L.k4e) cudaMemsetAsync(L.k4e, 0, sizeof(uint32_t) * size_t(L.g.nnz), s);
         cudaMemsetAsync(&L.ctl->work3, 0, sizeof(unsigned long long), s);
@@ -571,6 +583,24 @@ int launch_decomp(const DecompLaunch &L, void *stream) {
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) {
         set_error(std::string("decomposition kernel launch: ") + cudaGetErrorString(err));
+        return -1;
+    }
+    return 0;
+}
+
+int launch_decomp_triangles(const DecompLaunch &L, void *stream) {
+    int device = 0;
+    cudaGetDevice(&device);
+    cudaStream_t s = (cudaStream_t)stream;
+    TriArgs A{L.g, L.tasks, L.t, L.basis, L.ctl, nullptr, 0};
+    cudaMemsetAsync(L.t, 0, sizeof(int32_t) * size_t(L.g.nnz), s);
+    cudaMemsetAsync(&L.ctl->work3, 0, sizeof(unsigned long long), s);
+    tri_kernel<0><<<dc_blocks(device, (const void *)tri_kernel<0>), DC_WARPS * 32, 0, s>>>(A);
+    mirror_kernel<<<dc_blocks(device, (const void *)mirror_kernel), DC_WARPS * 32, 0, s>>>(L.g, L.t,
+                                                                                      nullptr);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) {
+        set_error(std::string("triangle pass launch: ") + cudaGetErrorString(err));
         return -1;
     }
     return 0;

@@ -168,7 +168,7 @@ enum DecompSum : int {
     DB_STAR3, DB_STAR4, DB_P4E, DB_TX3, DB_PAW, DB_FORK, DB_P5A, DB_TVD, DB_CRICKET,
     DB_LOLLI_V, DB_BOWTIE_V, DB_BULL, DB_LOLLI_E, DB_KITE, DB_DART_E, DB_BOOK,
     DB_C5TRI, DB_DART_TRI, DB_GEM_TRI, DB_BANNER2, DB_HOUSE, DB_C5Q, DB_C5CORR, DB_C5TM,
-    DB_K23I, DB_COUNT
+    DB_K23I, DB_W4, DB_K23, DB_K23E, DB_COUNT
 };
 // The patterns counted this way (unlabeled, edge-induced).
 enum DecompFormula : int {
@@ -176,14 +176,46 @@ enum DecompFormula : int {
     DF_STAR4, DF_FORK, DF_P5, DF_CRICKET, DF_BULL, DF_LOLLIPOP, DF_BANNER, DF_C5, DF_KITE,
     DF_DART, DF_BOWTIE, DF_HOUSE, DF_BOOK, DF_GEM, DF_K4PENDANT,   // 5 vertices
     DF_K4, DF_K5, DF_K5P3,                                         // cliques, K5 minus a 2-path
+    DF_W4, DF_K23, DF_K23E,                     // 4-wheel, K2,3, K2,3 plus an edge in its 3-side
     DF_COUNT
 };
 // Passes beyond triangle pass 1, the mirror and the vertex/edge pass:
 // triangle pass 2, 2-path pass (with the 5-cycle scan), out-neighbourhood
-// bitmaps (4-cliques; 5-cliques; 4-cliques per edge).
+// bitmaps (4-cliques; 5-cliques; 4-cliques per edge), neighbourhood graphs
+// (common-neighbour lists with the 4-wheel pass; with the K2,3 root pass).
 enum DecompPass : int {
-    DP_TRI2 = 1, DP_PATHS = 2, DP_C5 = 4, DP_LOCAL = 8, DP_K5 = 16, DP_K4E = 32
+    DP_TRI2 = 1, DP_PATHS = 2, DP_C5 = 4, DP_LOCAL = 8, DP_K5 = 16, DP_K4E = 32,
+    DP_W4 = 64, DP_K23E = 128
 };
+// Neighbourhood-graph pass (wheel.cu).
+struct WheelArgs {
+    DevGraph g;
+    const int32_t *t;         // triangles per CSR slot (both endpoints' rows)
+    int64_t *toff;            // nnz + 1 list offsets (exclusive scan of t)
+    int32_t *T;               // common-neighbour lists, positions in the slot's own row
+    int64_t *bsum;            // scan scratch: one word per 8192 slots
+    int32_t *hub_rank;        // popcount rank index of the hub bitmaps, or nullptr
+    int64_t n_hubs;
+    int32_t *mpos;            // DP_K23E: per slot (v, u), v's position in u's row
+    uint32_t *gcnt;           // DP_W4: per block 32-bit counters above 65536 positions, or nullptr
+    int64_t gcnt_words;
+    int w4_blocks;
+    uint32_t *kW;             // DP_K23E: per block n 2-path counters (zero on entry and exit)
+    unsigned long long *kE;   // per block n diamond counters (zero on entry and exit)
+    int32_t *ktouched;        // per block n touched vertices
+    int k23_blocks;
+    uint64_t *basis;
+    Control *ctl;
+    unsigned long long *stats;   // nullable: algorithmic bytes
+};
+size_t w4_smem_bytes();
+int w4_blocks(int device);
+int k23_blocks(int device);
+int64_t w4_global_words(int64_t max_degree);
+int64_t tscan_blocks(int64_t nnz);
+int launch_wheel(const WheelArgs &A, int passes, void *stream);
+int launch_list_offsets(const WheelArgs &A, void *stream);
+int wheel_launches(const WheelArgs &A, int passes);
 // Out-neighbourhood bitmap pass (local.cu).
 struct LocalArgs {
     DevGraph g;
@@ -214,6 +246,7 @@ struct DecompLaunch {
     uint32_t *k4e;            // one uint32 per CSR slot (DP_K4E), or nullptr
     LocalArgs local;          // DP_LOCAL: scratch of the bitmap pass
     int local_blocks;
+    WheelArgs wheel;          // DP_W4 | DP_K23E: lists and counters of the neighbourhood-graph pass
     uint32_t *W;              // path_blocks x n (zero on entry and exit)
     int32_t *touched;         // path_blocks x n
     int path_blocks;
@@ -223,6 +256,8 @@ struct DecompLaunch {
 };
 int decomp_path_blocks(int device);
 int launch_decomp(const DecompLaunch &L, void *stream);
+// triangle pass 1 and the mirror only: t for every slot (list sizes)
+int launch_decomp_triangles(const DecompLaunch &L, void *stream);
 int launch_flag_targets(Control *ctl, uint8_t *timed_out, const int32_t *targets, int n_targets,
                         void *stream);
 int launch_decomp_combine(const uint64_t *basis, const int32_t *targets, int n_targets,

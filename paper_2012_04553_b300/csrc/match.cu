@@ -1055,6 +1055,7 @@ __global__ void arm_kernel(Control *ctl, uint64_t budget_ns) {
     ctl->work3 = 0;
     ctl->work2 = 0;
     ctl->status = 0;
+    ctl->fault = 0;
     ctl->n_deferred = 0;
     ctl->n_pieces = 0;
     ctl->deadline = budget_ns ? global_ns() + budget_ns : 0;

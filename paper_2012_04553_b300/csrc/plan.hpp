@@ -124,7 +124,7 @@ struct DevTasks {
 struct Control {
     unsigned long long work;      // first-pass chunk counter
     int status;
-    int pad;
+    int fault;                    // non-zero: a pass found its inputs inconsistent
     unsigned long long deadline;
     unsigned long long work2;     // second-pass piece counter
     unsigned int n_deferred;      // chunks appended to the deferred list

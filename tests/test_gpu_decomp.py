@@ -17,7 +17,9 @@ pytestmark = pytest.mark.gpu
 
 # canonical masks (lexicographic pair order) of the decomposed patterns
 DECOMP4 = [7, 13, 15, 31, 63]                      # star, P4, tailed triangle, diamond, 4-clique
-DECOMP5 = [15, 29, 58, 31, 59, 62, 185, 220, 63, 187, 207, 221, 127, 223, 191, 255, 1023]
+DECOMP5 = [15, 29, 58, 31, 59, 62, 185, 220, 63, 187, 207, 221, 127, 223, 191, 255, 1023,
+           126, 254, 495]                  # K2,3, K2,3 plus an edge, 4-wheel (neighbourhood graphs)
+WHEEL5 = [126, 254, 495]
 
 
 def ei(k, m):
@@ -111,9 +113,9 @@ def test_decomposition_equals_set_operations_scale11():
 
 @pytest.mark.parametrize("scale,ef,seed", [(7, 6, 306), (8, 6, 307)])
 def test_five_motifs_morphed_with_decomposition(scale, ef, seed):
-    """Vertex-induced 5-motifs via naive morphing (17 edge-induced counts from
-    the decomposition, 4 from set operations) against the oracle's direct
-    vertex-induced counts."""
+    """Vertex-induced 5-motifs via naive morphing (20 edge-induced counts from
+    the decomposition, K5 minus an edge from set operations) against the
+    oracle's direct vertex-induced counts."""
     n = 1 << scale
     s, d = rmat_edges(scale, ef, seed=seed)
     og = oracle.prepare_graph(n, s, d)
@@ -154,3 +156,74 @@ def test_decomposition_on_scale20_matches_free_plans():
     free = pm.Plan(g, qs, mode=pm.MORPH_NONE)
     free.select(pm.PLANS_FREE)
     assert free.count(timeout_s=120.0) == got
+
+
+def test_decomposition_with_hub_bitmaps_everywhere(monkeypatch):
+    """Adjacency bitmaps for every vertex of degree >= 3: the common-neighbour
+    lists and mirror positions then come from the popcount rank index."""
+    monkeypatch.setenv("PM_HUB_MIN_DEGREE", "3")
+    n, s, d = hub_graph()
+    og = oracle.prepare_graph(n, s, d)
+    g = pm.Graph(n, s, d)
+    qs = [ei(5, m) for m in WHEEL5] + [ei(4, 31), ei(5, 1023)]
+    want = [oracle.count(og, algebra.Pattern.from_mask(5, m)) for m in WHEEL5] + \
+           [oracle.count(og, algebra.Pattern.from_mask(4, 31)), oracle.count(og, algebra.Pattern.from_mask(5, 1023))]
+    assert pm.Plan(g, qs, mode=pm.MORPH_NONE).count() == want
+
+
+def big_hub_graph(n, p, seed):
+    """A vertex adjacent to all n-1 others over a random graph on the rest
+    (G(n-1, p), or about p*n*n/2 uniform pairs above 4096 vertices) with a
+    dense 40-vertex block: one row far above 2048 positions (block tasks of
+    the 4-wheel pass), many rims through the hub."""
+    if n <= 4096:
+        s, d = gnp_edges(n - 1, p, seed)
+    else:
+        m = int(p * n * n / 2)
+        s, d = uniform_ints(seed, 3, m, 0, n - 1), uniform_ints(seed, 4, m, 0, n - 1)
+    dense = uniform_ints(seed + 1, 1, 40 * 40, 0, 2)
+    bs = [10 + i for i in range(40) for j in range(i + 1, 40) if dense[i * 40 + j]]
+    bd = [10 + j for i in range(40) for j in range(i + 1, 40) if dense[i * 40 + j]]
+    S = np.concatenate([s.astype(np.int32) + 1, np.array(bs, np.int32), np.zeros(n - 1, np.int32)])
+    D = np.concatenate([d.astype(np.int32) + 1, np.array(bd, np.int32), np.arange(1, n, dtype=np.int32)])
+    return S, D
+
+
+def wheel_vs_plans(g, masks):
+    qs = [ei(5, m) for m in masks]
+    dec = pm.Plan(g, qs, mode=pm.MORPH_NONE)
+    dec.select(pm.PLANS_DECOMP)
+    got = dec.count()
+    for fam in (pm.PLANS_FREE, pm.PLANS_ROOTED):
+        other = pm.Plan(g, qs, mode=pm.MORPH_NONE)
+        other.select(fam)
+        assert other.count(timeout_s=300.0) == got, fam
+    return got
+
+
+@pytest.mark.parametrize("which", ["rmat14", "hub2600"])
+def test_wheel_block_tasks_match_set_operations(which):
+    """Rows of more than 2048 positions (shared-memory block tasks of the
+    4-wheel pass, hub roots of the K2,3 pass) against the free and rooted
+    set-operation plans."""
+    if which == "rmat14":
+        s, d = rmat_edges(14, 16, seed=309)
+        n = 1 << 14
+    else:
+        n = 2600
+        s, d = big_hub_graph(n, 0.004, 310)
+    g = pm.Graph(n, s, d)
+    assert g.info()["max_degree"] > 2048
+    got = wheel_vs_plans(g, WHEEL5)
+    assert all(c > 0 for c in got)
+
+
+def test_wheel_global_counters_above_65536_positions():
+    """A row of 70000 positions: 4-wheel tasks beyond 65536 positions use the
+    per-block global counters."""
+    n = 70001
+    s, d = big_hub_graph(n, 5.0 / n, 311)
+    g = pm.Graph(n, s, d)
+    assert g.info()["max_degree"] == n - 1
+    got = wheel_vs_plans(g, [495])
+    assert got[0] > 0
