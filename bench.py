@@ -422,9 +422,9 @@ def run_serve(args):
     nv = sum(k for k, _, _ in pool)
     label_draw = zipf_labels(nv, 8, s=1.2, seed=66)            # one label per query vertex
     coin = uniform01(65, 0, np.arange(nv, dtype=np.uint64))    # labeled with probability 1/2
-    srv = pm.Server(graphs, workers_per_graph=2, max_batch_patterns=512,
-                    hbm_budget_bytes=100 << 30, batch_timeout_s=0.5, batch_total_s=4.0,
-                    family=pm.PLANS_QUICK)
+    srv = pm.Server(graphs, workers_per_graph=2, max_batch_patterns=256,
+                    hbm_budget_bytes=100 << 30, batch_timeout_s=0.5, batch_total_s=2.0,
+                    family=pm.PLANS_QUICK, request_timeout_s=2.0)
     ids, at, vat, t0 = [], 0, 0, time.time()
     for i in range(nreq):
         wait = arrivals[i] - (time.time() - t0)
@@ -459,8 +459,10 @@ def run_serve(args):
                                    f"3-{args.serve_kmax} vertex "
                                    "patterns per request, R-MAT scale 16/20/22 ef 16 (scale 22 with 8 "
                                    "Zipf(1.2) labels, half the query vertices labeled), naive morph, "
-                                   "quick plan family (no autotuning), 2 workers per graph, 0.5 s "
-                                   "deadline per matched pattern, 4 s per batch"}}
+                                   "quick plan family (no autotuning), 2 workers per graph, batches of "
+                                   "at most 256 patterns, 0.5 s deadline per matched pattern, 2 s per "
+                                   "batch, 2 s per request from submission (requests queued longer are "
+                                   "shed unrun)"}}
     print(json.dumps(line), flush=True)
 
 

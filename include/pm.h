@@ -429,7 +429,12 @@ pm_status pm_count_c4_noalloc(const int64_t *rowptr, const int32_t *col, int64_t
  * join the next batch as soon as a worker is free and the batch's device
  * memory estimate fits hbm_budget_bytes beside the batches in flight;
  * batches on different workers overlap on the device.  Latency is measured
- * from pm_server_submit to the end of the request's batch. */
+ * from pm_server_submit to the end of the request's batch.  With
+ * request_timeout_s > 0 a request still queued that long after submission
+ * completes with PM_ETIMEOUT without device work (load shedding: the queue
+ * cannot grow without bound when requests arrive faster than batches
+ * finish), and a batch's total deadline is cut to the time left to its
+ * oldest request. */
 typedef struct pm_server pm_server;
 typedef struct {
     int32_t workers_per_graph;
@@ -439,12 +444,14 @@ typedef struct {
     double batch_total_s;       /* deadline of the whole batch (<= 0: none) */
     int32_t mode;               /* pm_morph_mode */
     int32_t family;             /* plan family for every batch (pm_plan_select) */
+    double request_timeout_s;   /* deadline of a request from its submission (<= 0: none) */
 } pm_server_config;
 typedef struct {
     int64_t requests_submitted, requests_done, batches, patterns_done;
     int64_t matched_alone;      /* sum over requests of matched patterns if planned alone */
     int64_t matched_batched;    /* sum over batches of matched patterns (after deduplication) */
     int64_t timeouts, failures; /* requests whose batch hit the deadline / failed otherwise */
+    int64_t shed;               /* of the timeouts: dropped unrun after request_timeout_s */
 } pm_server_stats;
 /* graphs stay owned by the caller and must outlive the server. */
 pm_status pm_server_create(const pm_graph *const *graphs, int32_t n_graphs,

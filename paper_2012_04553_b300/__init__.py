@@ -58,13 +58,14 @@ class c_plan_info(ctypes.Structure):
 class c_server_config(ctypes.Structure):
     _fields_ = [("workers_per_graph", ctypes.c_int32), ("max_batch_patterns", ctypes.c_int32),
                 ("hbm_budget_bytes", ctypes.c_int64), ("batch_timeout_s", ctypes.c_double),
-                ("batch_total_s", ctypes.c_double), ("mode", ctypes.c_int32), ("family", ctypes.c_int32)]
+                ("batch_total_s", ctypes.c_double), ("mode", ctypes.c_int32), ("family", ctypes.c_int32),
+                ("request_timeout_s", ctypes.c_double)]
 
 
 class c_server_stats(ctypes.Structure):
     _fields_ = [(nm, ctypes.c_int64) for nm in (
         "requests_submitted", "requests_done", "batches", "patterns_done", "matched_alone",
-        "matched_batched", "timeouts", "failures")]
+        "matched_batched", "timeouts", "failures", "shed")]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)
@@ -529,11 +530,12 @@ class Server:
 
     def __init__(self, graphs, workers_per_graph=2, max_batch_patterns=256,
                  hbm_budget_bytes=64 << 30, batch_timeout_s=0.0, batch_total_s=0.0,
-                 mode=MORPH_NAIVE, family=PLANS_AUTO):
+                 mode=MORPH_NAIVE, family=PLANS_AUTO, request_timeout_s=0.0):
         self.graphs = list(graphs)
         arr = (ctypes.c_void_p * len(self.graphs))(*[g.handle for g in self.graphs])
         cfg = c_server_config(workers_per_graph, max_batch_patterns, int(hbm_budget_bytes),
-                              float(batch_timeout_s), float(batch_total_s), mode, family)
+                              float(batch_timeout_s), float(batch_total_s), mode, family,
+                              float(request_timeout_s))
         h = ctypes.c_void_p()
         _check(_lib.pm_server_create(arr, len(self.graphs), ctypes.byref(cfg), ctypes.byref(h)),
                "pm_server_create")

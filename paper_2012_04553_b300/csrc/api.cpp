@@ -2,6 +2,7 @@
 // the plan-family autotuner, launches and the host half of the morph
 // transform.
 #include <algorithm>
+#include <chrono>
 #include <cstdlib>
 #include <cmath>
 #include <cstddef>
@@ -913,6 +914,14 @@ bool decomp_default(const pm_query_plan *p, size_t j) {
             p->forced == PM_PLANS_DECOMP);
 }
 
+// Family without timing: decomposition where it applies, the rooted family
+// where it runs the wedge kernel, else free.
+int quick_family(const pm_query_plan *p, size_t j) {
+    const bool wedge = p->rooted_begin[j + 1] - p->rooted_begin[j] == 1 &&
+                       p->rooted[p->rooted_begin[j]].kind == PLAN_WEDGE_PAIRS;
+    return decomp_default(p, j) ? PM_PLANS_DECOMP : (wedge ? PM_PLANS_ROOTED : PM_PLANS_FREE);
+}
+
 // Autotuner: for every matched pattern without a decision, time its rooted
 // plans and its free plan (counting kernels) on the same sample of task
 // chunks (every stride-th chunk, about 4096 chunks, 0.5 s deadline each) and
@@ -921,6 +930,9 @@ bool decomp_default(const pm_query_plan *p, size_t j) {
 pm_status autotune(pm_query_plan *p, cudaStream_t s) {
     const pm_graph *g = p->g;
     const size_t nm = p->morph.matched.size();
+    double budget_s = 30.0;
+    if (const char *env = std::getenv("PM_AUTOTUNE_BUDGET_S")) budget_s = std::atof(env);
+    const auto t_start = std::chrono::steady_clock::now();
     for (size_t j = 0; j < nm; j++) {
         if (p->choice[j] >= 0) continue;
         if (decomp_default(p, j)) {
@@ -937,6 +949,13 @@ pm_status autotune(pm_query_plan *p, cudaStream_t s) {
                 p->split_code[j] = sp != g->tuned_split.end() ? sp->second : 1;
                 continue;
             }
+        }
+        if (budget_s > 0 &&
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count() > budget_s) {
+            // sampling budget spent: the quick rule, not cached on the graph
+            p->choice[j] = quick_family(p, j);
+            p->split_code[j] = 1;
+            continue;
         }
         const DevTasks tasks = all_tasks(g);
         float best = std::numeric_limits<float>::infinity();
@@ -1035,14 +1054,7 @@ pm_status prepare_active(pm_query_plan *p, cudaStream_t s) {
     const size_t nm = p->morph.matched.size();
     std::vector<int> want(nm);
     if (p->forced == PM_PLANS_QUICK) {
-        // no timing: decomposition where it applies, the rooted family where
-        // it runs the wedge kernel, else free
-        for (size_t j = 0; j < nm; j++) {
-            const bool wedge = p->rooted_begin[j + 1] - p->rooted_begin[j] == 1 &&
-                               p->rooted[p->rooted_begin[j]].kind == PLAN_WEDGE_PAIRS;
-            want[j] = decomp_default(p, j) ? PM_PLANS_DECOMP
-                                            : (wedge ? PM_PLANS_ROOTED : PM_PLANS_FREE);
-        }
+        for (size_t j = 0; j < nm; j++) want[j] = quick_family(p, j);
     } else if (p->forced == PM_PLANS_ROOTED || p->forced == PM_PLANS_FREE) {
         std::fill(want.begin(), want.end(), p->forced);
     } else {
@@ -1084,6 +1096,22 @@ pm_status prepare_active(pm_query_plan *p, cudaStream_t s) {
     p->decomp_passes_active = passes;
     std::stable_partition(plans.begin(), plans.end(),
                           [](const DevPlan &dp) { return dp.kind == PLAN_SETOPS; });
+    // set-operation plans cheapest pattern first (the autotuner's sampled
+    // time, untimed patterns last; a pattern's plans stay adjacent), so in
+    // one shared launch with a deadline the cheap patterns finish first
+    {
+        std::vector<double> cost(nm, std::numeric_limits<double>::infinity());
+        std::lock_guard<std::mutex> lk(p->g->tune_mu);
+        for (size_t j = 0; j < nm; j++) {
+            auto it = p->g->tuned_ms.find(canonical(p->morph.matched[j]));
+            if (it != p->g->tuned_ms.end()) cost[j] = it->second;
+        }
+        auto setops_end = std::find_if(plans.begin(), plans.end(),
+                                       [](const DevPlan &dp) { return dp.kind != PLAN_SETOPS; });
+        std::stable_sort(plans.begin(), setops_end, [&](const DevPlan &a, const DevPlan &b) {
+            return cost[size_t(a.counter)] < cost[size_t(b.counter)];
+        });
+    }
     if (p->active.plans.size() != plans.size() ||
         std::memcmp(p->active.plans.data(), plans.data(), sizeof(DevPlan) * plans.size()) != 0) {
         p->active.plans = plans;

@@ -12,7 +12,9 @@
 // (morphed) patterns shared by the batch's requests, and every request reads
 // its own slice of the batch's counts.  Each matched pattern of a batch has
 // its own deadline (pm_count_each), so a pattern that runs out of time fails
-// only the requests whose queries need it.  Admission reserves an estimate of the
+// only the requests whose queries need it.  A request queued longer than
+// request_timeout_s is completed unrun with PM_ETIMEOUT (load shedding), and
+// a batch's total deadline never outlasts its oldest request's.  Admission reserves an estimate of the
 // batch's device memory against `hbm_budget_bytes`; a batch waits until the
 // estimate fits.  Latency is measured from submission to completion.
 #include <algorithm>
@@ -79,6 +81,7 @@ void worker_loop(pm_server *s, int graph) {
     const int64_t est = batch_estimate(g);
     for (;;) {
         std::vector<uint64_t> batch;
+        Clock::time_point oldest{};
         {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv_work.wait(lk, [&] {
@@ -87,14 +90,34 @@ void worker_loop(pm_server *s, int graph) {
             });
             if (s->stop) break;
             int npat = 0;
+            bool shed = false;
+            const auto now = Clock::now();
             while (!s->pending[graph].empty()) {
                 const uint64_t id = s->pending[graph].front();
-                const int nq = int(s->reqs[id].queries.size());
+                Request &r = s->reqs[id];
+                if (s->cfg.request_timeout_s > 0 && seconds(now - r.submitted) > s->cfg.request_timeout_s) {
+                    // queued past its deadline: completed unrun
+                    s->pending[graph].pop_front();
+                    r.status = PM_ETIMEOUT;
+                    r.counts.assign(2 * r.queries.size(), 0);
+                    r.finished = now;
+                    r.done = true;
+                    s->stats.matched_alone += r.matched_alone;
+                    s->stats.timeouts++;
+                    s->stats.shed++;
+                    s->stats.requests_done++;
+                    shed = true;
+                    continue;
+                }
+                const int nq = int(r.queries.size());
                 if (!batch.empty() && npat + nq > s->cfg.max_batch_patterns) break;
+                if (batch.empty()) oldest = r.submitted;
                 batch.push_back(id);
                 npat += nq;
                 s->pending[graph].pop_front();
             }
+            if (shed) s->cv_done.notify_all();
+            if (batch.empty()) continue;
             s->reserved += est;
         }
         // one plan for the whole batch
@@ -121,8 +144,13 @@ void worker_loop(pm_server *s, int graph) {
             pm_plan_select(plan, s->cfg.family);
             // a deadline per matched pattern: a heavy pattern fails only the
             // requests that need it
-            st = pm_count_each(plan, stream, s->cfg.batch_timeout_s, s->cfg.batch_total_s,
-                               counts.data(), qstatus.data());
+            double total = s->cfg.batch_total_s;
+            if (s->cfg.request_timeout_s > 0) {
+                // no longer than the oldest request has left
+                const double left = std::max(0.05, s->cfg.request_timeout_s - seconds(Clock::now() - oldest));
+                total = total > 0 ? std::min(total, left) : left;
+            }
+            st = pm_count_each(plan, stream, s->cfg.batch_timeout_s, total, counts.data(), qstatus.data());
             pm_free_plan(plan);
         }
         {

@@ -48,6 +48,8 @@ constexpr int W4_WARP_CAP = 2048;                  // counter positions of a war
 constexpr int W4_SMEM_WORDS = 32768;               // 128 KB: 65536 16-bit block counters
 constexpr int64_t W4_BLOCK_CAP = 2 * int64_t(W4_SMEM_WORDS);
 constexpr int K23_THREADS = 1024;
+constexpr int K23_WARP_CAP = 2048;                 // walk-B window of a warp item (positions)
+constexpr int K23_SMEM_WORDS = 32768;              // 128 KB: 32 warps x 1024 words, or one block window
 
 __device__ __forceinline__ u128 w_c2(uint64_t x) { return x >= 2 ? u128(x) * (x - 1) / 2 : 0; }
 
@@ -465,24 +467,75 @@ __global__ void __launch_bounds__(TL_WARPS * 32) mpos_kernel(WheelArgs A) {
 
 __device__ __forceinline__ u128 w_c3(uint64_t x) { return x >= 3 ? u128(x) * (x - 1) * (x - 2) / 6 : 0; }
 
+// Walk B of one neighbour x of root a (a at position mx of x's row): for
+// each y > x in T_(x,a), +1 at the positions of T_(x,y) below mx.  With
+// CNT != nullptr the counts go to 16-bit counters over x's positions
+// (packed two to a word; a count never exceeds |T_(x,a)| <= 65535 here) and
+// are added to E once per position afterwards; otherwise straight to E.
+template <int STRIDE>
+__device__ __forceinline__ uint64_t k23_walk_b(const WheelArgs &A, unsigned long long *E, uint32_t *cnt,
+                                               int64_t rowx, const int32_t *Y, int32_t k0, int32_t ny,
+                                               int32_t mx, int first, int lane) {
+    uint64_t stat = 0;
+    for (int32_t k = k0 + first; k < ny; k += STRIDE) {
+        const int64_t sy = rowx + __ldg(Y + k);
+        const int64_t b0 = __ldg(A.toff + sy);
+        const int32_t nb = int32_t(__ldg(A.toff + sy + 1) - b0);
+        for (int32_t j = lane; j < nb; j += 32) {
+            const int32_t pb = __ldg(A.T + b0 + j);
+            if (A.stats) stat += 4;
+            if (pb >= mx) break;
+            if (cnt) atomicAdd(cnt + (pb >> 1), (pb & 1) ? 65536u : 1u);
+            else atomicAdd(E + __ldg(A.g.col + rowx + pb), 1ull);
+        }
+        if (A.stats && lane == 0) stat += 4 + 16;
+    }
+    return stat;
+}
+
+// Adds the packed 16-bit counts of positions [0, mx) of x's row to E and
+// clears them (threads `first`, `first` + STRIDE, ...).
+template <int STRIDE>
+__device__ __forceinline__ uint64_t k23_flush(const WheelArgs &A, unsigned long long *E, uint32_t *cnt,
+                                              int64_t rowx, int32_t mx, int first) {
+    uint64_t stat = 0;
+    for (int32_t w = first; w < (mx + 1) / 2; w += STRIDE) {
+        const uint32_t v = cnt[w];
+        if (!v) continue;
+        if (v & 0xffffu) atomicAdd(E + __ldg(A.g.col + rowx + 2 * w), (unsigned long long)(v & 0xffffu));
+        if (v >> 16) atomicAdd(E + __ldg(A.g.col + rowx + 2 * w + 1), (unsigned long long)(v >> 16));
+        cnt[w] = 0;
+        if (A.stats) stat += 4 * (((v & 0xffffu) != 0) + ((v >> 16) != 0)) + 8;
+    }
+    return stat;
+}
+
 // K2,3 and K2,3+e, one block per root (highest-ranked first), with the
-// block's counters W (32-bit), E (64-bit) and touched list in global memory;
-// warps take neighbours of the root from a shared counter in both walks.
-__global__ void __launch_bounds__(K23_THREADS) k23_kernel(WheelArgs A) {
+// block's counters W (32-bit), E (64-bit) and touched list in global memory.
+// Walk A: warps take neighbours w of the root from a shared counter.  Walk
+// B: a warp takes each neighbour x whose window (a's position in x's row)
+// fits its own 2048 16-bit counters; the whole block then takes the others
+// one at a time with 65536 counters in shared memory (rows above that, or
+// lists longer than 65535, add to E directly).
+__global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
+    extern __shared__ uint32_t sc[];
     __shared__ unsigned long long s_root;
     __shared__ int s_stop;
     __shared__ int s_nt;
     __shared__ int s_next[2];
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const DevGraph &g = A.g;
     Control *ctl = A.ctl;
     const uint64_t deadline = *(volatile unsigned long long *)&ctl->deadline;
     uint32_t *W = A.kW + size_t(blockIdx.x) * size_t(g.n);
     unsigned long long *E = A.kE + size_t(blockIdx.x) * size_t(g.n);
     int32_t *touched = A.ktouched + size_t(blockIdx.x) * size_t(g.n);
+    uint32_t *wc = sc + warp * (K23_WARP_CAP / 2);
     u128 k23 = 0, k23e = 0;
     uint64_t stat = 0;
+    for (int i = tid; i < K23_SMEM_WORDS; i += K23_THREADS) sc[i] = 0;
     for (;;) {
+        __syncthreads();
         if (tid == 0) {
             s_root = atomicAdd(&ctl->work3, 1ull);
             s_stop = w_should_stop(ctl, deadline);
@@ -511,14 +564,15 @@ __global__ void __launch_bounds__(K23_THREADS) k23_kernel(WheelArgs A) {
             }
             if (A.stats && lane == 0) stat += 4 + 4 + 16 + 16ull * uint64_t(m);
         }
-        // walk B: edges x < y of G_a, tips b < a in T_(x,y) (x's coordinates)
+        // walk B, warp items: edges x < y of G_a, tips b < a in T_(x,y)
         for (;;) {
             int32_t i = 0;
             if (lane == 0) i = atomicAdd(&s_next[1], 1);
             i = __shfl_sync(FULL, i, 0);
             if (i >= da) break;
-            const int32_t x = __ldg(g.col + rowa + i);
             const int32_t mx = __ldg(A.mpos + rowa + i);          // a's position in x's row
+            if (mx > K23_WARP_CAP) continue;                       // block item
+            const int32_t x = __ldg(g.col + rowa + i);
             const int64_t rowx = __ldg(g.rowptr + x);
             const int64_t y0 = __ldg(A.toff + rowx + mx);         // T_(x,a): the y in N(x) n N(a)
             const int32_t ny = int32_t(__ldg(A.toff + rowx + mx + 1) - y0);
@@ -528,18 +582,37 @@ __global__ void __launch_bounds__(K23_THREADS) k23_kernel(WheelArgs A) {
             const int32_t lox = lower_bound_dev(g.col + rowx, dx, x);    // positions of y > x
             const int32_t k0 = lower_bound_dev(A.T + y0, ny, lox);
             if (A.stats && lane == 0) stat += 8 + w_probe_bytes(dx) + w_probe_bytes(ny);
-            for (int32_t k = k0; k < ny; k++) {
-                const int64_t sy = rowx + __ldg(A.T + y0 + k);
-                const int64_t b0 = __ldg(A.toff + sy);
-                const int32_t nb = int32_t(__ldg(A.toff + sy + 1) - b0);
-                for (int32_t j = lane; j < nb; j += 32) {
-                    const int32_t pb = __ldg(A.T + b0 + j);
-                    if (A.stats) stat += 4;
-                    if (pb >= mx) break;
-                    atomicAdd(E + __ldg(g.col + rowx + pb), 1ull);
-                    if (A.stats) stat += 4 + 16;
-                }
-                if (A.stats && lane == 0) stat += 4 + 16;
+            if (k0 >= ny) continue;
+            const bool agg = ny <= 65535;
+            stat += k23_walk_b<1>(A, E, agg ? wc : nullptr, rowx, A.T + y0, k0, ny, mx, 0, lane);
+            if (agg) {
+                __syncwarp();
+                stat += k23_flush<32>(A, E, wc, rowx, mx, lane);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        // walk B, block items: windows above K23_WARP_CAP, one at a time
+        for (int32_t i = 0; i < da; i++) {
+            const int32_t mx = __ldg(A.mpos + rowa + i);
+            if (mx <= K23_WARP_CAP) continue;                      // uniform
+            const int32_t x = __ldg(g.col + rowa + i);
+            const int64_t rowx = __ldg(g.rowptr + x);
+            const int64_t y0 = __ldg(A.toff + rowx + mx);
+            const int32_t ny = int32_t(__ldg(A.toff + rowx + mx + 1) - y0);
+            if (ny == 0) continue;
+            const int32_t dx = int32_t(__ldg(g.rowptr + x + 1) - rowx);
+            const int32_t lox = lower_bound_dev(g.col + rowx, dx, x);
+            const int32_t k0 = lower_bound_dev(A.T + y0, ny, lox);
+            if (k0 >= ny) continue;
+            if (A.stats && tid == 0) stat += 4 + 4 + 16 + 16 + 8 + w_probe_bytes(dx) + w_probe_bytes(ny);
+            const bool agg = ny <= 65535 && mx <= 2 * K23_SMEM_WORDS;
+            stat += k23_walk_b<K23_THREADS / 32>(A, E, agg ? sc : nullptr, rowx, A.T + y0, k0, ny, mx, warp,
+                                                 lane);
+            if (agg) {
+                __syncthreads();
+                stat += k23_flush<K23_THREADS>(A, E, sc, rowx, mx, tid);
+                __syncthreads();
             }
         }
         __syncthreads();
@@ -557,16 +630,18 @@ __global__ void __launch_bounds__(K23_THREADS) k23_kernel(WheelArgs A) {
             W[b] = 0;
             if (A.stats) stat += 4 + 4 + 8 + 4 + (e ? 8 : 0);
         }
-        __syncthreads();
     }
     w_flush(A.basis, DB_K23, k23, lane);
     w_flush(A.basis, DB_K23E, k23e, lane);
     w_flush_stat(A.stats, stat, lane);
 }
 
+size_t k23_smem_bytes() { return sizeof(uint32_t) * K23_SMEM_WORDS; }
+
 int k23_blocks(int device) {
+    cudaFuncSetAttribute(k23_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(k23_smem_bytes()));
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k23_kernel, K23_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k23_kernel, K23_THREADS, k23_smem_bytes());
     if (per_sm < 1) per_sm = 1;
     return device_sm_count(device) * per_sm;
 }
@@ -617,7 +692,8 @@ int launch_wheel(const WheelArgs &A, int passes, void *stream) {
     if (passes & DP_K23E) {
         mpos_kernel<<<device_sm_count(device) * per_sm, TL_WARPS * 32, 0, s>>>(A);
         cudaMemsetAsync(&A.ctl->work3, 0, sizeof(unsigned long long), s);
-        k23_kernel<<<A.k23_blocks, K23_THREADS, 0, s>>>(A);
+        cudaFuncSetAttribute(k23_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(k23_smem_bytes()));
+        k23_kernel<<<A.k23_blocks, K23_THREADS, k23_smem_bytes(), s>>>(A);
     }
     if (passes & DP_W4) {
         if (A.gcnt) cudaMemsetAsync(A.gcnt, 0, sizeof(uint32_t) * size_t(A.gcnt_words) * size_t(A.w4_blocks), s);

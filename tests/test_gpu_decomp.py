@@ -189,12 +189,12 @@ def big_hub_graph(n, p, seed):
     return S, D
 
 
-def wheel_vs_plans(g, masks):
+def wheel_vs_plans(g, masks, families=(pm.PLANS_FREE, pm.PLANS_ROOTED)):
     qs = [ei(5, m) for m in masks]
     dec = pm.Plan(g, qs, mode=pm.MORPH_NONE)
     dec.select(pm.PLANS_DECOMP)
     got = dec.count()
-    for fam in (pm.PLANS_FREE, pm.PLANS_ROOTED):
+    for fam in families:
         other = pm.Plan(g, qs, mode=pm.MORPH_NONE)
         other.select(fam)
         assert other.count(timeout_s=300.0) == got, fam
@@ -225,5 +225,5 @@ def test_wheel_global_counters_above_65536_positions():
     s, d = big_hub_graph(n, 5.0 / n, 311)
     g = pm.Graph(n, s, d)
     assert g.info()["max_degree"] == n - 1
-    got = wheel_vs_plans(g, [495])
+    got = wheel_vs_plans(g, [495], families=(pm.PLANS_FREE,))
     assert got[0] > 0

@@ -69,3 +69,24 @@ def test_server_rejects_bad_requests():
     with pytest.raises(pm.PMError):
         srv.submit(3, [pm.make_pattern(3, 0b111)])      # no such graph
     srv.close()
+
+
+def test_requests_past_their_deadline_are_shed():
+    """With a request deadline shorter than any batch, requests queued behind
+    the first batch complete unrun with PM_ETIMEOUT (load shedding), the
+    server keeps answering, and a later request with time to spare runs."""
+    s, d = rmat_edges(8, 8, seed=124)
+    g = pm.Graph(256, s, d)
+    q = [pm.make_pattern(4, 0b111111, pm.EDGE_INDUCED)]
+    srv = pm.Server([g], workers_per_graph=1, max_batch_patterns=1, request_timeout_s=1e-9)
+    ids = [srv.submit(0, q) for _ in range(50)]
+    res = [srv.wait(rid) for rid in ids]
+    assert all(done for done, _, _, _ in res)
+    assert all(st == pm.PM_ETIMEOUT for _, _, _, st in res)
+    st = srv.stats()
+    assert st["shed"] >= 1 and st["timeouts"] == 50 and st["requests_done"] == 50
+    srv.close()
+    srv = pm.Server([g], workers_per_graph=1, max_batch_patterns=1, request_timeout_s=30.0)
+    done, counts, lat, status = srv.wait(srv.submit(0, q))
+    assert done and status == pm.PM_OK and counts == pm.Plan(g, q, mode=pm.MORPH_NONE).count()
+    srv.close()
