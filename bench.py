@@ -27,7 +27,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from pm_inputs import cached_rmat, uniform_ints  # noqa: E402
+from pm_inputs import cached_rmat, rmat_edges, uniform_ints  # noqa: E402
 
 SCALE, EDGE_FACTOR, SEED = 20, 16, 2
 FALLBACK_HBM_GBS = 6400.0
@@ -45,12 +45,8 @@ def parse():
                     help="mc: the timed 4-motif counting line (default); mc5: 5-motif counting on "
                          "a systematic root sample, morphed vs direct; fsm / batch / serve: one "
                          "measurement line of the other workloads")
-    ap.add_argument("--mc5-roots", type=int, default=1024, help="root sample size of the mc5 workload")
-    ap.add_argument("--mc5-deadline", type=float, default=60.0, help="deadline of each sampled-root mc5 count")
-    ap.add_argument("--mc5-pattern-deadline", type=float, default=35.0,
-                    help="deadline of each edge-induced 5-vertex pattern in the whole-graph mc5 count")
-    ap.add_argument("--mc5-total-deadline", type=float, default=150.0,
-                    help="deadline of the whole-graph mc5 count")
+    ap.add_argument("--mc5-direct-deadline", type=float, default=60.0,
+                    help="deadline of the whole-graph direct 5-motif count")
     ap.add_argument("--no-mc5", action="store_true", help="leave the 5-motif measurements out of the mc line")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--batch-scale", type=int, default=SCALE)
@@ -476,75 +472,64 @@ def simple_degrees(n, src, dst):
     return np.bincount(key // n, minlength=n) + np.bincount(key % n, minlength=n)
 
 
-def mc5_measurements(pm, g, n, degrees, stream=None, roots_n=1024, deadline=60.0, per_pattern_s=30.0,
-                     total_s=240.0, direct_s=30.0, max_root_degree=48):
-    """5-motif counting (the 21 connected vertex-induced unlabeled patterns)
-    on the loaded graph, morphed vs direct:
-    * sampled roots: occurrences whose highest-ranked vertex is one of a
-      systematic sample of R roots (evenly spaced, in degree order, over the
-      vertices of degree <= max_root_degree), rooted plans, each count under
-      `deadline`; morphed and direct counts must agree exactly;
-    * whole graph, morphed: the 21 edge-induced patterns (Theorem 3.1 /
-      Corollary 3.1 turn them into the 21 vertex-induced counts), each under
-      its own deadline (pm_count_each), with its status and device time;
-    * whole graph, direct: the 21 vertex-induced patterns under `direct_s`."""
+def mc5_measurements(pm, g, n, stream=None, direct_s=60.0, reps=2):
+    """5-motif counting (the 21 connected vertex-induced unlabeled patterns),
+    morphed vs direct:
+    * whole graph, morphed: one plan over the 21 vertex-induced patterns with
+      naive morphing (Theorem 3.1 / Corollary 3.1 over the 21 edge-induced
+      patterns, all counted by the decomposition kernels); one untimed run
+      (list and counter allocation), then `reps` timed runs; per-pattern
+      device time of the edge-induced group;
+    * whole graph, direct: the 21 vertex-induced patterns matched by
+      set-operation plans under `direct_s`;
+    * the R-MAT scale-12 ef-8 graph: both ways to completion, counts
+      compared."""
     import torch
-    # sampled roots: every stride-th vertex, in degree order, among those of
-    # degree <= max_root_degree (rooted plans enumerate about degree^4 maps
-    # per root for the vertex-induced 5-star)
-    by_rank = np.empty(n, dtype=np.int64)
-    by_rank[g.vertex_order()] = np.arange(n)
-    eligible = by_rank[degrees[by_rank] <= max_root_degree]  # ascending degree order
-    stride = max(1, len(eligible) // roots_n)
-    roots = np.sort(eligible[stride // 2::stride][:roots_n]).astype(np.int32)
     masks = connected_classes(5)
     vq = [pm.make_pattern(5, m, pm.VERTEX_INDUCED) for m in masks]
-    sample = {}
-    for name, mode in (("morphed", pm.MORPH_NAIVE), ("direct", pm.MORPH_NONE)):
-        plan = pm.Plan(g, vq, mode=mode)
-        torch.cuda.synchronize()
-        t0 = time.time()
-        try:
-            c = plan.count_roots(roots, stream=stream, timeout_s=deadline)
+
+    def timed(plan, deadline, runs):
+        out = []
+        for _ in range(runs):
             torch.cuda.synchronize()
-            sample[name] = {"wall_s": round(time.time() - t0, 4), "counts": [str(x) for x in c]}
-        except pm.PMTimeout:
-            sample[name] = {"timed_out_after_s": round(time.time() - t0, 3), "deadline_s": deadline}
-    m, d = sample["morphed"], sample["direct"]
-    sample["counts_equal"] = (m["counts"] == d["counts"]) if "counts" in m and "counts" in d else None
-    sample["roots"] = int(len(roots))
-    sample["max_root_degree"] = int(degrees[roots].max()) if len(roots) else 0
-    # whole graph, morphed: edge-induced patterns with a deadline each
-    eplan = pm.Plan(g, [pm.make_pattern(5, mm, pm.EDGE_INDUCED) for mm in masks], mode=pm.MORPH_NONE)
-    eplan.autotune(stream=stream)
-    torch.cuda.synchronize()
-    t0 = time.time()
-    ecounts, status = eplan.count_each(timeout_per_pattern_s=per_pattern_s, timeout_total_s=total_s,
-                                       stream=stream)
-    torch.cuda.synchronize()
-    wall = time.time() - t0
-    fam = eplan.autotune(stream=stream)
-    ms = eplan.pattern_ms()
+            t0 = time.time()
+            try:
+                c = plan.count(stream=stream, timeout_s=deadline)
+                torch.cuda.synchronize()
+                out.append((time.time() - t0, [str(x) for x in c]))
+            except pm.PMTimeout:
+                return None, time.time() - t0
+        return out, None
+
+    morphed = pm.Plan(g, vq, mode=pm.MORPH_NAIVE)
+    fam = morphed.autotune(stream=stream)
+    timed(morphed, 0.0, 1)                                  # allocation run
+    runs, _ = timed(morphed, 0.0, reps)
     names = {0: "rooted", 1: "free", 3: "decomposition"}
-    per = [{"edge_mask": mm, "status": "ok" if st == pm.PM_OK else "deadline", "family": names.get(f, f),
-            "device_ms": round(t, 3)} for mm, st, f, t in zip(masks, status, fam, ms)]
-    whole = {"wall_s": round(wall, 3), "per_pattern_deadline_s": per_pattern_s, "total_deadline_s": total_s,
-             "edge_induced": per, "completed": int(sum(st == pm.PM_OK for st in status))}
-    if all(st == pm.PM_OK for st in status):
-        vplan = pm.Plan(g, vq, mode=pm.MORPH_NAIVE)
-        order = {q[1]: i for i, q in enumerate(eplan.matched_patterns())}
-        matched = [ecounts[order[q[1]]] for q in vplan.matched_patterns()]
-        whole["vertex_induced_counts"] = [str(x) for x in vplan.morph(matched)]
+    whole = {"wall_s": round(min(t for t, _ in runs), 4), "runs_s": [round(t, 4) for t, _ in runs],
+             "vertex_induced_counts": runs[-1][1], "n_matched": morphed.n_matched,
+             "matched_families": sorted({names.get(f, f) for f in fam}),
+             "group_device_ms": round(max(morphed.pattern_ms()), 3), "launches": morphed.last_launches()}
     direct = pm.Plan(g, vq, mode=pm.MORPH_NONE)
-    torch.cuda.synchronize()
-    t0 = time.time()
-    try:
-        dc = direct.count(stream=stream, timeout_s=direct_s)
-        whole_direct = {"wall_s": round(time.time() - t0, 3),
-                        "counts_equal_morphed": [str(x) for x in dc] == whole.get("vertex_induced_counts")}
-    except pm.PMTimeout:
-        whole_direct = {"timed_out_after_s": round(time.time() - t0, 3), "deadline_s": direct_s}
-    return {"sampled_roots": sample, "whole_graph_morphed": whole, "whole_graph_direct": whole_direct}
+    res, out_after = timed(direct, direct_s, 1)
+    if res is None:
+        whole_direct = {"timed_out_after_s": round(out_after, 3), "deadline_s": direct_s}
+    else:
+        whole_direct = {"wall_s": round(res[0][0], 3), "counts_equal_morphed": res[0][1] == whole["vertex_induced_counts"]}
+    # a graph on which direct matching finishes too
+    ss, sd = rmat_edges(12, 8, seed=SEED)
+    gs = pm.Graph(1 << 12, ss, sd)
+    small = {"graph": "R-MAT scale 12, ef 8, seed 2"}
+    for name, mode in (("morphed", pm.MORPH_NAIVE), ("direct", pm.MORPH_NONE)):
+        plan = pm.Plan(gs, vq, mode=mode)
+        plan.autotune(stream=stream)
+        timed(plan, 0.0, 1)
+        r, _ = timed(plan, 0.0, reps)
+        small[name] = {"wall_s": round(min(t for t, _ in r), 5), "counts": r[-1][1]}
+    small["counts_equal"] = small["morphed"]["counts"] == small["direct"]["counts"]
+    small["speedup_morphed_over_direct"] = round(small["direct"]["wall_s"] / small["morphed"]["wall_s"], 2)
+    gs.free()
+    return {"whole_graph_morphed": whole, "whole_graph_direct": whole_direct, "small_graph": small}
 
 
 def run_mc5(args):
@@ -553,9 +538,7 @@ def run_mc5(args):
     n = 1 << SCALE
     src, dst = cached_rmat(SCALE, EDGE_FACTOR, SEED)
     g = pm.Graph(n, src, dst)
-    res = mc5_measurements(pm, g, n, simple_degrees(n, src, dst), roots_n=args.mc5_roots,
-                           deadline=args.mc5_deadline, per_pattern_s=args.mc5_pattern_deadline,
-                           total_s=args.mc5_total_deadline)
+    res = mc5_measurements(pm, g, n, direct_s=args.mc5_direct_deadline)
     line = {"metric": "5-motif counting, morphed vs direct, R-MAT scale 20",
             "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "int64", "data": "synthetic",
             "value": res["whole_graph_morphed"]["wall_s"], "mc5": res,
@@ -709,10 +692,7 @@ def main():
         "graph": {"n": info["n"], "m": info["m"], "max_degree": info["max_degree"]},
     }
     if rank == 0 and not args.no_mc5:
-        line["mc5"] = mc5_measurements(pm, g, n, simple_degrees(n, src, dst), stream=stream,
-                                       roots_n=args.mc5_roots, deadline=args.mc5_deadline,
-                                       per_pattern_s=args.mc5_pattern_deadline,
-                                       total_s=args.mc5_total_deadline)
+        line["mc5"] = mc5_measurements(pm, g, n, stream=stream, direct_s=args.mc5_direct_deadline)
     if rank == 0 and world == 1 and not args.no_baseline:
         base = cpu_oracle_sample(n, src, dst, ks)
         roots = base.pop("roots")

@@ -178,6 +178,10 @@ struct pm_query_plan {
         size_t b_toff = 0, b_T = 0, b_bsum = 0, b_rank = 0, b_mpos = 0, b_gcnt = 0, b_kW = 0, b_kE = 0;
         int64_t gcnt_words = 0;
         int w4_blocks = 0, k23_blocks = 0;
+        uint32_t *k5g = nullptr;
+        size_t b_k5g = 0;
+        int64_t k5g_words = 0;
+        int k5e_blocks = 0;
     } wh;
     // CUDA graph of a whole pm_count (pm_plan_capture): replayed by pm_count
     cudaGraphExec_t graph_exec = nullptr;
@@ -204,6 +208,7 @@ void free_wheel(pm_query_plan *p, int dev) {
     dev_free(w.kW, w.b_kW, dev);
     dev_free(w.kE, w.b_kE, dev);
     dev_free(w.ktouched, w.b_kW, dev);
+    dev_free(w.k5g, w.b_k5g, dev);
     p->wh = {};
 }
 
@@ -586,7 +591,7 @@ pm_status ensure_decomp(pm_query_plan *p, cudaStream_t s) {
             return PM_ENOMEM;
         }
     }
-    if ((passes & (DP_W4 | DP_K23E)) && !p->wh.T) {
+    if ((passes & DP_WHEEL) && !p->wh.T) {
         auto &w = p->wh;
         const int64_t nnz = 2 * g->m;
         auto fail = [&](const char *what) {
@@ -652,6 +657,23 @@ pm_status ensure_decomp(pm_query_plan *p, cudaStream_t s) {
         cudaError_t e = cudaMemsetAsync(w.kW, 0, w.b_kW, s);
         if (!e) e = cudaMemsetAsync(w.kE, 0, w.b_kE, s);
         if (e) return cuda_fail("K2,3 root counters", e);
+    }
+    if ((passes & DP_K5E) && !p->wh.k5e_blocks) {
+        auto &w = p->wh;
+        w.k5e_blocks = k5e_blocks(g->device);
+        w.k5g_words = k5e_global_words(g->max_updeg, g->max_degree);
+        if (w.k5g_words) {
+            // per warp (16 per block): 32-bit counters over the largest up-degree
+            w.b_k5g = sizeof(uint32_t) * size_t(w.k5g_words) * size_t(w.k5e_blocks) * 16;
+            w.k5g = (uint32_t *)dev_alloc(w.b_k5g, g->device);
+            if (!w.k5g) {
+                free_wheel(p, g->device);
+                set_error("device allocation failed (K5 minus an edge counters)");
+                return PM_ENOMEM;
+            }
+            cudaError_t e = cudaMemsetAsync(w.k5g, 0, w.b_k5g, s);
+            if (e) return cuda_fail("K5 minus an edge counters", e);
+        }
     }
     if ((passes & DP_W4) && !p->wh.w4_blocks) {
         auto &w = p->wh;
@@ -857,6 +879,9 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
         D.wheel.kE = p->wh.kE;
         D.wheel.ktouched = p->wh.ktouched;
         D.wheel.k23_blocks = p->wh.k23_blocks;
+        D.wheel.k5g = p->wh.k5g;
+        D.wheel.k5g_words = p->wh.k5g_words;
+        D.wheel.k5e_blocks = p->wh.k5e_blocks;
         D.wheel.g = L.g;
         D.W = p->d_dW;
         D.touched = p->d_dtouched;
@@ -866,7 +891,7 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
         D.stats = stats ? stats + 1 + first : nullptr;
         p->launches += 3 + int((D.passes & DP_TRI2) != 0) + int((D.passes & DP_PATHS) != 0) +
                        2 * int((D.passes & DP_LOCAL) != 0) + 1 +
-                       ((D.passes & (DP_W4 | DP_K23E)) ? wheel_launches(D.wheel, D.passes) : 0);
+                       ((D.passes & DP_WHEEL) ? wheel_launches(D.wheel, D.passes) : 0);
         if (launch_decomp(D, s)) return PM_ECUDA;
         if (launch_decomp_combine(p->d_basis, p->d_targets, nt, p->d_counters, s)) return PM_ECUDA;
         mark(first, 1);
@@ -885,6 +910,7 @@ void rezero_wedge(pm_query_plan *p, cudaStream_t s) {
     if (p->d_dW) cudaMemsetAsync(p->d_dW, 0, p->bytes_dW, s);
     if (p->wh.kW) cudaMemsetAsync(p->wh.kW, 0, p->wh.b_kW, s);
     if (p->wh.kE) cudaMemsetAsync(p->wh.kE, 0, p->wh.b_kE, s);
+    if (p->wh.k5g) cudaMemsetAsync(p->wh.k5g, 0, p->wh.b_k5g, s);
 }
 
 // Task granularity: the second-level candidates a chunk keeps before the

@@ -496,6 +496,7 @@ __global__ void combine_kernel(const uint64_t *basis, const int32_t *targets, in
             case DF_W4: v = ld128(basis, DB_W4); break;
             case DF_K23: v = ld128(basis, DB_K23); break;
             case DF_K23E: v = ld128(basis, DB_K23E); break;
+            case DF_K5E: v = ld128(basis, DB_K5E); break;
             default: break;
         }
         const int slot = targets[2 * i + 1];
@@ -551,7 +552,7 @@ int launch_decomp(const DecompLaunch &L, void *stream) {
     tri_kernel<0><<<dc_blocks(device, (const void *)tri_kernel<0>), DC_WARPS * 32, 0, s>>>(A);
     mirror_kernel<<<dc_blocks(device, (const void *)mirror_kernel), DC_WARPS * 32, 0, s>>>(L.g, L.t,
                                                                                       L.stats);
-    if (L.passes & (DP_W4 | DP_K23E)) {
+    if (L.passes & DP_WHEEL) {
         WheelArgs w = L.wheel;
         w.g = L.g;
         w.t = L.t;

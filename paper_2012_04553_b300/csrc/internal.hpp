@@ -168,7 +168,7 @@ enum DecompSum : int {
     DB_STAR3, DB_STAR4, DB_P4E, DB_TX3, DB_PAW, DB_FORK, DB_P5A, DB_TVD, DB_CRICKET,
     DB_LOLLI_V, DB_BOWTIE_V, DB_BULL, DB_LOLLI_E, DB_KITE, DB_DART_E, DB_BOOK,
     DB_C5TRI, DB_DART_TRI, DB_GEM_TRI, DB_BANNER2, DB_HOUSE, DB_C5Q, DB_C5CORR, DB_C5TM,
-    DB_K23I, DB_W4, DB_K23, DB_K23E, DB_COUNT
+    DB_K23I, DB_W4, DB_K23, DB_K23E, DB_K5E, DB_COUNT
 };
 // The patterns counted this way (unlabeled, edge-induced).
 enum DecompFormula : int {
@@ -177,6 +177,7 @@ enum DecompFormula : int {
     DF_DART, DF_BOWTIE, DF_HOUSE, DF_BOOK, DF_GEM, DF_K4PENDANT,   // 5 vertices
     DF_K4, DF_K5, DF_K5P3,                                         // cliques, K5 minus a 2-path
     DF_W4, DF_K23, DF_K23E,                     // 4-wheel, K2,3, K2,3 plus an edge in its 3-side
+    DF_K5E,                                     // K5 minus an edge
     DF_COUNT
 };
 // Passes beyond triangle pass 1, the mirror and the vertex/edge pass:
@@ -185,7 +186,8 @@ enum DecompFormula : int {
 // (common-neighbour lists with the 4-wheel pass; with the K2,3 root pass).
 enum DecompPass : int {
     DP_TRI2 = 1, DP_PATHS = 2, DP_C5 = 4, DP_LOCAL = 8, DP_K5 = 16, DP_K4E = 32,
-    DP_W4 = 64, DP_K23E = 128
+    DP_W4 = 64, DP_K23E = 128, DP_K5E = 256,
+    DP_WHEEL = DP_W4 | DP_K23E | DP_K5E        // passes that need the common-neighbour lists
 };
 // Neighbourhood-graph pass (wheel.cu).
 struct WheelArgs {
@@ -204,6 +206,9 @@ struct WheelArgs {
     unsigned long long *kE;   // per block n diamond counters (zero on entry and exit)
     int32_t *ktouched;        // per block n touched vertices
     int k23_blocks;
+    uint32_t *k5g;            // DP_K5E: per warp 32-bit counters above 2048 positions, or nullptr
+    int64_t k5g_words;
+    int k5e_blocks;
     uint64_t *basis;
     Control *ctl;
     unsigned long long *stats;   // nullable: algorithmic bytes
@@ -211,6 +216,8 @@ struct WheelArgs {
 size_t w4_smem_bytes();
 int w4_blocks(int device);
 int k23_blocks(int device);
+int k5e_blocks(int device);
+int64_t k5e_global_words(int64_t max_updeg, int64_t max_degree);
 int64_t w4_global_words(int64_t max_degree);
 int64_t tscan_blocks(int64_t nnz);
 int launch_wheel(const WheelArgs &A, int passes, void *stream);

@@ -481,7 +481,7 @@ int decomp_formula(const Pat &p) {
             {5, 63, DF_KITE}, {5, 187, DF_DART}, {5, 207, DF_BOWTIE}, {5, 221, DF_HOUSE},
             {5, 127, DF_BOOK}, {5, 223, DF_GEM}, {5, 191, DF_K4PENDANT},
             {4, 63, DF_K4}, {5, 1023, DF_K5}, {5, 255, DF_K5P3},
-            {5, 495, DF_W4}, {5, 126, DF_K23}, {5, 254, DF_K23E}};
+            {5, 495, DF_W4}, {5, 126, DF_K23}, {5, 254, DF_K23E}, {5, 511, DF_K5E}};
         std::map<Key, int> m;
         for (const auto &r : rows) m[canonical(Pat::from_mask(r.k, r.mask, none, false))] = r.f;
         return m;
@@ -502,6 +502,7 @@ int decomp_passes(int f) {
         case DF_K4PENDANT: case DF_K5P3: return DP_LOCAL | DP_K4E;
         case DF_W4: return DP_W4;
         case DF_K23: case DF_K23E: return DP_K23E;
+        case DF_K5E: return DP_K5E;
         default: return 0;
     }
 }

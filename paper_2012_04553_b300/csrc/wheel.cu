@@ -33,6 +33,17 @@
 // walk B adds 1 to E[b] over the "diamonds" with tips a > b, each edge xy of
 // G_a once (x < y) and b in T_(x,y) below a, read in x's coordinates through
 // the mirror position of a in x's row.
+//
+// K5 minus an edge (9 edges): every edge-induced copy is a triangle
+// (x, y, z) plus two of its common neighbours, so with k_xyz the number of
+// vertices adjacent to all three, K5-e = sum over triangles of C(k_xyz, 2).
+// Each triangle is taken from its lowest-ranked vertex x and edge y < z of
+// G_x above x: per slot (x, y), y > x, +1 at z for every w in T_(x,y) and
+// z in T_(x,w) above y, then k_xyz is the count at each z of T_(x,y) above
+// y.  The counters cover x's positions above y only (fewer than x's
+// neighbours ranked above x, a few hundred on R-MAT graphs).
+#include <algorithm>
+
 #include "devgraph.cuh"
 #include "internal.hpp"
 
@@ -48,6 +59,8 @@ constexpr int W4_WARP_CAP = 2048;                  // counter positions of a war
 constexpr int W4_SMEM_WORDS = 32768;               // 128 KB: 65536 16-bit block counters
 constexpr int64_t W4_BLOCK_CAP = 2 * int64_t(W4_SMEM_WORDS);
 constexpr int K23_THREADS = 1024;
+constexpr int K5E_THREADS = 512;
+constexpr int K5E_WARP_WORDS = 1024;               // 2048 16-bit counters per warp (64 KB per block)
 constexpr int K23_WARP_CAP = 2048;                 // walk-B window of a warp item (positions)
 constexpr int K23_SMEM_WORDS = 32768;              // 128 KB: 32 warps x 1024 words, or one block window
 
@@ -646,6 +659,107 @@ int k23_blocks(int device) {
     return device_sm_count(device) * per_sm;
 }
 
+// K5-e, one warp per slot (x, y) with y > x (32 consecutive slots per
+// chunk), lanes over the w of T_(x,y); 16-bit counters over x's positions
+// above y in the warp's own 1024 shared words (or, for up-degrees above 2048
+// or lists above 65535, 32-bit counters in a per-warp global area).
+__global__ void __launch_bounds__(K5E_THREADS) k5e_kernel(WheelArgs A) {
+    extern __shared__ uint32_t sh[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const DevGraph &g = A.g;
+    Control *ctl = A.ctl;
+    const uint64_t deadline = *(volatile unsigned long long *)&ctl->deadline;
+    const int64_t nnz = g.nnz;
+    const unsigned long long n_chunks = (unsigned long long)((nnz + 31) / 32);
+    uint32_t *wc = sh + warp * K5E_WARP_WORDS;
+    uint32_t *gc = A.k5g ? A.k5g + (size_t(blockIdx.x) * (K5E_THREADS / 32) + size_t(warp)) * size_t(A.k5g_words)
+                         : nullptr;
+    for (int i = lane; i < K5E_WARP_WORDS; i += 32) wc[i] = 0;
+    __syncwarp();
+    u128 acc = 0;
+    uint64_t stat = 0;
+    while (true) {
+        unsigned long long c = 0;
+        int stop = 0;
+        if (lane == 0) {
+            c = atomicAdd(&ctl->work3, 1ull);
+            stop = w_should_stop(ctl, deadline);
+        }
+        c = __shfl_sync(FULL, c, 0);
+        stop = __shfl_sync(FULL, stop, 0);
+        if (c >= n_chunks || stop) break;
+        const int64_t base = int64_t(c) * 32;
+        int32_t xrow = 0;
+        if (base + lane < nnz) xrow = row_of_slot(g.rowptr, base + lane, 0, g.n);
+        for (int q = 0; q < 32; q++) {
+            const int64_t s = base + q;
+            if (s >= nnz) break;
+            const int32_t x = __shfl_sync(FULL, xrow, q);
+            const int32_t y = __ldg(g.col + s);
+            const int32_t ts = __ldg(A.t + s);
+            if (y < x || ts < 2) continue;
+            const int64_t rowx = __ldg(g.rowptr + x);
+            const int32_t dx = int32_t(__ldg(g.rowptr + x + 1) - rowx);
+            const int32_t py = int32_t(s - rowx);
+            const int32_t range = dx - py - 1;                  // positions py+1 .. dx-1
+            const int64_t b0 = __ldg(A.toff + s);
+            const int32_t *TY = A.T + b0;
+            const bool smem = range <= 2 * K5E_WARP_WORDS && ts <= 65535;
+            if (!smem && !gc) {
+                if (lane == 0) atomicExch(&ctl->fault, 1);    // no counters for this slot
+                continue;
+            }
+            // counts: every w of T_(x,y), every z of T_(x,w) above y
+            for (int32_t k = lane; k < ts; k += 32) {
+                const int64_t sw = rowx + __ldg(TY + k);
+                const int64_t w0 = __ldg(A.toff + sw);
+                const int32_t nw = int32_t(__ldg(A.toff + sw + 1) - w0);
+                const int32_t *TW = A.T + w0;
+                for (int32_t j = lower_bound_dev(TW, nw, py + 1); j < nw; j++) {
+                    const int32_t z = __ldg(TW + j) - py - 1;
+                    if (smem) atomicAdd(wc + (z >> 1), (z & 1) ? 65536u : 1u);
+                    else atomicAdd(gc + z, 1u);
+                    if (A.stats) stat += 4;
+                }
+                if (A.stats) stat += 4 + 16 + w_probe_bytes(nw);
+            }
+            __syncwarp();
+            // C(k, 2) at each z of T_(x,y) above y
+            for (int32_t k = lane; k < ts; k += 32) {
+                const int32_t pz = __ldg(TY + k);
+                if (pz <= py) continue;
+                const int32_t z = pz - py - 1;
+                const uint32_t v = smem ? ((wc[z >> 1] >> (16 * (z & 1))) & 0xffffu) : gc[z];
+                acc += w_c2(v);
+                if (A.stats) stat += 4;
+            }
+            __syncwarp();
+            if (smem) {
+                for (int32_t w = lane; w < (range + 1) / 2; w += 32) wc[w] = 0;
+            } else {
+                for (int32_t w = lane; w < range; w += 32) gc[w] = 0;
+            }
+            __syncwarp();
+        }
+    }
+    w_flush(A.basis, DB_K5E, acc, lane);
+    w_flush_stat(A.stats, stat, lane);
+}
+
+int64_t k5e_global_words(int64_t max_updeg, int64_t max_degree) {
+    return (max_updeg > 2 * K5E_WARP_WORDS || max_degree > 65536) ? std::max<int64_t>(max_updeg, 1) : 0;
+}
+
+size_t k5e_smem_bytes() { return sizeof(uint32_t) * (K5E_THREADS / 32) * K5E_WARP_WORDS; }
+
+int k5e_blocks(int device) {
+    cudaFuncSetAttribute(k5e_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(k5e_smem_bytes()));
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k5e_kernel, K5E_THREADS, k5e_smem_bytes());
+    if (per_sm < 1) per_sm = 1;
+    return device_sm_count(device) * per_sm;
+}
+
 size_t w4_smem_bytes() { return sizeof(uint32_t) * W4_SMEM_WORDS; }
 
 int w4_blocks(int device) {
@@ -695,6 +809,11 @@ int launch_wheel(const WheelArgs &A, int passes, void *stream) {
         cudaFuncSetAttribute(k23_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(k23_smem_bytes()));
         k23_kernel<<<A.k23_blocks, K23_THREADS, k23_smem_bytes(), s>>>(A);
     }
+    if (passes & DP_K5E) {
+        cudaMemsetAsync(&A.ctl->work3, 0, sizeof(unsigned long long), s);
+        cudaFuncSetAttribute(k5e_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(k5e_smem_bytes()));
+        k5e_kernel<<<A.k5e_blocks, K5E_THREADS, k5e_smem_bytes(), s>>>(A);
+    }
     if (passes & DP_W4) {
         if (A.gcnt) cudaMemsetAsync(A.gcnt, 0, sizeof(uint32_t) * size_t(A.gcnt_words) * size_t(A.w4_blocks), s);
         cudaMemsetAsync(&A.ctl->work3, 0, sizeof(unsigned long long), s);
@@ -714,7 +833,7 @@ int launch_wheel(const WheelArgs &A, int passes, void *stream) {
 int wheel_launches(const WheelArgs &A, int passes) {
     if (A.g.nnz == 0) return 0;
     return 4 + int(A.g.hub && A.hub_rank && A.n_hubs > 0) + 2 * int((passes & DP_K23E) != 0) +
-           int((passes & DP_W4) != 0);
+           int((passes & DP_W4) != 0) + int((passes & DP_K5E) != 0);
 }
 
 }  // namespace pm
