@@ -435,20 +435,23 @@ def run_serve(args):
             qs.append(pm.make_pattern(k, m, ind, labels))
         at += int(sizes[i])
         ids.append((srv.submit(int(which[i]), qs), len(qs)))
-    lats, ok_pat, statuses = [], 0, {}
+    lats, ok_pat, ok_q, statuses = [], 0, 0, {}
     for rid, nq in ids:
-        done, counts, lat, st = srv.wait(rid)
+        done, counts, lat, st, qst = srv.wait(rid, per_query=True)
         lats.append(lat)
         statuses[st] = statuses.get(st, 0) + 1
         if st == pm.PM_OK:
             ok_pat += nq
+        ok_q += sum(x == pm.PM_OK for x in qst)
     wall = time.time() - t0
     stats = srv.stats()
     srv.close()
     line = {"metric": "serving p50/p99 request latency and patterns/s (Poisson 200 req/s)",
             "value": float(np.percentile(lats, 50)), "unit": "s", "higher_is_better": False,
             "p50_s": float(np.percentile(lats, 50)), "p99_s": float(np.percentile(lats, 99)),
-            "patterns_per_s_completed": ok_pat / wall, "requests": nreq,
+            "patterns_per_s_completed": ok_pat / wall,
+            "query_patterns_per_s_ok": ok_q / wall, "query_patterns_ok": int(ok_q),
+            "query_patterns": int(sizes.sum()), "requests": nreq,
             "status_counts": {str(k): v for k, v in statuses.items()}, "server": stats,
             "n_gpus": 1, "data": "synthetic",
             "config": {"workload": f"Poisson 200 req/s for {args.serve_seconds:.0f} s, 1-64 random "

@@ -461,11 +461,15 @@ pm_status pm_server_create(const pm_graph *const *graphs, int32_t n_graphs,
 pm_status pm_server_submit(pm_server *s, int32_t graph, const pm_pattern *queries, int32_t nq,
                            uint64_t *id);
 /* Wait up to timeout_s (< 0: forever, 0: poll) for request id.  *done = 1
- * when it finished: counts (2*nq words, nullable), *latency_s and
- * *request_status (the batch's pm_count status) are then filled and the
- * request is forgotten. */
+ * when it finished: counts (2*nq words, nullable), *latency_s,
+ * *request_status (PM_OK only if every query of the request succeeded) and
+ * query_status (nq entries, nullable: each query's own status; a query
+ * whose patterns all finished has PM_OK and its count even when another
+ * query of the request timed out) are then filled and the request is
+ * forgotten. */
 pm_status pm_server_wait(pm_server *s, uint64_t id, double timeout_s, int32_t *done,
-                         uint64_t *counts, double *latency_s, pm_status *request_status);
+                         uint64_t *counts, double *latency_s, pm_status *request_status,
+                         int32_t *query_status);
 pm_status pm_server_get_stats(pm_server *s, pm_server_stats *out);
 /* Stops the workers after their current batches; queued requests are dropped. */
 void pm_server_destroy(pm_server *s);

@@ -100,7 +100,7 @@ def _load():
         "pm_server_create": [vp, i32, ctypes.POINTER(c_server_config), ctypes.POINTER(vp)],
         "pm_server_submit": [vp, i32, ctypes.POINTER(c_pattern), i32, ctypes.POINTER(ctypes.c_uint64)],
         "pm_server_wait": [vp, ctypes.c_uint64, dbl, ctypes.POINTER(i32), vp, ctypes.POINTER(dbl),
-                           ctypes.POINTER(ctypes.c_int)],
+                           ctypes.POINTER(ctypes.c_int), vp],
         "pm_server_get_stats": [vp, ctypes.POINTER(c_server_stats)],
         "pm_fsm": [vp, i32, ctypes.c_uint64, ctypes.c_int, vp, dbl, vp, vp, vp, i32, ctypes.POINTER(i32)],
         "pm_count_instrumented": [vp, vp, vp, vp],
@@ -550,19 +550,23 @@ class Server:
         self._nq[rid.value] = len(patterns)
         return rid.value
 
-    def wait(self, rid, timeout_s=-1.0):
-        """(done, counts or None, latency_s, status)."""
+    def wait(self, rid, timeout_s=-1.0, per_query=False):
+        """(done, counts or None, latency_s, status); with per_query=True a
+        fifth item, each query's own status."""
         nq = self._nq[rid]
         out = np.zeros(2 * nq, dtype=np.uint64)
+        qst = np.zeros(nq, dtype=np.int32)
         done = ctypes.c_int32()
         lat = ctypes.c_double()
         st = ctypes.c_int()
         _check(_lib.pm_server_wait(self._h, ctypes.c_uint64(rid), float(timeout_s), ctypes.byref(done),
-                                   _ptr(out), ctypes.byref(lat), ctypes.byref(st)), "pm_server_wait")
+                                   _ptr(out), ctypes.byref(lat), ctypes.byref(st), _ptr(qst)),
+               "pm_server_wait")
         if not done.value:
-            return False, None, None, None
+            return (False, None, None, None) + ((None,) if per_query else ())
         del self._nq[rid]
-        return True, _words_to_ints(out), lat.value, st.value
+        res = (True, _words_to_ints(out), lat.value, st.value)
+        return res + ([int(x) for x in qst],) if per_query else res
 
     def stats(self):
         s = c_server_stats()

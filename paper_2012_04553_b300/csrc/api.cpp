@@ -959,7 +959,14 @@ pm_status autotune(pm_query_plan *p, cudaStream_t s) {
     double budget_s = 30.0;
     if (const char *env = std::getenv("PM_AUTOTUNE_BUDGET_S")) budget_s = std::atof(env);
     const auto t_start = std::chrono::steady_clock::now();
-    for (size_t j = 0; j < nm; j++) {
+    // smallest patterns first, so a spent budget leaves the largest untimed
+    std::vector<size_t> order(nm);
+    for (size_t j = 0; j < nm; j++) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+        const Pat &x = p->morph.matched[a], &y = p->morph.matched[b];
+        return x.k != y.k ? x.k < y.k : x.n_edges() < y.n_edges();
+    });
+    for (size_t j : order) {
         if (p->choice[j] >= 0) continue;
         if (decomp_default(p, j)) {
             p->choice[j] = PM_PLANS_DECOMP;   // per plan: the decision depends on the operation
@@ -1122,8 +1129,8 @@ pm_status prepare_active(pm_query_plan *p, cudaStream_t s) {
     p->decomp_passes_active = passes;
     std::stable_partition(plans.begin(), plans.end(),
                           [](const DevPlan &dp) { return dp.kind == PLAN_SETOPS; });
-    // set-operation plans cheapest pattern first (the autotuner's sampled
-    // time, untimed patterns last; a pattern's plans stay adjacent), so in
+    // set-operation plans smallest pattern first, then by the autotuner's
+    // sampled time (untimed last; a pattern's plans stay adjacent), so in
     // one shared launch with a deadline the cheap patterns finish first
     {
         std::vector<double> cost(nm, std::numeric_limits<double>::infinity());
@@ -1135,6 +1142,8 @@ pm_status prepare_active(pm_query_plan *p, cudaStream_t s) {
         auto setops_end = std::find_if(plans.begin(), plans.end(),
                                        [](const DevPlan &dp) { return dp.kind != PLAN_SETOPS; });
         std::stable_sort(plans.begin(), setops_end, [&](const DevPlan &a, const DevPlan &b) {
+            const Pat &x = p->morph.matched[size_t(a.counter)], &y = p->morph.matched[size_t(b.counter)];
+            if (x.k != y.k) return x.k < y.k;
             return cost[size_t(a.counter)] < cost[size_t(b.counter)];
         });
     }

@@ -40,6 +40,7 @@ struct Request {
     std::vector<pm_pattern> queries;
     Clock::time_point submitted, finished;
     std::vector<uint64_t> counts;   // 2 words per query
+    std::vector<int32_t> qstatus;   // per query
     pm_status status = PM_OK;
     bool done = false;
     int32_t matched_alone = 0;      // matched patterns if planned by itself
@@ -100,6 +101,7 @@ void worker_loop(pm_server *s, int graph) {
                     s->pending[graph].pop_front();
                     r.status = PM_ETIMEOUT;
                     r.counts.assign(2 * r.queries.size(), 0);
+                    r.qstatus.assign(r.queries.size(), PM_ETIMEOUT);
                     r.finished = now;
                     r.done = true;
                     s->stats.matched_alone += r.matched_alone;
@@ -159,9 +161,12 @@ void worker_loop(pm_server *s, int graph) {
             for (size_t b = 0; b < batch.size(); b++) {
                 Request &r = s->reqs[batch[b]];
                 r.status = st;
+                r.qstatus.assign(r.queries.size(), int32_t(st));
                 if (st == PM_OK)
-                    for (size_t qi = 0; qi < r.queries.size(); qi++)
+                    for (size_t qi = 0; qi < r.queries.size(); qi++) {
+                        r.qstatus[qi] = qstatus[first[b] + qi];
                         if (qstatus[first[b] + qi] != PM_OK) r.status = pm_status(qstatus[first[b] + qi]);
+                    }
                 r.counts.assign(counts.begin() + 2 * first[b],
                                 counts.begin() + 2 * (first[b] + r.queries.size()));
                 r.finished = now;
@@ -235,7 +240,8 @@ pm_status pm_server_submit(pm_server *s, int32_t graph, const pm_pattern *querie
 }
 
 pm_status pm_server_wait(pm_server *s, uint64_t id, double timeout_s, int32_t *done,
-                         uint64_t *counts, double *latency_s, pm_status *request_status) {
+                         uint64_t *counts, double *latency_s, pm_status *request_status,
+                         int32_t *query_status) {
     if (!s || !done) return PM_EINVAL;
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->reqs.find(id);
@@ -252,6 +258,7 @@ pm_status pm_server_wait(pm_server *s, uint64_t id, double timeout_s, int32_t *d
     if (counts) std::copy(r.counts.begin(), r.counts.end(), counts);
     if (latency_s) *latency_s = seconds(r.finished - r.submitted);
     if (request_status) *request_status = r.status;
+    if (query_status) std::copy(r.qstatus.begin(), r.qstatus.end(), query_status);
     s->reqs.erase(id);
     return PM_OK;
 }

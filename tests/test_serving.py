@@ -7,7 +7,7 @@ import pytest
 import oracle
 from oracle import algebra
 import paper_2012_04553_b300 as pm
-from pm_inputs import rmat_edges, random_patterns, uniform_ints
+from pm_inputs import pair_index, rmat_edges, random_patterns, uniform_ints
 
 pytestmark = pytest.mark.gpu
 
@@ -80,9 +80,9 @@ def test_requests_past_their_deadline_are_shed():
     q = [pm.make_pattern(4, 0b111111, pm.EDGE_INDUCED)]
     srv = pm.Server([g], workers_per_graph=1, max_batch_patterns=1, request_timeout_s=1e-9)
     ids = [srv.submit(0, q) for _ in range(50)]
-    res = [srv.wait(rid) for rid in ids]
-    assert all(done for done, _, _, _ in res)
-    assert all(st == pm.PM_ETIMEOUT for _, _, _, st in res)
+    res = [srv.wait(rid, per_query=True) for rid in ids]
+    assert all(done for done, _, _, _, _ in res)
+    assert all(st == pm.PM_ETIMEOUT and qst == [pm.PM_ETIMEOUT] for _, _, _, st, qst in res)
     st = srv.stats()
     assert st["shed"] >= 1 and st["timeouts"] == 50 and st["requests_done"] == 50
     srv.close()
@@ -90,3 +90,22 @@ def test_requests_past_their_deadline_are_shed():
     done, counts, lat, status = srv.wait(srv.submit(0, q))
     assert done and status == pm.PM_OK and counts == pm.Plan(g, q, mode=pm.MORPH_NONE).count()
     srv.close()
+
+
+def test_per_query_status_keeps_finished_queries():
+    """A request mixing a pattern that finishes at once (the triangle) with
+    one far beyond its deadline (the vertex-induced 6-star matched directly
+    on hub rows of several hundred): the request fails, the finished query
+    keeps PM_OK and its exact count."""
+    s, d = rmat_edges(12, 16, seed=125)
+    g = pm.Graph(4096, s, d)
+    easy = pm.make_pattern(3, 0b111)
+    star6 = sum(1 << pair_index(6, 0, v) for v in range(1, 6))
+    hard = pm.make_pattern(6, star6, pm.VERTEX_INDUCED)
+    want = pm.Plan(g, [easy], mode=pm.MORPH_NONE).count()[0]
+    srv = pm.Server([g], workers_per_graph=1, max_batch_patterns=8, batch_timeout_s=0.2,
+                    mode=pm.MORPH_NONE, family=pm.PLANS_FREE)
+    done, counts, lat, st, qst = srv.wait(srv.submit(0, [easy, hard]), per_query=True)
+    srv.close()
+    assert done and st == pm.PM_ETIMEOUT
+    assert qst == [pm.PM_OK, pm.PM_ETIMEOUT] and counts[0] == want
