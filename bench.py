@@ -535,7 +535,6 @@ def mc5_measurements(pm, g, n, stream=None, direct_s=60.0, reps=2):
         small[name] = {"wall_s": round(min(t for t, _ in r), 5), "counts": r[-1][1]}
     small["counts_equal"] = small["morphed"]["counts"] == small["direct"]["counts"]
     small["speedup_morphed_over_direct"] = round(small["direct"]["wall_s"] / small["morphed"]["wall_s"], 2)
-    gs.free()
     return {"whole_graph_morphed": whole, "whole_graph_direct": whole_direct, "small_graph": small}
 
 

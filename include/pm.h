@@ -275,10 +275,10 @@ pm_status pm_plan_capture(pm_query_plan *p, void *stream, double timeout_s);
 /* pm_count_each recorded as one CUDA graph (the per-pattern and total
  * deadlines are fixed into it); later pm_count_each calls on the plan replay
  * it and ignore their own deadlines.  In PM_LAUNCH_SINGLE mode the plans
- * share one persistent launch and every pattern's deadline runs from the
- * launch start: the patterns whose work the deadline cuts (counted from
- * per-plan progress counters) report PM_ETIMEOUT, the others their exact
- * counts. */
+ * of each pattern size share one persistent launch (sizes in increasing
+ * order) and every pattern's deadline runs from its launch's start: the
+ * patterns whose work the deadline cuts (counted from per-plan progress
+ * counters) report PM_ETIMEOUT, the others their exact counts. */
 pm_status pm_plan_capture_each(pm_query_plan *p, void *stream, double timeout_per_pattern_s,
                                double timeout_total_s);
 

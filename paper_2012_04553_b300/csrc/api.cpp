@@ -172,10 +172,9 @@ struct pm_query_plan {
         int32_t *rank = nullptr;
         int32_t *mpos = nullptr;
         uint32_t *gcnt = nullptr;
-        uint32_t *kW = nullptr;
-        unsigned long long *kE = nullptr;
+        unsigned long long *kV = nullptr;
         int32_t *ktouched = nullptr;
-        size_t b_toff = 0, b_T = 0, b_bsum = 0, b_rank = 0, b_mpos = 0, b_gcnt = 0, b_kW = 0, b_kE = 0;
+        size_t b_toff = 0, b_T = 0, b_bsum = 0, b_rank = 0, b_mpos = 0, b_gcnt = 0, b_kV = 0, b_kt = 0;
         int64_t gcnt_words = 0;
         int w4_blocks = 0, k23_blocks = 0;
         uint32_t *k5g = nullptr;
@@ -205,9 +204,8 @@ void free_wheel(pm_query_plan *p, int dev) {
     dev_free(w.rank, w.b_rank, dev);
     dev_free(w.mpos, w.b_mpos, dev);
     dev_free(w.gcnt, w.b_gcnt, dev);
-    dev_free(w.kW, w.b_kW, dev);
-    dev_free(w.kE, w.b_kE, dev);
-    dev_free(w.ktouched, w.b_kW, dev);
+    dev_free(w.kV, w.b_kV, dev);
+    dev_free(w.ktouched, w.b_kt, dev);
     dev_free(w.k5g, w.b_k5g, dev);
     p->wh = {};
 }
@@ -218,6 +216,9 @@ struct DeviceGuard {
     explicit DeviceGuard(int dev) {
         cudaGetDevice(&prev);
         ok = cudaSetDevice(dev) == cudaSuccess;
+        // a failed runtime call made earlier on this thread (outside this
+        // call) must not be read back as this call's launch error
+        if (ok) cudaGetLastError();
     }
     ~DeviceGuard() { cudaSetDevice(prev); }
 };
@@ -639,23 +640,25 @@ pm_status ensure_decomp(pm_query_plan *p, cudaStream_t s) {
         w.T = (int32_t *)dev_alloc(w.b_T, g->device);
         if (!w.T) return fail("common-neighbour lists");
     }
-    if ((passes & DP_K23E) && !p->wh.kW) {
+    if ((passes & DP_K23E) && !p->wh.kV) {
+        if (g->max_degree > k23_max_degree()) {
+            set_error("K2,3 counts: the largest degree exceeds the packed counters' range");
+            return PM_EUNSUPPORTED;
+        }
         auto &w = p->wh;
         w.k23_blocks = k23_blocks(g->device);
         w.b_mpos = sizeof(int32_t) * size_t(std::max<int64_t>(2 * g->m, 1));
-        w.b_kW = sizeof(uint32_t) * size_t(g->n) * size_t(w.k23_blocks);
-        w.b_kE = sizeof(unsigned long long) * size_t(g->n) * size_t(w.k23_blocks);
+        w.b_kV = sizeof(unsigned long long) * size_t(g->n) * size_t(w.k23_blocks);
+        w.b_kt = sizeof(int32_t) * size_t(g->n) * size_t(w.k23_blocks);
         w.mpos = (int32_t *)dev_alloc(w.b_mpos, g->device);
-        w.kW = (uint32_t *)dev_alloc(w.b_kW, g->device);
-        w.kE = (unsigned long long *)dev_alloc(w.b_kE, g->device);
-        w.ktouched = (int32_t *)dev_alloc(w.b_kW, g->device);
-        if (!w.mpos || !w.kW || !w.kE || !w.ktouched) {
+        w.kV = (unsigned long long *)dev_alloc(w.b_kV, g->device);
+        w.ktouched = (int32_t *)dev_alloc(w.b_kt, g->device);
+        if (!w.mpos || !w.kV || !w.ktouched) {
             free_wheel(p, g->device);
             set_error("device allocation failed (K2,3 root counters)");
             return PM_ENOMEM;
         }
-        cudaError_t e = cudaMemsetAsync(w.kW, 0, w.b_kW, s);
-        if (!e) e = cudaMemsetAsync(w.kE, 0, w.b_kE, s);
+        cudaError_t e = cudaMemsetAsync(w.kV, 0, w.b_kV, s);
         if (e) return cuda_fail("K2,3 root counters", e);
     }
     if ((passes & DP_K5E) && !p->wh.k5e_blocks) {
@@ -772,38 +775,60 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
             mark(t.plans[b].counter, 1);
             b = e;
         }
-    } else if (n_setops > 0 && L.n_echunks > 0) {
+    } else if (n_setops > 0 && L.n_echunks > 0 && !gate_flags) {
         L.nplans = n_setops;
-        if (gate_flags) {
-            // per-pattern deadlines inside the one launch: every pattern gets
-            // the budget from the launch start; plans whose work is cut are
-            // flagged from their progress counters afterwards
-            if (!p->d_plan_done || p->plan_done_cap < size_t(n_setops)) {
-                dev_free(p->d_plan_done, sizeof(unsigned int) * 3 * p->plan_done_cap, g->device);
-                p->plan_done_cap = size_t(n_setops);
-                p->d_plan_done = (unsigned int *)dev_alloc(sizeof(unsigned int) * 3 * p->plan_done_cap,
-                                                           g->device);
-                if (!p->d_plan_done) {
-                    p->plan_done_cap = 0;
-                    set_error("device allocation failed (plan progress)");
-                    return PM_ENOMEM;
-                }
-            }
-            cudaMemsetAsync(p->d_plan_done, 0, sizeof(unsigned int) * 3 * size_t(n_setops), s);
-            L.plan_done = p->d_plan_done;
-            p->launches++;
-            if (launch_pattern_gate(p->d_ctl, gate_flags, -1, gate_budget_ns, s)) return PM_ECUDA;
-        }
         p->launches += 3;
         L.stats = stats ? stats + 1 + t.plans[0].counter : nullptr;     // one launch: all on the first
         const int rc = domains ? launch_domains(L, s) : launch_count(L, s);
         if (rc) return PM_ECUDA;
-        if (gate_flags) {
+    } else if (n_setops > 0 && L.n_echunks > 0) {
+        // per-pattern deadlines in the shared launch: one persistent launch
+        // (both passes over one queue) per pattern size, smallest first (the
+        // plans are sorted so), each pattern with the budget from its
+        // launch's start; plans whose work is cut are flagged from their
+        // progress counters.  A size's deferred hub pieces are thus taken up
+        // as soon as that size's first pass ends, not behind larger patterns.
+        if (!p->d_plan_done || p->plan_done_cap < size_t(n_setops)) {
+            dev_free(p->d_plan_done, sizeof(unsigned int) * 3 * p->plan_done_cap, g->device);
+            p->plan_done_cap = size_t(n_setops);
+            p->d_plan_done = (unsigned int *)dev_alloc(sizeof(unsigned int) * 3 * p->plan_done_cap,
+                                                       g->device);
+            if (!p->d_plan_done) {
+                p->plan_done_cap = 0;
+                set_error("device allocation failed (plan progress)");
+                return PM_ENOMEM;
+            }
+        }
+        int b = 0;
+        while (b < n_setops) {
+            const int kb = p->morph.matched[size_t(t.plans[b].counter)].k;
+            int e = b + 1;
+            while (e < n_setops && p->morph.matched[size_t(t.plans[e].counter)].k == kb) e++;
+            MatchLaunch G = L;
+            G.plans = t.d + b;
+            G.nplans = e - b;
+            std::vector<DevPlan> sub(t.plans.begin() + b, t.plans.begin() + e);
+            G.n_echunks = echunks_for(sub, tasks);
+            G.max_enum = 2;
+            for (const DevPlan &dp : sub) G.max_enum = std::max(G.max_enum, int(dp.n_enum));
+            if (G.n_echunks == 0) {
+                b = e;
+                continue;
+            }
+            cudaMemsetAsync(p->d_plan_done, 0, sizeof(unsigned int) * 3 * size_t(e - b), s);
+            G.plan_done = p->d_plan_done;
+            p->launches++;
+            if (launch_pattern_gate(p->d_ctl, gate_flags, -1, gate_budget_ns, s)) return PM_ECUDA;
+            p->launches += 3;
+            G.stats = stats ? stats + 1 + t.plans[b].counter : nullptr;
+            const int rc = domains ? launch_domains(G, s) : launch_count(G, s);
+            if (rc) return PM_ECUDA;
             const int64_t stride = sample_stride > 1 ? sample_stride : 1;
             p->launches++;
-            if (launch_plan_flags(p->d_ctl, t.d, n_setops, p->d_plan_done,
-                                  (unsigned long long)((L.n_echunks + stride - 1) / stride), gate_flags, s))
+            if (launch_plan_flags(p->d_ctl, G.plans, e - b, p->d_plan_done,
+                                  (unsigned long long)((G.n_echunks + stride - 1) / stride), gate_flags, s))
                 return PM_ECUDA;
+            b = e;
         }
     }
     int last = n_setops > 0 && !(gate_flags && p->launch_mode == PM_LAUNCH_SINGLE)
@@ -875,8 +900,7 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
         D.wheel.gcnt = p->wh.gcnt;
         D.wheel.gcnt_words = p->wh.gcnt_words;
         D.wheel.w4_blocks = p->wh.w4_blocks;
-        D.wheel.kW = p->wh.kW;
-        D.wheel.kE = p->wh.kE;
+        D.wheel.kV = p->wh.kV;
         D.wheel.ktouched = p->wh.ktouched;
         D.wheel.k23_blocks = p->wh.k23_blocks;
         D.wheel.k5g = p->wh.k5g;
@@ -908,8 +932,7 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
 void rezero_wedge(pm_query_plan *p, cudaStream_t s) {
     if (p->d_wedge) cudaMemsetAsync(p->d_wedge, 0, p->bytes_wedge, s);
     if (p->d_dW) cudaMemsetAsync(p->d_dW, 0, p->bytes_dW, s);
-    if (p->wh.kW) cudaMemsetAsync(p->wh.kW, 0, p->wh.b_kW, s);
-    if (p->wh.kE) cudaMemsetAsync(p->wh.kE, 0, p->wh.b_kE, s);
+    if (p->wh.kV) cudaMemsetAsync(p->wh.kV, 0, p->wh.b_kV, s);
     if (p->wh.k5g) cudaMemsetAsync(p->wh.k5g, 0, p->wh.b_k5g, s);
 }
 

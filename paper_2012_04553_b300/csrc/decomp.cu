@@ -340,6 +340,29 @@ __global__ void __launch_bounds__(DC_WARPS * 32) ve_kernel(DevGraph g, const int
     (void)ctl;
 }
 
+// Several lists per warp, one per lane (cnt_l entries each): prefix sums
+// over the lanes, and for entry e of their concatenation the lane that
+// holds it (last lane whose exclusive prefix is <= e).  Every lane calls
+// both, so owner context can be fetched with shuffles.
+__device__ __forceinline__ int32_t lanes_scan(int32_t cnt, int lane, int32_t &excl) {
+    int32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    excl = incl - cnt;
+    return __shfl_sync(FULL, incl, 31);
+}
+
+__device__ __forceinline__ int lanes_owner(int32_t excl, int32_t e) {
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+        if (__shfl_sync(FULL, excl, lo + step) <= e) lo += step;
+    return lo;
+}
+
 // 2-path pass: one block per root a at a time (highest-ranked first, from a
 // shared counter), with the block's counters W (n words, zero between roots)
 // and its list of touched vertices in global memory.
@@ -382,60 +405,101 @@ __global__ void __launch_bounds__(P2_THREADS) paths2_kernel(DevGraph g, const in
         const int32_t da = int32_t(__ldg(g.rowptr + a + 1) - rowa);
         const int32_t la = lower_bound_dev(g.col + rowa, da, a);
         if (stats && tid == 0) stat += 16 + probe_bytes(da) + 4ull * uint64_t(la);
-        // walk 1
-        for (int i = warp; i < la; i += nwarps) {
-            const int32_t b = __ldg(g.col + rowa + i);
-            const int64_t rowb = __ldg(g.rowptr + b);
-            const int32_t bl = lower_bound_dev(g.col + rowb, int32_t(__ldg(g.rowptr + b + 1) - rowb), a);
-            if (stats && lane == 0)
-                stat += 2 * (16 + probe_bytes(__ldg(g.rowptr + b + 1) - rowb)) + uint64_t(bl) * (12 + 28);
-            for (int32_t j = lane; j < bl; j += 32) {
-                const int32_t c = __ldg(g.col + rowb + j);
-                const uint32_t old = atomicAdd(W + c, 1u);
-                c4acc += old;
-                if (old == 0) touched[atomicAdd(&s_nt, 1)] = c;
+        // walk 1 (32 neighbours b per warp, one per lane, their rows below a
+        // walked together)
+        for (int i0 = warp * 32; i0 < la; i0 += nwarps * 32) {
+            const int i = i0 + lane;
+            int64_t rowb = 0;
+            int32_t bl = 0;
+            if (i < la) {
+                const int32_t b = __ldg(g.col + rowa + i);
+                rowb = __ldg(g.rowptr + b);
+                const int64_t db = __ldg(g.rowptr + b + 1) - rowb;
+                bl = lower_bound_dev(g.col + rowb, int32_t(db), a);
+                if (stats) stat += 2 * (16 + probe_bytes(db)) + uint64_t(bl) * (12 + 28);
+            }
+            int32_t excl;
+            const int32_t total = lanes_scan(bl, lane, excl);
+            for (int32_t e0 = 0; e0 < total; e0 += 32) {
+                const int32_t e = e0 + lane;
+                const int o = lanes_owner(excl, e);
+                const int64_t orow = __shfl_sync(FULL, rowb, o);
+                const int32_t oex = __shfl_sync(FULL, excl, o);
+                if (e < total) {
+                    const int32_t c = __ldg(g.col + orow + (e - oex));
+                    const uint32_t old = atomicAdd(W + c, 1u);
+                    c4acc += old;
+                    if (old == 0) touched[atomicAdd(&s_nt, 1)] = c;
+                }
             }
         }
         __syncthreads();
-        // walk 2
-        for (int i = warp; i < la; i += nwarps) {
-            const int32_t b = __ldg(g.col + rowa + i);
-            const int64_t rowb = __ldg(g.rowptr + b);
-            const int32_t db = int32_t(__ldg(g.rowptr + b + 1) - rowb);
-            const int32_t bl = lower_bound_dev(g.col + rowb, db, a);
-            const int64_t tab = __ldg(t + rowa + i);
-            for (int32_t j = lane; j < bl; j += 32) {
-                const int32_t c = __ldg(g.col + rowb + j);
-                const uint32_t w = W[c];
-                if (w > 1) {
-                    const int64_t dc = deg_of(g, c);
-                    banner += u128(w - 1) * uint64_t(2 * int64_t(db) + da + dc - 8);
-                    house += u128(w - 1) * uint64_t(tab + __ldg(t + rowb + j));
-                }
-            }
-            if (lane == 0) {
+        // walk 2 (same grouping)
+        for (int i0 = warp * 32; i0 < la; i0 += nwarps * 32) {
+            const int i = i0 + lane;
+            int64_t rowb = 0;
+            int32_t bl = 0, db = 0, tab = 0;
+            if (i < la) {
+                const int32_t b = __ldg(g.col + rowa + i);
+                rowb = __ldg(g.rowptr + b);
+                db = int32_t(__ldg(g.rowptr + b + 1) - rowb);
+                bl = lower_bound_dev(g.col + rowb, db, a);
+                tab = __ldg(t + rowa + i);
                 const uint32_t wb = W[b];
                 corr += u128(uint64_t(bl)) * wb;
                 tm += wb;
             }
+            int32_t excl;
+            const int32_t total = lanes_scan(bl, lane, excl);
+            for (int32_t e0 = 0; e0 < total; e0 += 32) {
+                const int32_t e = e0 + lane;
+                const int o = lanes_owner(excl, e);
+                const int64_t orow = __shfl_sync(FULL, rowb, o);
+                const int32_t oex = __shfl_sync(FULL, excl, o);
+                const int32_t odb = __shfl_sync(FULL, db, o);
+                const int32_t otab = __shfl_sync(FULL, tab, o);
+                if (e < total) {
+                    const int64_t slot = orow + (e - oex);
+                    const int32_t c = __ldg(g.col + slot);
+                    const uint32_t w = W[c];
+                    if (w > 1) {
+                        const int64_t dc = deg_of(g, c);
+                        banner += u128(w - 1) * uint64_t(2 * int64_t(odb) + da + dc - 8);
+                        house += u128(w - 1) * uint64_t(int64_t(otab) + __ldg(t + slot));
+                    }
+                }
+            }
         }
-        // touched vertices
+        // touched vertices (32 per warp; for 5-cycles their rows below them
+        // walked together)
         const int nt = s_nt;
-        for (int q = warp; q < nt; q += nwarps) {
-            const int32_t c = touched[q];
-            const uint32_t w = W[c];
-            if (lane == 0) k23 += c3(w);
-            if (stats && lane == 0) stat += 8 + 4;       // touched entry, its counter, the reset
-            if (with_c5) {
-                const int64_t rowc = __ldg(g.rowptr + c);
-                const int32_t lc = lower_bound_dev(g.col + rowc, int32_t(__ldg(g.rowptr + c + 1) - rowc), c);
-                if (stats && lane == 0)
-                    stat += 16 + probe_bytes(__ldg(g.rowptr + c + 1) - rowc) + 8ull * uint64_t(lc);
-                uint64_t s = 0;
-                for (int32_t j = lane; j < lc; j += 32) s += W[__ldg(g.col + rowc + j)];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-                if (lane == 0) qh += u128(w) * s;
+        for (int q0 = warp * 32; q0 < nt; q0 += nwarps * 32) {
+            const int q = q0 + lane;
+            int32_t c = 0, lc = 0;
+            uint32_t w = 0;
+            int64_t rowc = 0;
+            if (q < nt) {
+                c = touched[q];
+                w = W[c];
+                k23 += c3(w);
+                if (stats) stat += 8 + 4;       // touched entry, its counter, the reset
+                if (with_c5) {
+                    rowc = __ldg(g.rowptr + c);
+                    const int64_t dcc = __ldg(g.rowptr + c + 1) - rowc;
+                    lc = lower_bound_dev(g.col + rowc, int32_t(dcc), c);
+                    if (stats) stat += 16 + probe_bytes(dcc) + 8ull * uint64_t(lc);
+                }
+            }
+            if (!with_c5) continue;
+            int32_t excl;
+            const int32_t total = lanes_scan(lc, lane, excl);
+            for (int32_t e0 = 0; e0 < total; e0 += 32) {
+                const int32_t e = e0 + lane;
+                const int o = lanes_owner(excl, e);
+                const int64_t orow = __shfl_sync(FULL, rowc, o);
+                const int32_t oex = __shfl_sync(FULL, excl, o);
+                const uint32_t ow = __shfl_sync(FULL, w, o);
+                if (e < total) qh += u128(ow) * W[__ldg(g.col + orow + (e - oex))];
             }
         }
         __syncthreads();

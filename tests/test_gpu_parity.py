@@ -611,9 +611,10 @@ def test_batch_128_patterns_single_launch_with_deadlines():
 
 
 def test_single_launch_per_pattern_deadlines():
-    """In one persistent launch every pattern's deadline runs from the launch
-    start: the vertex-induced 5-star (seconds of work here) is cut and
-    reported, the triangle and wedge complete exactly, captured or not."""
+    """In the shared launch mode (one persistent launch per pattern size)
+    every pattern's deadline runs from its launch's start: the
+    vertex-induced 5-star (seconds of work here) is cut and reported, the
+    triangle and wedge complete exactly, captured or not."""
     s, d = rmat_edges(14, 16, seed=119)
     g = load(1 << 14, s, d)
     light = [pm.make_pattern(3, 0b111), pm.make_pattern(3, 0b011)]
