@@ -14,7 +14,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpm_b300.so")
+# PM_DEBUG=1 selects the bounds-checked build (build.py --debug)
+LIB_PATH = os.path.join(_HERE, "libpm_b300_debug.so" if os.environ.get("PM_DEBUG") == "1" else "libpm_b300.so")
 
 PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_ETIMEOUT, PM_EOVERFLOW, PM_EUNSUPPORTED, PM_ECANCELLED = \
     0, -1, -2, -3, -4, -5, -6, -7
@@ -74,7 +75,8 @@ _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2012_04553_b300/build.py`")
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2012_04553_b300/build.py`"
+                          + (" --debug" if LIB_PATH.endswith("_debug.so") else ""))
     lib = ctypes.CDLL(LIB_PATH)
     vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
     sig = {

@@ -189,10 +189,13 @@ struct pm_query_plan {
 
 namespace {
 
-// A pass found its inputs inconsistent (common-neighbour lists whose
-// lengths differ from the per-edge triangle counts): an internal error.
-pm_status list_fault(const char *who) {
-    set_error(std::string(who) + ": common-neighbour lists disagree with the per-edge triangle counts");
+// A kernel set the control block's fault word: 1 = common-neighbour lists
+// whose lengths differ from the per-edge triangle counts, 2 = an index out
+// of range caught by the PM_DEBUG build's bounds checks (the access was
+// skipped).  Both are internal errors; the results are not returned.
+pm_status list_fault(const char *who, int fault) {
+    set_error(std::string(who) + (fault == 2 ? ": a kernel bounds check failed (PM_DEBUG build)"
+                                             : ": common-neighbour lists disagree with the per-edge triangle counts"));
     return PM_ECUDA;
 }
 
@@ -893,6 +896,7 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
         }
         D.wheel.toff = p->wh.toff;
         D.wheel.T = p->wh.T;
+        D.wheel.T_len = int64_t(p->wh.b_T / sizeof(int32_t));
         D.wheel.bsum = p->wh.bsum;
         D.wheel.hub_rank = p->wh.rank;
         D.wheel.n_hubs = p->wh.rank ? g->n_hubs : 0;
@@ -1317,7 +1321,7 @@ pm_status run_count(pm_query_plan *p, void *stream, double timeout_s, const int3
         set_error("pm_count: deadline expired");
         return PM_ETIMEOUT;
     }
-    if (ctl.fault) return list_fault("pm_count");
+    if (ctl.fault) return list_fault("pm_count", ctl.fault);
     if (matched) std::memcpy(matched, raw.data(), sizeof(uint64_t) * 2 * nm);
     return pm_morph(p, raw.data(), counts);
 }
@@ -1354,7 +1358,7 @@ pm_status run_count_each(pm_query_plan *p, void *stream, double timeout_s, doubl
         std::memcpy(flags.data(), reinterpret_cast<uint8_t *>(p->h_pinned + 2 * nm) + sizeof(Control), nm);
         Control ctl;
         std::memcpy(&ctl, p->h_pinned + 2 * nm, sizeof(Control));
-        if (ctl.fault) return list_fault("pm_count_each (graph replay)");
+        if (ctl.fault) return list_fault("pm_count_each (graph replay)", ctl.fault);
         bool any = false;
         for (size_t j = 0; j < nm; j++) any |= flags[j] != 0;
         if (any) {
@@ -1401,7 +1405,7 @@ pm_status run_count_each(pm_query_plan *p, void *stream, double timeout_s, doubl
     if (!e) e = cudaMemcpyAsync(&ctl, p->d_ctl, sizeof(Control), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return cuda_fail("pm_count_each: kernel or readback", e);
-    if (ctl.fault) return list_fault("pm_count_each");
+    if (ctl.fault) return list_fault("pm_count_each", ctl.fault);
     bool any = false;
     for (size_t j = 0; j < nm; j++) any |= flags[j] != 0;
     if (any) {
@@ -1742,7 +1746,7 @@ pm_status pm_count(pm_query_plan *p, void *stream, double timeout_s, uint64_t *c
             set_error("pm_count: deadline expired");
             return PM_ETIMEOUT;
         }
-        if (ctl.fault) return list_fault("pm_count (graph replay)");
+        if (ctl.fault) return list_fault("pm_count (graph replay)", ctl.fault);
         p->timed = true;
         if (matched) std::memcpy(matched, p->h_pinned, sizeof(uint64_t) * 2 * nm);
         (void)timeout_s;

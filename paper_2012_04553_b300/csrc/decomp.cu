@@ -33,6 +33,7 @@ namespace pm {
 
 constexpr int DC_WARPS = 8;          // warps per block of the triangle and vertex passes
 constexpr int P2_THREADS = 1024;     // threads per block of the 2-path pass
+constexpr int32_t P2_LONG = 64;      // rows longer than this: walked by a whole warp
 
 __device__ __forceinline__ int32_t deg_of(const DevGraph &g, int32_t v) {
     return int32_t(__ldg(g.rowptr + v + 1) - __ldg(g.rowptr + v));
@@ -407,39 +408,52 @@ __global__ void __launch_bounds__(P2_THREADS) paths2_kernel(DevGraph g, const in
         if (stats && tid == 0) stat += 16 + probe_bytes(da) + 4ull * uint64_t(la);
         // walk 1 (32 neighbours b per warp, one per lane, their rows below a
         // walked together)
-        for (int i0 = warp * 32; i0 < la; i0 += nwarps * 32) {
+        // neighbours per warp round: up to 32, fewer when the root has few
+        const int per = min(32, max(1, (la + nwarps - 1) / nwarps));
+        for (int i0 = warp * per; i0 < la; i0 += nwarps * per) {
             const int i = i0 + lane;
             int64_t rowb = 0;
             int32_t bl = 0;
-            if (i < la) {
+            if (lane < per && i < la) {
                 const int32_t b = __ldg(g.col + rowa + i);
                 rowb = __ldg(g.rowptr + b);
                 const int64_t db = __ldg(g.rowptr + b + 1) - rowb;
                 bl = lower_bound_dev(g.col + rowb, int32_t(db), a);
                 if (stats) stat += 2 * (16 + probe_bytes(db)) + uint64_t(bl) * (12 + 28);
             }
+            auto bump = [&](int32_t c) {
+                if (!PM_DCHECK(ctl, c >= 0 && c < g.n)) return;
+                const uint32_t old = atomicAdd(W + c, 1u);
+                c4acc += old;
+                if (old == 0) {
+                    const int q = atomicAdd(&s_nt, 1);
+                    if (PM_DCHECK(ctl, q < g.n)) touched[q] = c;
+                }
+            };
+            // long rows one at a time with all lanes, short ones together
+            for (unsigned longs = __ballot_sync(FULL, bl > P2_LONG); longs; longs &= longs - 1) {
+                const int l = __ffs(longs) - 1;
+                const int64_t orow = __shfl_sync(FULL, rowb, l);
+                const int32_t on = __shfl_sync(FULL, bl, l);
+                for (int32_t j = lane; j < on; j += 32) bump(__ldg(g.col + orow + j));
+            }
             int32_t excl;
-            const int32_t total = lanes_scan(bl, lane, excl);
+            const int32_t total = lanes_scan(bl <= P2_LONG ? bl : 0, lane, excl);
             for (int32_t e0 = 0; e0 < total; e0 += 32) {
                 const int32_t e = e0 + lane;
                 const int o = lanes_owner(excl, e);
                 const int64_t orow = __shfl_sync(FULL, rowb, o);
                 const int32_t oex = __shfl_sync(FULL, excl, o);
-                if (e < total) {
-                    const int32_t c = __ldg(g.col + orow + (e - oex));
-                    const uint32_t old = atomicAdd(W + c, 1u);
-                    c4acc += old;
-                    if (old == 0) touched[atomicAdd(&s_nt, 1)] = c;
-                }
+                if (e < total) bump(__ldg(g.col + orow + (e - oex)));
             }
         }
         __syncthreads();
         // walk 2 (same grouping)
-        for (int i0 = warp * 32; i0 < la; i0 += nwarps * 32) {
+        for (int i0 = warp * per; i0 < la; i0 += nwarps * per) {
             const int i = i0 + lane;
             int64_t rowb = 0;
             int32_t bl = 0, db = 0, tab = 0;
-            if (i < la) {
+            if (lane < per && i < la) {
                 const int32_t b = __ldg(g.col + rowa + i);
                 rowb = __ldg(g.rowptr + b);
                 db = int32_t(__ldg(g.rowptr + b + 1) - rowb);
@@ -449,8 +463,25 @@ __global__ void __launch_bounds__(P2_THREADS) paths2_kernel(DevGraph g, const in
                 corr += u128(uint64_t(bl)) * wb;
                 tm += wb;
             }
+            auto visit = [&](int64_t slot, int32_t odb, int32_t otab) {
+                const int32_t c = __ldg(g.col + slot);
+                const uint32_t w = W[c];
+                if (w > 1) {
+                    const int64_t dc = deg_of(g, c);
+                    banner += u128(w - 1) * uint64_t(2 * int64_t(odb) + da + dc - 8);
+                    house += u128(w - 1) * uint64_t(int64_t(otab) + __ldg(t + slot));
+                }
+            };
+            for (unsigned longs = __ballot_sync(FULL, bl > P2_LONG); longs; longs &= longs - 1) {
+                const int l = __ffs(longs) - 1;
+                const int64_t orow = __shfl_sync(FULL, rowb, l);
+                const int32_t on = __shfl_sync(FULL, bl, l);
+                const int32_t odb = __shfl_sync(FULL, db, l);
+                const int32_t otab = __shfl_sync(FULL, tab, l);
+                for (int32_t j = lane; j < on; j += 32) visit(orow + j, odb, otab);
+            }
             int32_t excl;
-            const int32_t total = lanes_scan(bl, lane, excl);
+            const int32_t total = lanes_scan(bl <= P2_LONG ? bl : 0, lane, excl);
             for (int32_t e0 = 0; e0 < total; e0 += 32) {
                 const int32_t e = e0 + lane;
                 const int o = lanes_owner(excl, e);
@@ -458,27 +489,19 @@ __global__ void __launch_bounds__(P2_THREADS) paths2_kernel(DevGraph g, const in
                 const int32_t oex = __shfl_sync(FULL, excl, o);
                 const int32_t odb = __shfl_sync(FULL, db, o);
                 const int32_t otab = __shfl_sync(FULL, tab, o);
-                if (e < total) {
-                    const int64_t slot = orow + (e - oex);
-                    const int32_t c = __ldg(g.col + slot);
-                    const uint32_t w = W[c];
-                    if (w > 1) {
-                        const int64_t dc = deg_of(g, c);
-                        banner += u128(w - 1) * uint64_t(2 * int64_t(odb) + da + dc - 8);
-                        house += u128(w - 1) * uint64_t(int64_t(otab) + __ldg(t + slot));
-                    }
-                }
+                if (e < total) visit(orow + (e - oex), odb, otab);
             }
         }
         // touched vertices (32 per warp; for 5-cycles their rows below them
         // walked together)
         const int nt = s_nt;
-        for (int q0 = warp * 32; q0 < nt; q0 += nwarps * 32) {
+        const int per_t = min(32, max(1, (nt + nwarps - 1) / nwarps));
+        for (int q0 = warp * per_t; q0 < nt; q0 += nwarps * per_t) {
             const int q = q0 + lane;
             int32_t c = 0, lc = 0;
             uint32_t w = 0;
             int64_t rowc = 0;
-            if (q < nt) {
+            if (lane < per_t && q < nt) {
                 c = touched[q];
                 w = W[c];
                 k23 += c3(w);
@@ -491,8 +514,17 @@ __global__ void __launch_bounds__(P2_THREADS) paths2_kernel(DevGraph g, const in
                 }
             }
             if (!with_c5) continue;
+            for (unsigned longs = __ballot_sync(FULL, lc > P2_LONG); longs; longs &= longs - 1) {
+                const int l = __ffs(longs) - 1;
+                const int64_t orow = __shfl_sync(FULL, rowc, l);
+                const int32_t on = __shfl_sync(FULL, lc, l);
+                const uint32_t ow = __shfl_sync(FULL, w, l);
+                uint64_t sum = 0;
+                for (int32_t j = lane; j < on; j += 32) sum += W[__ldg(g.col + orow + j)];
+                qh += u128(ow) * sum;
+            }
             int32_t excl;
-            const int32_t total = lanes_scan(lc, lane, excl);
+            const int32_t total = lanes_scan(lc <= P2_LONG ? lc : 0, lane, excl);
             for (int32_t e0 = 0; e0 < total; e0 += 32) {
                 const int32_t e = e0 + lane;
                 const int o = lanes_owner(excl, e);

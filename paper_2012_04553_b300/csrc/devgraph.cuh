@@ -43,6 +43,16 @@ __device__ __forceinline__ bool contains(const DevGraph &g, int32_t v, int32_t x
     return p < len && __ldg(a + p) == x;
 }
 
+// Bounds checks of the PM_DEBUG build: an index derived from data must
+// satisfy `cond` for the access that follows; otherwise the control block's
+// fault word becomes 2 (reported by the host as an error) and the caller
+// skips the access.  Without PM_DEBUG the check compiles to `true`.
+#ifdef PM_DEBUG
+#define PM_DCHECK(ctl, cond) ((cond) ? true : (atomicExch(&(ctl)->fault, 2), false))
+#else
+#define PM_DCHECK(ctl, cond) true
+#endif
+
 __device__ __forceinline__ void add_u128(uint64_t *counter, u128 v) {
     const unsigned long long lo = (unsigned long long)(uint64_t)v;
     unsigned long long hi = (unsigned long long)(uint64_t)(v >> 64);

@@ -195,6 +195,7 @@ struct WheelArgs {
     const int32_t *t;         // triangles per CSR slot (both endpoints' rows)
     int64_t *toff;            // nnz + 1 list offsets (exclusive scan of t)
     int32_t *T;               // common-neighbour lists, positions in the slot's own row
+    int64_t T_len;            // entries allocated for T (bounds checks of the PM_DEBUG build)
     int64_t *bsum;            // scan scratch: one word per 8192 slots
     int32_t *hub_rank;        // popcount rank index of the hub bitmaps, or nullptr
     int64_t n_hubs;

@@ -64,7 +64,6 @@ constexpr int K5E_WARP_WORDS = 1024;               // 2048 16-bit counters per w
 constexpr int K23_WARP_CAP = 2048;                 // walk-B window of a warp item (positions)
 constexpr int K23_SMEM_WORDS = 32768;              // 128 KB: 32 warps x 1024 words, or one block window
 constexpr int K23_BIG_A = 4096;                    // walk-A rows longer than this: block items
-constexpr int K23_BIG_NY = 64;                     // walk-B neighbours with more y's: block items
 constexpr int K23_BIG_CAP = 2048;                  // block items per root (the rest stay warp items)
 
 __device__ __forceinline__ u128 w_c2(uint64_t x) { return x >= 2 ? u128(x) * (x - 1) / 2 : 0; }
@@ -111,16 +110,36 @@ __device__ __forceinline__ int32_t row_of_slot(const int64_t *rowptr, int64_t s,
     return int32_t(lo);
 }
 
-// Warp walk over up to 32 lists at once: lane l holds a list of cnt_l
-// entries starting at T[base_l]; the warp visits all of them with every lane
-// busy (entry e of the concatenation goes to lane e mod 32; its list is
-// found by a binary search over the lanes' exclusive prefix sums), calling
-// f(value) for each entry.  Short lists (the common case: the common
-// neighbours of a hub and a low-degree vertex) then cost no idle lanes and
-// many loads are in flight at once.
-template <class F>
-__device__ __forceinline__ void warp_lists(const int32_t *__restrict__ T, int64_t base, int32_t cnt, int lane,
-                                           F f) {
+// Warp walk over up to 32 sorted lists at once, lane l holding
+// T[base_l .. base_l + len_l), calling f(value) for each entry (with CUT,
+// only for the entries below `bound`, the same for all lanes).  Lists
+// longer than WL_LONG are walked one at a time by the whole warp (lanes
+// stride over the entries, with CUT stopping at the first entry >= bound);
+// the short ones (the common case: the common neighbours of a hub and a
+// low-degree vertex) are cut by a binary search and then walked together,
+// entry e of their concatenation going to lane e mod 32 (its list found by
+// a binary search over the lanes' exclusive prefix sums), so short lists
+// leave no lane idle and many loads are in flight at once.
+constexpr int32_t WL_LONG = 64;
+
+template <bool CUT, class F>
+__device__ __forceinline__ void warp_lists(const int32_t *__restrict__ T, int64_t base, int32_t len,
+                                           int32_t bound, int lane, Control *ctl, int64_t limit, F f) {
+    unsigned longs = __ballot_sync(FULL, len > WL_LONG);
+    while (longs) {
+        const int l = __ffs(longs) - 1;
+        longs &= longs - 1;
+        const int64_t ob = __shfl_sync(FULL, base, l);
+        const int32_t on = __shfl_sync(FULL, len, l);
+        for (int32_t j = lane; j < on; j += 32) {
+            if (!PM_DCHECK(ctl, ob + j < limit)) break;
+            const int32_t v = __ldg(T + ob + j);
+            if (CUT && v >= bound) break;
+            f(v);
+        }
+    }
+    int32_t cnt = 0;
+    if (len > 0 && len <= WL_LONG) cnt = CUT ? lower_bound_dev(T + base, len, bound) : len;
     int32_t incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -139,7 +158,7 @@ __device__ __forceinline__ void warp_lists(const int32_t *__restrict__ T, int64_
         }
         const int64_t ob = __shfl_sync(FULL, base, lo);
         const int32_t oex = __shfl_sync(FULL, excl, lo);
-        if (e < total) f(__ldg(T + ob + (e - oex)));
+        if (e < total && PM_DCHECK(ctl, ob + (e - oex) < limit)) f(__ldg(T + ob + (e - oex)));
     }
 }
 
@@ -288,7 +307,7 @@ __global__ void __launch_bounds__(TL_WARPS * 32) tlist_kernel(WheelArgs A) {
                     }
                     const unsigned m = __ballot_sync(FULL, found);
                     const int32_t k = written + __popc(m & lt);
-                    if (found && k < ts) out[k] = pos;
+                    if (found && k < ts && PM_DCHECK(A.ctl, out + k < A.T + A.T_len)) out[k] = pos;
                     written += __popc(m);
                     if (A.stats) stat += (j < du ? 4 : 0) + (j < du ? (hv >= 0 ? 8 : w_probe_bytes(dv)) : 0);
                 }
@@ -299,7 +318,7 @@ __global__ void __launch_bounds__(TL_WARPS * 32) tlist_kernel(WheelArgs A) {
                     const bool found = p < dv && contains(g, u, __ldg(g.col + rowv + p));
                     const unsigned m = __ballot_sync(FULL, found);
                     const int32_t k = written + __popc(m & lt);
-                    if (found && k < ts) out[k] = p;
+                    if (found && k < ts && PM_DCHECK(A.ctl, out + k < A.T + A.T_len)) out[k] = p;
                     written += __popc(m);
                     if (A.stats && p < dv) stat += 4 + (g.hub && __ldg(g.hub + u) >= 0 ? 4 : w_probe_bytes(du));
                 }
@@ -332,18 +351,22 @@ template <bool SMEM, int STRIDE>
 __device__ __forceinline__ uint64_t w4_walk(const WheelArgs &A, uint32_t *cnt, int64_t rowc,
                                             const int32_t *X, int32_t nx, int32_t pa, int first, int lane) {
     uint64_t stat = 0;
-    for (int32_t k0 = first * 32; k0 < nx; k0 += STRIDE * 32) {
+    // x's per warp round: up to 32 (one per lane), fewer when there are
+    // few, so every warp of the stride gets some
+    const int32_t per = min(32, max(1, (nx + STRIDE - 1) / STRIDE));
+    for (int32_t k0 = first * per; k0 < nx; k0 += STRIDE * per) {
         const int32_t k = k0 + lane;
         int64_t b0 = 0;
-        int32_t cut = 0;
-        if (k < nx) {
+        int32_t len = 0;
+        if (lane < per && k < nx) {
             const int64_t sx = rowc + __ldg(X + k);
             b0 = __ldg(A.toff + sx);
-            const int32_t len = int32_t(__ldg(A.toff + sx + 1) - b0);
-            cut = lower_bound_dev(A.T + b0, len, pa);
-            if (A.stats) stat += 16 + w_probe_bytes(len) + 4ull * uint64_t(cut);
+            len = int32_t(__ldg(A.toff + sx + 1) - b0);
+            if (A.stats) stat += 16 + 4ull * uint64_t(len);
         }
-        warp_lists(A.T, b0, cut, lane, [&](int32_t pb) { w4_bump<SMEM>(cnt, pb); });
+        warp_lists<true>(A.T, b0, len, pa, lane, A.ctl, A.T_len, [&](int32_t pb) {
+            if (PM_DCHECK(A.ctl, SMEM ? (pb >> 1) < W4_SMEM_WORDS : pb < A.gcnt_words)) w4_bump<SMEM>(cnt, pb);
+        });
     }
     return stat;
 }
@@ -512,9 +535,13 @@ __device__ __forceinline__ u128 w_c3(uint64_t x) { return x >= 3 ? u128(x) * (x 
 constexpr int K23_W_BITS = 24;
 constexpr unsigned long long K23_W_MASK = (1ull << K23_W_BITS) - 1;
 
-__device__ __forceinline__ void k23_bump(unsigned long long *V, int32_t *touched, int *s_nt, int32_t b,
-                                         unsigned long long add) {
-    if (atomicAdd(V + b, add) == 0) touched[atomicAdd(s_nt, 1)] = b;
+__device__ __forceinline__ void k23_bump(const WheelArgs &A, unsigned long long *V, int32_t *touched, int *s_nt,
+                                         int32_t b, unsigned long long add) {
+    if (!PM_DCHECK(A.ctl, b >= 0 && b < A.g.n)) return;
+    if (atomicAdd(V + b, add) == 0) {
+        const int q = atomicAdd(s_nt, 1);
+        if (PM_DCHECK(A.ctl, q < A.g.n)) touched[q] = b;
+    }
 }
 
 // Walk B of one neighbour x of root a (a at position mx of x's row): for
@@ -529,20 +556,23 @@ __device__ __forceinline__ uint64_t k23_walk_b(const WheelArgs &A, unsigned long
                                                int32_t k0, int32_t ny, int32_t mx, int first, int lane) {
     uint64_t stat = 0;
     // groups of 32 y's, one per lane; each lane cuts its T_(x,y) at mx
-    for (int32_t g0 = k0 + first * 32; g0 < ny; g0 += STRIDE * 32) {
+    const int32_t per = min(32, max(1, (ny - k0 + STRIDE - 1) / STRIDE));
+    for (int32_t g0 = k0 + first * per; g0 < ny; g0 += STRIDE * per) {
         const int32_t k = g0 + lane;
         int64_t b0 = 0;
-        int32_t cut = 0;
-        if (k < ny) {
+        int32_t nb = 0;
+        if (lane < per && k < ny) {
             const int64_t sy = rowx + __ldg(Y + k);
             b0 = __ldg(A.toff + sy);
-            const int32_t nb = int32_t(__ldg(A.toff + sy + 1) - b0);
-            cut = lower_bound_dev(A.T + b0, nb, mx);
-            if (A.stats) stat += 4 + 16 + w_probe_bytes(nb) + 4ull * uint64_t(cut);
+            nb = int32_t(__ldg(A.toff + sy + 1) - b0);
+            if (A.stats) stat += 4 + 16 + 4ull * uint64_t(nb);
         }
-        warp_lists(A.T, b0, cut, lane, [&](int32_t pb) {
-            if (cnt) atomicAdd(cnt + (pb >> 1), (pb & 1) ? 65536u : 1u);
-            else k23_bump(V, touched, s_nt, __ldg(A.g.col + rowx + pb), 1ull << K23_W_BITS);
+        warp_lists<true>(A.T, b0, nb, mx, lane, A.ctl, A.T_len, [&](int32_t pb) {
+            if (cnt) {
+                if (PM_DCHECK(A.ctl, (pb >> 1) < K23_SMEM_WORDS)) atomicAdd(cnt + (pb >> 1), (pb & 1) ? 65536u : 1u);
+            } else {
+                k23_bump(A, V, touched, s_nt, __ldg(A.g.col + rowx + pb), 1ull << K23_W_BITS);
+            }
         });
     }
     return stat;
@@ -558,10 +588,10 @@ __device__ __forceinline__ uint64_t k23_flush(const WheelArgs &A, unsigned long 
         const uint32_t v = cnt[w];
         if (!v) continue;
         if (v & 0xffffu)
-            k23_bump(V, touched, s_nt, __ldg(A.g.col + rowx + 2 * w),
+            k23_bump(A, V, touched, s_nt, __ldg(A.g.col + rowx + 2 * w),
                      (unsigned long long)(v & 0xffffu) << K23_W_BITS);
         if (v >> 16)
-            k23_bump(V, touched, s_nt, __ldg(A.g.col + rowx + 2 * w + 1),
+            k23_bump(A, V, touched, s_nt, __ldg(A.g.col + rowx + 2 * w + 1),
                      (unsigned long long)(v >> 16) << K23_W_BITS);
         cnt[w] = 0;
         if (A.stats) stat += 4 * (((v & 0xffffu) != 0) + ((v >> 16) != 0)) + 8;
@@ -575,9 +605,9 @@ __device__ __forceinline__ uint64_t k23_flush(const WheelArgs &A, unsigned long 
 // neighbour w, lanes over w's row below a) and walk B (a warp per
 // neighbour x whose window, a's position in x's row, fits the warp's own
 // 2048 16-bit counters).  Neighbours with long rows (walk A, more than
-// K23_BIG_A entries) or many y's or a wide window (walk B) go to a shared
-// list that the whole block then takes one at a time (walk B with 65,536
-// counters in shared memory), so one root's work is spread over its warps.
+// K23_BIG_A entries) or a wide window (walk B) go to a shared list that the
+// whole block then takes one at a time (walk B with 65,536 counters in
+// shared memory).
 __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
     extern __shared__ uint32_t sc[];
     __shared__ unsigned long long s_root;
@@ -613,15 +643,16 @@ __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
         const int32_t da = int32_t(__ldg(g.rowptr + a + 1) - rowa);
         // walk A: 2-paths a-w-b, b < a (the entries of w's row before a),
         // 32 neighbours w per warp (one per lane) walked together
+        const int32_t per_a = min(32, max(1, (da + K23_THREADS / 32 - 1) / (K23_THREADS / 32)));
         for (;;) {
             int32_t i0 = 0;
-            if (lane == 0) i0 = atomicAdd(&s_next[0], 32);
+            if (lane == 0) i0 = atomicAdd(&s_next[0], per_a);
             i0 = __shfl_sync(FULL, i0, 0);
             if (i0 >= da) break;
             const int32_t i = i0 + lane;
             int64_t base = 0;
             int32_t cnt = 0;
-            if (i < da) {
+            if (lane < per_a && i < da) {
                 const int32_t m = __ldg(A.mpos + rowa + i);
                 bool big = false;
                 if (m > K23_BIG_A) {
@@ -637,7 +668,8 @@ __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
                     if (A.stats) stat += 4 + 4 + 16 + 16ull * uint64_t(m);
                 }
             }
-            warp_lists(g.col, base, cnt, lane, [&](int32_t b) { k23_bump(V, touched, &s_nt, b, 1ull); });
+            warp_lists<false>(g.col, base, cnt, 0, lane, ctl, g.nnz,
+                              [&](int32_t b) { k23_bump(A, V, touched, &s_nt, b, 1ull); });
         }
         // walk B, warp items: edges x < y of G_a, tips b < a in T_(x,y)
         for (;;) {
@@ -657,7 +689,7 @@ __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
             const int32_t k0 = lower_bound_dev(A.T + y0, ny, lox);
             if (A.stats && lane == 0) stat += 8 + w_probe_bytes(dx) + w_probe_bytes(ny);
             if (k0 >= ny) continue;
-            if (mx > K23_WARP_CAP || ny - k0 > K23_BIG_NY) {
+            if (mx > K23_WARP_CAP) {
                 int slot = K23_BIG_CAP;
                 if (lane == 0) slot = atomicAdd(&s_nbig, 1);
                 slot = __shfl_sync(FULL, slot, 0);
@@ -683,7 +715,8 @@ __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
             if (item >= 0) {                                        // walk A
                 const int32_t m = __ldg(A.mpos + rowa + i);
                 const int64_t roww = __ldg(g.rowptr + __ldg(g.col + rowa + i));
-                for (int32_t j = tid; j < m; j += K23_THREADS) k23_bump(V, touched, &s_nt, __ldg(g.col + roww + j), 1ull);
+                for (int32_t j = tid; j < m; j += K23_THREADS)
+                    k23_bump(A, V, touched, &s_nt, __ldg(g.col + roww + j), 1ull);
                 if (A.stats && tid == 0) stat += 4 + 4 + 16 + 16ull * uint64_t(m);
                 continue;                                           // no barrier needed
             }
@@ -802,8 +835,9 @@ __global__ void __launch_bounds__(K5E_THREADS) k5e_kernel(WheelArgs A) {
                     cnt = nw - j0;
                     if (A.stats) stat += 4 + 16 + w_probe_bytes(nw) + 4ull * uint64_t(cnt);
                 }
-                warp_lists(A.T, base, cnt, lane, [&](int32_t pz) {
+                warp_lists<false>(A.T, base, cnt, 0, lane, ctl, A.T_len, [&](int32_t pz) {
                     const int32_t z = pz - py - 1;
+                    if (!PM_DCHECK(ctl, z >= 0 && z < range)) return;
                     if (smem) atomicAdd(wc + (z >> 1), (z & 1) ? 65536u : 1u);
                     else atomicAdd(gc + z, 1u);
                 });

@@ -227,3 +227,33 @@ def test_wheel_global_counters_above_65536_positions():
     assert g.info()["max_degree"] == n - 1
     got = wheel_vs_plans(g, [495], families=(pm.PLANS_FREE,))
     assert got[0] > 0
+
+
+def test_bounds_checked_build_agrees_with_the_oracle():
+    """The PM_DEBUG library (every data-derived index checked before its
+    access, a failed check reported as an error) counts the hub graph's
+    decomposed patterns, the neighbourhood-graph ones included, exactly as
+    the oracle, in a child process that loads it."""
+    import json
+    import os
+    import subprocess
+    import sys
+    n, s, d = hub_graph()
+    og = oracle.prepare_graph(n, s, d)
+    masks5 = [220, 221] + WHEEL5
+    want = [oracle.count(og, algebra.Pattern.from_mask(5, m)) for m in masks5]
+    code = (
+        "import json, numpy as np, paper_2012_04553_b300 as pm\n"
+        "from tests.test_gpu_decomp import hub_graph\n"
+        "assert pm.LIB_PATH.endswith('libpm_b300_debug.so')\n"
+        "n, s, d = hub_graph()\n"
+        "g = pm.Graph(n, s, d)\n"
+        f"qs = [pm.make_pattern(5, m, pm.EDGE_INDUCED) for m in {masks5!r}]\n"
+        "print(json.dumps([str(c) for c in pm.Plan(g, qs, mode=pm.MORPH_NONE).count()]))\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PM_DEBUG="1", PYTHONPATH=root)
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
+                         timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    got = [int(x) for x in json.loads(out.stdout.strip().splitlines()[-1])]
+    assert got == want

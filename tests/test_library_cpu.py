@@ -233,3 +233,19 @@ def test_host_fault_injection(monkeypatch):
     assert e.value.status == pm.PM_EINVAL and "fault injected" in str(e.value)
     monkeypatch.delenv("PM_FAULT")
     assert pm.Plan(None, [pm.make_pattern(3, 0b111)]).n_matched == 1
+
+
+def test_debug_build_exports_the_same_symbols():
+    """The PM_DEBUG (bounds-checked) library builds for sm_103a and exports
+    the same C ABI as the release library."""
+    import runpy
+    import subprocess
+    here = os.path.dirname(os.path.abspath(pm.__file__))
+    mod = runpy.run_path(os.path.join(here, "build.py"))
+    rel, dbg = mod["build"](), mod["build"](debug=True)
+
+    def exported(path):
+        out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+        return {line.split()[-1] for line in out.splitlines() if line.split()[-1].startswith("pm_")}
+    assert exported(dbg) == exported(rel)
+    assert set(pm.ABI_SYMBOLS) <= exported(dbg)
