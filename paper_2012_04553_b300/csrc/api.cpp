@@ -172,9 +172,10 @@ struct pm_query_plan {
         int32_t *rank = nullptr;
         int32_t *mpos = nullptr;
         uint32_t *gcnt = nullptr;
-        unsigned long long *kV = nullptr;
+        uint32_t *kW = nullptr;
+        unsigned long long *kE = nullptr;
         int32_t *ktouched = nullptr;
-        size_t b_toff = 0, b_T = 0, b_bsum = 0, b_rank = 0, b_mpos = 0, b_gcnt = 0, b_kV = 0, b_kt = 0;
+        size_t b_toff = 0, b_T = 0, b_bsum = 0, b_rank = 0, b_mpos = 0, b_gcnt = 0, b_kW = 0, b_kE = 0;
         int64_t gcnt_words = 0;
         int w4_blocks = 0, k23_blocks = 0;
         uint32_t *k5g = nullptr;
@@ -207,8 +208,9 @@ void free_wheel(pm_query_plan *p, int dev) {
     dev_free(w.rank, w.b_rank, dev);
     dev_free(w.mpos, w.b_mpos, dev);
     dev_free(w.gcnt, w.b_gcnt, dev);
-    dev_free(w.kV, w.b_kV, dev);
-    dev_free(w.ktouched, w.b_kt, dev);
+    dev_free(w.kW, w.b_kW, dev);
+    dev_free(w.kE, w.b_kE, dev);
+    dev_free(w.ktouched, w.b_kW, dev);
     dev_free(w.k5g, w.b_k5g, dev);
     p->wh = {};
 }
@@ -643,25 +645,23 @@ pm_status ensure_decomp(pm_query_plan *p, cudaStream_t s) {
         w.T = (int32_t *)dev_alloc(w.b_T, g->device);
         if (!w.T) return fail("common-neighbour lists");
     }
-    if ((passes & DP_K23E) && !p->wh.kV) {
-        if (g->max_degree > k23_max_degree()) {
-            set_error("K2,3 counts: the largest degree exceeds the packed counters' range");
-            return PM_EUNSUPPORTED;
-        }
+    if ((passes & DP_K23E) && !p->wh.kW) {
         auto &w = p->wh;
         w.k23_blocks = k23_blocks(g->device);
         w.b_mpos = sizeof(int32_t) * size_t(std::max<int64_t>(2 * g->m, 1));
-        w.b_kV = sizeof(unsigned long long) * size_t(g->n) * size_t(w.k23_blocks);
-        w.b_kt = sizeof(int32_t) * size_t(g->n) * size_t(w.k23_blocks);
+        w.b_kW = sizeof(uint32_t) * size_t(g->n) * size_t(w.k23_blocks);
+        w.b_kE = sizeof(unsigned long long) * size_t(g->n) * size_t(w.k23_blocks);
         w.mpos = (int32_t *)dev_alloc(w.b_mpos, g->device);
-        w.kV = (unsigned long long *)dev_alloc(w.b_kV, g->device);
-        w.ktouched = (int32_t *)dev_alloc(w.b_kt, g->device);
-        if (!w.mpos || !w.kV || !w.ktouched) {
+        w.kW = (uint32_t *)dev_alloc(w.b_kW, g->device);
+        w.kE = (unsigned long long *)dev_alloc(w.b_kE, g->device);
+        w.ktouched = (int32_t *)dev_alloc(w.b_kW, g->device);
+        if (!w.mpos || !w.kW || !w.kE || !w.ktouched) {
             free_wheel(p, g->device);
             set_error("device allocation failed (K2,3 root counters)");
             return PM_ENOMEM;
         }
-        cudaError_t e = cudaMemsetAsync(w.kV, 0, w.b_kV, s);
+        cudaError_t e = cudaMemsetAsync(w.kW, 0, w.b_kW, s);
+        if (!e) e = cudaMemsetAsync(w.kE, 0, w.b_kE, s);
         if (e) return cuda_fail("K2,3 root counters", e);
     }
     if ((passes & DP_K5E) && !p->wh.k5e_blocks) {
@@ -904,7 +904,8 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
         D.wheel.gcnt = p->wh.gcnt;
         D.wheel.gcnt_words = p->wh.gcnt_words;
         D.wheel.w4_blocks = p->wh.w4_blocks;
-        D.wheel.kV = p->wh.kV;
+        D.wheel.kW = p->wh.kW;
+        D.wheel.kE = p->wh.kE;
         D.wheel.ktouched = p->wh.ktouched;
         D.wheel.k23_blocks = p->wh.k23_blocks;
         D.wheel.k5g = p->wh.k5g;
@@ -936,7 +937,8 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
 void rezero_wedge(pm_query_plan *p, cudaStream_t s) {
     if (p->d_wedge) cudaMemsetAsync(p->d_wedge, 0, p->bytes_wedge, s);
     if (p->d_dW) cudaMemsetAsync(p->d_dW, 0, p->bytes_dW, s);
-    if (p->wh.kV) cudaMemsetAsync(p->wh.kV, 0, p->wh.b_kV, s);
+    if (p->wh.kW) cudaMemsetAsync(p->wh.kW, 0, p->wh.b_kW, s);
+    if (p->wh.kE) cudaMemsetAsync(p->wh.kE, 0, p->wh.b_kE, s);
     if (p->wh.k5g) cudaMemsetAsync(p->wh.k5g, 0, p->wh.b_k5g, s);
 }
 

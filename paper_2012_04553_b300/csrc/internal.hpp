@@ -203,7 +203,8 @@ struct WheelArgs {
     uint32_t *gcnt;           // DP_W4: per block 32-bit counters above 65536 positions, or nullptr
     int64_t gcnt_words;
     int w4_blocks;
-    unsigned long long *kV;   // DP_K23E: per block n counter words (2-path and diamond counts; zero between roots)
+    uint32_t *kW;             // DP_K23E: per block n 2-path counters (zero on entry and exit)
+    unsigned long long *kE;   // per block n diamond counters (zero on entry and exit)
     int32_t *ktouched;        // per block n touched vertices
     int k23_blocks;
     uint32_t *k5g;            // DP_K5E: per warp 32-bit counters above 2048 positions, or nullptr
@@ -216,7 +217,6 @@ struct WheelArgs {
 size_t w4_smem_bytes();
 int w4_blocks(int device);
 int k23_blocks(int device);
-int64_t k23_max_degree();     // largest degree whose counts fit the packed counter words
 int k5e_blocks(int device);
 int64_t k5e_global_words(int64_t max_updeg, int64_t max_degree);
 int64_t w4_global_words(int64_t max_degree);

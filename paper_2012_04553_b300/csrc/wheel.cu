@@ -63,8 +63,6 @@ constexpr int K5E_THREADS = 512;
 constexpr int K5E_WARP_WORDS = 1024;               // 2048 16-bit counters per warp (64 KB per block)
 constexpr int K23_WARP_CAP = 2048;                 // walk-B window of a warp item (positions)
 constexpr int K23_SMEM_WORDS = 32768;              // 128 KB: 32 warps x 1024 words, or one block window
-constexpr int K23_BIG_A = 4096;                    // walk-A rows longer than this: block items
-constexpr int K23_BIG_CAP = 2048;                  // block items per root (the rest stay warp items)
 
 __device__ __forceinline__ u128 w_c2(uint64_t x) { return x >= 2 ? u128(x) * (x - 1) / 2 : 0; }
 
@@ -344,29 +342,24 @@ __device__ __forceinline__ void w4_bump(uint32_t *cnt, int32_t pb) {
     else atomicAdd(cnt + pb, 1u);
 }
 
-// Walk of the x below p_a of one task (entries k = first, first + STRIDE,
-// ... of X in groups of 32, one per lane): each lane cuts its T_(c,x) at p_a
-// (binary search) and the warp walks the 32 prefixes together.
-template <bool SMEM, int STRIDE>
-__device__ __forceinline__ uint64_t w4_walk(const WheelArgs &A, uint32_t *cnt, int64_t rowc,
-                                            const int32_t *X, int32_t nx, int32_t pa, int first, int lane) {
+// Walk of one block task: warps over the x below p_a, lanes over T_(c,x).
+template <bool SMEM>
+__device__ __forceinline__ uint64_t w4_block_walk(const WheelArgs &A, uint32_t *cnt, int64_t rowc,
+                                                  const int32_t *X, int32_t nx, int32_t pa,
+                                                  int warp, int lane) {
     uint64_t stat = 0;
-    // x's per warp round: up to 32 (one per lane), fewer when there are
-    // few, so every warp of the stride gets some
-    const int32_t per = min(32, max(1, (nx + STRIDE - 1) / STRIDE));
-    for (int32_t k0 = first * per; k0 < nx; k0 += STRIDE * per) {
-        const int32_t k = k0 + lane;
-        int64_t b0 = 0;
-        int32_t len = 0;
-        if (lane < per && k < nx) {
-            const int64_t sx = rowc + __ldg(X + k);
-            b0 = __ldg(A.toff + sx);
-            len = int32_t(__ldg(A.toff + sx + 1) - b0);
-            if (A.stats) stat += 16 + 4ull * uint64_t(len);
-        }
-        warp_lists<true>(A.T, b0, len, pa, lane, A.ctl, A.T_len, [&](int32_t pb) {
+    for (int32_t k = warp; k < nx; k += W4_WARPS) {
+        const int64_t sx = rowc + __ldg(X + k);
+        const int64_t b0 = __ldg(A.toff + sx);
+        const int32_t len = int32_t(__ldg(A.toff + sx + 1) - b0);
+        const int32_t *B = A.T + b0;
+        for (int32_t j = lane; j < len; j += 32) {
+            const int32_t pb = __ldg(B + j);
+            if (A.stats) stat += 4;
+            if (pb >= pa) break;
             if (PM_DCHECK(A.ctl, SMEM ? (pb >> 1) < W4_SMEM_WORDS : pb < A.gcnt_words)) w4_bump<SMEM>(cnt, pb);
-        });
+        }
+        if (A.stats && lane == 0) stat += 16;
     }
     return stat;
 }
@@ -423,8 +416,8 @@ __global__ void __launch_bounds__(W4_THREADS, 1) w4_kernel(WheelArgs A) {
             const int32_t nx = lower_bound_dev(X, ts, pa);
             if (nx < 2) continue;
             const bool smem = pa <= W4_BLOCK_CAP;
-            if (smem) stat += w4_walk<true, W4_WARPS>(A, sc, rowc, X, nx, pa, warp, lane);
-            else if (gcnt) stat += w4_walk<false, W4_WARPS>(A, gcnt, rowc, X, nx, pa, warp, lane);
+            if (smem) stat += w4_block_walk<true>(A, sc, rowc, X, nx, pa, warp, lane);
+            else if (gcnt) stat += w4_block_walk<false>(A, gcnt, rowc, X, nx, pa, warp, lane);
             __syncthreads();
             if (smem) {
                 for (int32_t w = tid; w < (pa + 1) / 2; w += W4_THREADS) {
@@ -480,7 +473,18 @@ __global__ void __launch_bounds__(W4_THREADS, 1) w4_kernel(WheelArgs A) {
                 if (m != FULL) break;
             }
             if (nx < 2) continue;
-            stat += w4_walk<true, 1>(A, wc, rowc, X, nx, pa, 0, lane);
+            for (int32_t k = 0; k < nx; k++) {
+                const int64_t sx = rowc + __ldg(X + k);
+                const int64_t b0 = __ldg(A.toff + sx);
+                const int32_t len = int32_t(__ldg(A.toff + sx + 1) - b0);
+                const int32_t *B = A.T + b0;
+                for (int32_t j = lane; j < len; j += 32) {
+                    const int32_t pb = __ldg(B + j);
+                    if (pb >= pa) break;
+                    if (PM_DCHECK(ctl, (pb >> 1) < W4_WARP_CAP / 2)) atomicAdd(wc + (pb >> 1), (pb & 1) ? 65536u : 1u);
+                }
+                if (A.stats && lane == 0) stat += 16 + 4ull * uint64_t(len);
+            }
             __syncwarp();
             for (int32_t w = lane; w < (pa + 1) / 2; w += 32) {
                 const uint32_t v = wc[w];
@@ -528,71 +532,47 @@ __global__ void __launch_bounds__(TL_WARPS * 32) mpos_kernel(WheelArgs A) {
 
 __device__ __forceinline__ u128 w_c3(uint64_t x) { return x >= 3 ? u128(x) * (x - 1) * (x - 2) / 6 : 0; }
 
-// Per-root counters of the K2,3 pass: one 64-bit word per vertex b, the
-// 2-path count c_ab in the low K23_W_BITS bits and the diamond count e_ab
-// above them (the host admits graphs whose largest degree keeps both in
-// range), so a root's two counts of b share one word and one atomic.
-constexpr int K23_W_BITS = 24;
-constexpr unsigned long long K23_W_MASK = (1ull << K23_W_BITS) - 1;
-
-__device__ __forceinline__ void k23_bump(const WheelArgs &A, unsigned long long *V, int32_t *touched, int *s_nt,
-                                         int32_t b, unsigned long long add) {
-    if (!PM_DCHECK(A.ctl, b >= 0 && b < A.g.n)) return;
-    if (atomicAdd(V + b, add) == 0) {
-        const int q = atomicAdd(s_nt, 1);
-        if (PM_DCHECK(A.ctl, q < A.g.n)) touched[q] = b;
-    }
-}
-
 // Walk B of one neighbour x of root a (a at position mx of x's row): for
-// each y > x in T_(x,a) (entries k0.. of the list Y), +1 at the positions of
-// T_(x,y) below mx.  With CNT != nullptr the counts go to 16-bit counters
-// over x's positions (packed two to a word; a count never exceeds the
-// number of y's, <= 65535 here) and are added to the root's words once per
-// position afterwards; otherwise straight to the words.
+// each y > x in T_(x,a), +1 at the positions of T_(x,y) below mx.  With
+// CNT != nullptr the counts go to 16-bit counters over x's positions
+// (packed two to a word; a count never exceeds |T_(x,a)| <= 65535 here) and
+// are added to E once per position afterwards; otherwise straight to E.
 template <int STRIDE>
-__device__ __forceinline__ uint64_t k23_walk_b(const WheelArgs &A, unsigned long long *V, int32_t *touched,
-                                               int *s_nt, uint32_t *cnt, int64_t rowx, const int32_t *Y,
-                                               int32_t k0, int32_t ny, int32_t mx, int first, int lane) {
+__device__ __forceinline__ uint64_t k23_walk_b(const WheelArgs &A, unsigned long long *E, uint32_t *cnt,
+                                               int64_t rowx, const int32_t *Y, int32_t k0, int32_t ny,
+                                               int32_t mx, int first, int lane) {
     uint64_t stat = 0;
-    // groups of 32 y's, one per lane; each lane cuts its T_(x,y) at mx
-    const int32_t per = min(32, max(1, (ny - k0 + STRIDE - 1) / STRIDE));
-    for (int32_t g0 = k0 + first * per; g0 < ny; g0 += STRIDE * per) {
-        const int32_t k = g0 + lane;
-        int64_t b0 = 0;
-        int32_t nb = 0;
-        if (lane < per && k < ny) {
-            const int64_t sy = rowx + __ldg(Y + k);
-            b0 = __ldg(A.toff + sy);
-            nb = int32_t(__ldg(A.toff + sy + 1) - b0);
-            if (A.stats) stat += 4 + 16 + 4ull * uint64_t(nb);
-        }
-        warp_lists<true>(A.T, b0, nb, mx, lane, A.ctl, A.T_len, [&](int32_t pb) {
+    for (int32_t k = k0 + first; k < ny; k += STRIDE) {
+        const int64_t sy = rowx + __ldg(Y + k);
+        const int64_t b0 = __ldg(A.toff + sy);
+        const int32_t nb = int32_t(__ldg(A.toff + sy + 1) - b0);
+        for (int32_t j = lane; j < nb; j += 32) {
+            const int32_t pb = __ldg(A.T + b0 + j);
+            if (A.stats) stat += 4;
+            if (pb >= mx) break;
             if (cnt) {
                 if (PM_DCHECK(A.ctl, (pb >> 1) < K23_SMEM_WORDS)) atomicAdd(cnt + (pb >> 1), (pb & 1) ? 65536u : 1u);
             } else {
-                k23_bump(A, V, touched, s_nt, __ldg(A.g.col + rowx + pb), 1ull << K23_W_BITS);
+                const int32_t b = __ldg(A.g.col + rowx + pb);
+                if (PM_DCHECK(A.ctl, b >= 0 && b < A.g.n)) atomicAdd(E + b, 1ull);
             }
-        });
+        }
+        if (A.stats && lane == 0) stat += 4 + 16;
     }
     return stat;
 }
 
-// Adds the packed 16-bit counts of positions [0, mx) of x's row to the
-// root's words and clears them (threads `first`, `first` + STRIDE, ...).
+// Adds the packed 16-bit counts of positions [0, mx) of x's row to E and
+// clears them (threads `first`, `first` + STRIDE, ...).
 template <int STRIDE>
-__device__ __forceinline__ uint64_t k23_flush(const WheelArgs &A, unsigned long long *V, int32_t *touched,
-                                              int *s_nt, uint32_t *cnt, int64_t rowx, int32_t mx, int first) {
+__device__ __forceinline__ uint64_t k23_flush(const WheelArgs &A, unsigned long long *E, uint32_t *cnt,
+                                              int64_t rowx, int32_t mx, int first) {
     uint64_t stat = 0;
     for (int32_t w = first; w < (mx + 1) / 2; w += STRIDE) {
         const uint32_t v = cnt[w];
         if (!v) continue;
-        if (v & 0xffffu)
-            k23_bump(A, V, touched, s_nt, __ldg(A.g.col + rowx + 2 * w),
-                     (unsigned long long)(v & 0xffffu) << K23_W_BITS);
-        if (v >> 16)
-            k23_bump(A, V, touched, s_nt, __ldg(A.g.col + rowx + 2 * w + 1),
-                     (unsigned long long)(v >> 16) << K23_W_BITS);
+        if (v & 0xffffu) atomicAdd(E + __ldg(A.g.col + rowx + 2 * w), (unsigned long long)(v & 0xffffu));
+        if (v >> 16) atomicAdd(E + __ldg(A.g.col + rowx + 2 * w + 1), (unsigned long long)(v >> 16));
         cnt[w] = 0;
         if (A.stats) stat += 4 * (((v & 0xffffu) != 0) + ((v >> 16) != 0)) + 8;
     }
@@ -600,27 +580,24 @@ __device__ __forceinline__ uint64_t k23_flush(const WheelArgs &A, unsigned long 
 }
 
 // K2,3 and K2,3+e, one block per root (highest-ranked first), with the
-// block's counter words and touched list in global memory (n each).  Warps
-// take the root's neighbours from shared counters: walk A (a warp per
-// neighbour w, lanes over w's row below a) and walk B (a warp per
-// neighbour x whose window, a's position in x's row, fits the warp's own
-// 2048 16-bit counters).  Neighbours with long rows (walk A, more than
-// K23_BIG_A entries) or a wide window (walk B) go to a shared list that the
-// whole block then takes one at a time (walk B with 65,536 counters in
-// shared memory).
+// block's counters W (32-bit), E (64-bit) and touched list in global memory.
+// Walk A: warps take neighbours w of the root from a shared counter.  Walk
+// B: a warp takes each neighbour x whose window (a's position in x's row)
+// fits its own 2048 16-bit counters; the whole block then takes the others
+// one at a time with 65536 counters in shared memory (rows above that, or
+// lists longer than 65535, add to E directly).
 __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
     extern __shared__ uint32_t sc[];
     __shared__ unsigned long long s_root;
     __shared__ int s_stop;
     __shared__ int s_nt;
     __shared__ int s_next[2];
-    __shared__ int s_nbig;
-    __shared__ int32_t s_big[K23_BIG_CAP];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const DevGraph &g = A.g;
     Control *ctl = A.ctl;
     const uint64_t deadline = *(volatile unsigned long long *)&ctl->deadline;
-    unsigned long long *V = A.kV + size_t(blockIdx.x) * size_t(g.n);
+    uint32_t *W = A.kW + size_t(blockIdx.x) * size_t(g.n);
+    unsigned long long *E = A.kE + size_t(blockIdx.x) * size_t(g.n);
     int32_t *touched = A.ktouched + size_t(blockIdx.x) * size_t(g.n);
     uint32_t *wc = sc + warp * (K23_WARP_CAP / 2);
     u128 k23 = 0, k23e = 0;
@@ -634,42 +611,31 @@ __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
             s_nt = 0;
             s_next[0] = 0;
             s_next[1] = 0;
-            s_nbig = 0;
         }
         __syncthreads();
         if (s_root >= (unsigned long long)g.n || s_stop) break;
         const int32_t a = int32_t(g.n - 1 - int64_t(s_root));
         const int64_t rowa = __ldg(g.rowptr + a);
         const int32_t da = int32_t(__ldg(g.rowptr + a + 1) - rowa);
-        // walk A: 2-paths a-w-b, b < a (the entries of w's row before a),
-        // 32 neighbours w per warp (one per lane) walked together
-        const int32_t per_a = min(32, max(1, (da + K23_THREADS / 32 - 1) / (K23_THREADS / 32)));
+        // walk A: 2-paths a-w-b, b < a (the entries of w's row before a)
         for (;;) {
-            int32_t i0 = 0;
-            if (lane == 0) i0 = atomicAdd(&s_next[0], per_a);
-            i0 = __shfl_sync(FULL, i0, 0);
-            if (i0 >= da) break;
-            const int32_t i = i0 + lane;
-            int64_t base = 0;
-            int32_t cnt = 0;
-            if (lane < per_a && i < da) {
-                const int32_t m = __ldg(A.mpos + rowa + i);
-                bool big = false;
-                if (m > K23_BIG_A) {
-                    const int slot = atomicAdd(&s_nbig, 1);
-                    if (slot < K23_BIG_CAP) {
-                        s_big[slot] = i;                             // walk A block item
-                        big = true;
-                    }
-                }
-                if (!big) {
-                    base = __ldg(g.rowptr + __ldg(g.col + rowa + i));
-                    cnt = m;
-                    if (A.stats) stat += 4 + 4 + 16 + 16ull * uint64_t(m);
+            int32_t i = 0;
+            if (lane == 0) i = atomicAdd(&s_next[0], 1);
+            i = __shfl_sync(FULL, i, 0);
+            if (i >= da) break;
+            const int32_t w = __ldg(g.col + rowa + i);
+            const int32_t m = __ldg(A.mpos + rowa + i);
+            const int64_t roww = __ldg(g.rowptr + w);
+            for (int32_t j = lane; j < m; j += 32) {
+                const int32_t b = __ldg(g.col + roww + j);
+                if (!PM_DCHECK(ctl, b >= 0 && b < g.n)) break;
+                const uint32_t old = atomicAdd(W + b, 1u);
+                if (old == 0) {
+                    const int q = atomicAdd(&s_nt, 1);
+                    if (PM_DCHECK(ctl, q < g.n)) touched[q] = b;
                 }
             }
-            warp_lists<false>(g.col, base, cnt, 0, lane, ctl, g.nnz,
-                              [&](int32_t b) { k23_bump(A, V, touched, &s_nt, b, 1ull); });
+            if (A.stats && lane == 0) stat += 4 + 4 + 16 + 16ull * uint64_t(m);
         }
         // walk B, warp items: edges x < y of G_a, tips b < a in T_(x,y)
         for (;;) {
@@ -678,6 +644,7 @@ __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
             i = __shfl_sync(FULL, i, 0);
             if (i >= da) break;
             const int32_t mx = __ldg(A.mpos + rowa + i);          // a's position in x's row
+            if (mx > K23_WARP_CAP) continue;                       // block item
             const int32_t x = __ldg(g.col + rowa + i);
             const int64_t rowx = __ldg(g.rowptr + x);
             const int64_t y0 = __ldg(A.toff + rowx + mx);         // T_(x,a): the y in N(x) n N(a)
@@ -689,68 +656,52 @@ __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
             const int32_t k0 = lower_bound_dev(A.T + y0, ny, lox);
             if (A.stats && lane == 0) stat += 8 + w_probe_bytes(dx) + w_probe_bytes(ny);
             if (k0 >= ny) continue;
-            if (mx > K23_WARP_CAP) {
-                int slot = K23_BIG_CAP;
-                if (lane == 0) slot = atomicAdd(&s_nbig, 1);
-                slot = __shfl_sync(FULL, slot, 0);
-                if (slot < K23_BIG_CAP) {
-                    if (lane == 0) s_big[slot] = i | int32_t(0x80000000u);   // walk B block item
-                    continue;
-                }
-            }
-            const bool agg = mx <= K23_WARP_CAP && ny <= 65535;
-            stat += k23_walk_b<1>(A, V, touched, &s_nt, agg ? wc : nullptr, rowx, A.T + y0, k0, ny, mx, 0, lane);
+            const bool agg = ny <= 65535;
+            stat += k23_walk_b<1>(A, E, agg ? wc : nullptr, rowx, A.T + y0, k0, ny, mx, 0, lane);
             if (agg) {
                 __syncwarp();
-                stat += k23_flush<32>(A, V, touched, &s_nt, wc, rowx, mx, lane);
+                stat += k23_flush<32>(A, E, wc, rowx, mx, lane);
                 __syncwarp();
             }
         }
         __syncthreads();
-        // block items, one at a time
-        const int nbig = s_nbig < K23_BIG_CAP ? s_nbig : K23_BIG_CAP;
-        for (int q = 0; q < nbig; q++) {
-            const int32_t item = s_big[q];
-            const int32_t i = item & 0x7fffffff;
-            if (item >= 0) {                                        // walk A
-                const int32_t m = __ldg(A.mpos + rowa + i);
-                const int64_t roww = __ldg(g.rowptr + __ldg(g.col + rowa + i));
-                for (int32_t j = tid; j < m; j += K23_THREADS)
-                    k23_bump(A, V, touched, &s_nt, __ldg(g.col + roww + j), 1ull);
-                if (A.stats && tid == 0) stat += 4 + 4 + 16 + 16ull * uint64_t(m);
-                continue;                                           // no barrier needed
-            }
+        // walk B, block items: windows above K23_WARP_CAP, one at a time
+        for (int32_t i = 0; i < da; i++) {
             const int32_t mx = __ldg(A.mpos + rowa + i);
+            if (mx <= K23_WARP_CAP) continue;                      // uniform
             const int32_t x = __ldg(g.col + rowa + i);
             const int64_t rowx = __ldg(g.rowptr + x);
             const int64_t y0 = __ldg(A.toff + rowx + mx);
             const int32_t ny = int32_t(__ldg(A.toff + rowx + mx + 1) - y0);
+            if (ny == 0) continue;
             const int32_t dx = int32_t(__ldg(g.rowptr + x + 1) - rowx);
             const int32_t lox = lower_bound_dev(g.col + rowx, dx, x);
             const int32_t k0 = lower_bound_dev(A.T + y0, ny, lox);
+            if (k0 >= ny) continue;
             if (A.stats && tid == 0) stat += 4 + 4 + 16 + 16 + 8 + w_probe_bytes(dx) + w_probe_bytes(ny);
             const bool agg = ny <= 65535 && mx <= 2 * K23_SMEM_WORDS;
-            __syncthreads();                                        // shared counters free
-            stat += k23_walk_b<K23_THREADS / 32>(A, V, touched, &s_nt, agg ? sc : nullptr, rowx, A.T + y0, k0,
-                                                 ny, mx, warp, lane);
+            stat += k23_walk_b<K23_THREADS / 32>(A, E, agg ? sc : nullptr, rowx, A.T + y0, k0, ny, mx, warp,
+                                                 lane);
             if (agg) {
                 __syncthreads();
-                stat += k23_flush<K23_THREADS>(A, V, touched, &s_nt, sc, rowx, mx, tid);
+                stat += k23_flush<K23_THREADS>(A, E, sc, rowx, mx, tid);
+                __syncthreads();
             }
         }
         __syncthreads();
         const int nt = s_nt;
         for (int q = tid; q < nt; q += K23_THREADS) {
             const int32_t b = touched[q];
-            const unsigned long long v = V[b];
-            const uint64_t w = v & K23_W_MASK, e = v >> K23_W_BITS;
+            const uint32_t w = W[b];
+            const unsigned long long e = E[b];
             k23 += w_c3(w);
             if (e) {
                 if (w < 2) atomicExch(&ctl->fault, 1);
                 else k23e += u128(e) * (w - 2);
+                E[b] = 0;
             }
-            V[b] = 0;
-            if (A.stats) stat += 4 + 8 + 8;
+            W[b] = 0;
+            if (A.stats) stat += 4 + 4 + 8 + 4 + (e ? 8 : 0);
         }
     }
     w_flush(A.basis, DB_K23, k23, lane);
@@ -759,8 +710,6 @@ __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
 }
 
 size_t k23_smem_bytes() { return sizeof(uint32_t) * K23_SMEM_WORDS; }
-
-int64_t k23_max_degree() { return 1000000; }
 
 int k23_blocks(int device) {
     cudaFuncSetAttribute(k23_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(k23_smem_bytes()));
