@@ -175,12 +175,6 @@ struct pm_query_plan {
         uint32_t *kW = nullptr;
         unsigned long long *kE = nullptr;
         int32_t *ktouched = nullptr;
-        uint32_t *hW = nullptr;
-        unsigned long long *hE = nullptr;
-        int32_t *htouched = nullptr;
-        unsigned int *hctl = nullptr;
-        int64_t heavy = 0;
-        size_t b_h = 0;           // bytes of hW and of htouched (hE: twice)
         size_t b_toff = 0, b_T = 0, b_bsum = 0, b_rank = 0, b_mpos = 0, b_gcnt = 0, b_kW = 0, b_kE = 0;
         int64_t gcnt_words = 0;
         int w4_blocks = 0, k23_blocks = 0;
@@ -217,10 +211,6 @@ void free_wheel(pm_query_plan *p, int dev) {
     dev_free(w.kW, w.b_kW, dev);
     dev_free(w.kE, w.b_kE, dev);
     dev_free(w.ktouched, w.b_kW, dev);
-    dev_free(w.hW, w.b_h, dev);
-    dev_free(w.hE, 2 * w.b_h, dev);
-    dev_free(w.htouched, w.b_h, dev);
-    dev_free(w.hctl, 4 * sizeof(unsigned int), dev);
     dev_free(w.k5g, w.b_k5g, dev);
     p->wh = {};
 }
@@ -673,30 +663,6 @@ pm_status ensure_decomp(pm_query_plan *p, cudaStream_t s) {
         cudaError_t e = cudaMemsetAsync(w.kW, 0, w.b_kW, s);
         if (!e) e = cudaMemsetAsync(w.kE, 0, w.b_kE, s);
         if (e) return cuda_fail("K2,3 root counters", e);
-        // heavy roots: the highest-ranked vertices of degree >= the threshold
-        // (environment PM_K23_HEAVY_DEGREE, default 1024), at most 4096, each
-        // counted by the whole grid with one set of counters
-        int64_t min_degree = 1024;
-        if (const char *env = std::getenv("PM_K23_HEAVY_DEGREE")) min_degree = std::max(1L, std::atol(env));
-        w.heavy = 0;
-        for (int64_t r = g->n - 1; r >= 0 && w.heavy < 4096 && g->degree[size_t(r)] >= min_degree; r--) w.heavy++;
-        if (w.heavy > 0) {
-            const size_t nb = sizeof(uint32_t) * size_t(g->n);
-            w.b_h = nb;
-            w.hW = (uint32_t *)dev_alloc(nb, g->device);
-            w.hE = (unsigned long long *)dev_alloc(2 * nb, g->device);
-            w.htouched = (int32_t *)dev_alloc(nb, g->device);
-            w.hctl = (unsigned int *)dev_alloc(4 * sizeof(unsigned int), g->device);
-            if (!w.hW || !w.hE || !w.htouched || !w.hctl) {
-                free_wheel(p, g->device);
-                set_error("device allocation failed (K2,3 heavy-root counters)");
-                return PM_ENOMEM;
-            }
-            e = cudaMemsetAsync(w.hW, 0, nb, s);
-            if (!e) e = cudaMemsetAsync(w.hE, 0, 2 * nb, s);
-            if (!e) e = cudaMemsetAsync(w.hctl, 0, 4 * sizeof(unsigned int), s);
-            if (e) return cuda_fail("K2,3 heavy-root counters", e);
-        }
     }
     if ((passes & DP_K5E) && !p->wh.k5e_blocks) {
         auto &w = p->wh;
@@ -940,11 +906,6 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
         D.wheel.w4_blocks = p->wh.w4_blocks;
         D.wheel.kW = p->wh.kW;
         D.wheel.kE = p->wh.kE;
-        D.wheel.hW = p->wh.hW;
-        D.wheel.hE = p->wh.hE;
-        D.wheel.htouched = p->wh.htouched;
-        D.wheel.hctl = p->wh.hctl;
-        D.wheel.k23_light_begin = p->wh.heavy;
         D.wheel.ktouched = p->wh.ktouched;
         D.wheel.k23_blocks = p->wh.k23_blocks;
         D.wheel.k5g = p->wh.k5g;

@@ -120,8 +120,6 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
         //    space: lower neighbours, higher neighbours, all neighbours
         std::vector<int64_t> off[3];
         for (int sp = 0; sp < 3; sp++) off[sp].assign(n + 1, 0);
-        g->degree.assign(n, 0);
-        for (int64_t r = 0; r < n; r++) g->degree[r] = int32_t(rowptr[r + 1] - rowptr[r]);
         for (int64_t i = 0; i < n; i++) {
             const int64_t r = n - 1 - i;
             const int64_t d = rowptr[r + 1] - rowptr[r];

@@ -22,7 +22,6 @@ struct pm_graph {
     bool labeled = false;
     std::vector<int32_t> new_id;     // caller id -> internal id
     std::vector<int32_t> lowdeg;     // internal id -> neighbours with smaller internal id
-    std::vector<int32_t> degree;     // internal id -> degree
     std::vector<uint8_t> labels;     // internal id -> label (labeled graphs)
     int64_t *d_rowptr = nullptr;
     int32_t *d_col = nullptr;
@@ -208,13 +207,6 @@ struct WheelArgs {
     unsigned long long *kE;   // per block n diamond counters (zero on entry and exit)
     int32_t *ktouched;        // per block n touched vertices
     int k23_blocks;
-    int64_t k23_light_begin;  // roots n-1-k23_light_begin .. 0 go to the block-per-root kernel
-    // heavy roots (the highest-ranked k23_light_begin), each counted by the
-    // whole grid with one set of counters that stays in L2
-    uint32_t *hW;             // n 2-path counters
-    unsigned long long *hE;   // n diamond counters
-    int32_t *htouched;        // n touched vertices
-    unsigned int *hctl;       // next walk-A item, next walk-B item, touched count, finished blocks
     uint32_t *k5g;            // DP_K5E: per warp 32-bit counters above 2048 positions, or nullptr
     int64_t k5g_words;
     int k5e_blocks;

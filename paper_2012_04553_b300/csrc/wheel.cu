@@ -613,8 +613,8 @@ __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
             s_next[1] = 0;
         }
         __syncthreads();
-        if (s_root + (unsigned long long)A.k23_light_begin >= (unsigned long long)g.n || s_stop) break;
-        const int32_t a = int32_t(g.n - 1 - A.k23_light_begin - int64_t(s_root));
+        if (s_root >= (unsigned long long)g.n || s_stop) break;
+        const int32_t a = int32_t(g.n - 1 - int64_t(s_root));
         const int64_t rowa = __ldg(g.rowptr + a);
         const int32_t da = int32_t(__ldg(g.rowptr + a + 1) - rowa);
         // walk A: 2-paths a-w-b, b < a (the entries of w's row before a)
@@ -707,116 +707,6 @@ __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
     w_flush(A.basis, DB_K23, k23, lane);
     w_flush(A.basis, DB_K23E, k23e, lane);
     w_flush_stat(A.stats, stat, lane);
-}
-
-// Heavy roots: one root per launch, counted by the whole grid.  Its
-// counters (n 32-bit 2-path counts, n 64-bit diamond counts) are a single
-// set for the GPU, so they stay in L2 instead of being one of 148 per-block
-// sets scattered over HBM.  Warps take the root's neighbours from global
-// counters: walk A as in the per-block kernel; walk B aggregated in the
-// warp's shared counters when a's position in x's row is below 2048, else
-// added to the diamond counts directly.
-__global__ void __launch_bounds__(K23_THREADS, 1) k23_heavy_kernel(WheelArgs A, int32_t a) {
-    extern __shared__ uint32_t sc[];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const DevGraph &g = A.g;
-    Control *ctl = A.ctl;
-    if (*(volatile int *)&ctl->status) return;
-    const uint64_t deadline = *(volatile unsigned long long *)&ctl->deadline;
-    unsigned int *H = A.hctl;
-    uint32_t *wc = sc + warp * (K23_WARP_CAP / 2);
-    for (int i = lane; i < K23_WARP_CAP / 2; i += 32) wc[i] = 0;
-    __syncwarp();
-    const int64_t rowa = __ldg(g.rowptr + a);
-    const int32_t da = int32_t(__ldg(g.rowptr + a + 1) - rowa);
-    uint64_t stat = 0;
-    for (;;) {
-        int32_t i = 0, stop = 0;
-        if (lane == 0) {
-            i = int32_t(atomicAdd(H + 0, 1u));
-            stop = w_should_stop(ctl, deadline);
-        }
-        i = __shfl_sync(FULL, i, 0);
-        stop = __shfl_sync(FULL, stop, 0);
-        if (i >= da || stop) break;
-        const int32_t m = __ldg(A.mpos + rowa + i);
-        const int64_t roww = __ldg(g.rowptr + __ldg(g.col + rowa + i));
-        for (int32_t j = lane; j < m; j += 32) {
-            const int32_t b = __ldg(g.col + roww + j);
-            if (!PM_DCHECK(ctl, b >= 0 && b < g.n)) break;
-            if (atomicAdd(A.hW + b, 1u) == 0) {
-                const unsigned int q = atomicAdd(H + 2, 1u);
-                if (PM_DCHECK(ctl, q < (unsigned long long)g.n)) A.htouched[q] = b;
-            }
-        }
-        if (A.stats && lane == 0) stat += 4 + 4 + 16 + 16ull * uint64_t(m);
-    }
-    for (;;) {
-        int32_t i = 0, stop = 0;
-        if (lane == 0) {
-            i = int32_t(atomicAdd(H + 1, 1u));
-            stop = w_should_stop(ctl, deadline);
-        }
-        i = __shfl_sync(FULL, i, 0);
-        stop = __shfl_sync(FULL, stop, 0);
-        if (i >= da || stop) break;
-        const int32_t mx = __ldg(A.mpos + rowa + i);
-        const int32_t x = __ldg(g.col + rowa + i);
-        const int64_t rowx = __ldg(g.rowptr + x);
-        const int64_t y0 = __ldg(A.toff + rowx + mx);
-        const int32_t ny = int32_t(__ldg(A.toff + rowx + mx + 1) - y0);
-        if (A.stats && lane == 0) stat += 4 + 4 + 16 + 16;
-        if (ny == 0) continue;
-        const int32_t dx = int32_t(__ldg(g.rowptr + x + 1) - rowx);
-        const int32_t lox = lower_bound_dev(g.col + rowx, dx, x);
-        const int32_t k0 = lower_bound_dev(A.T + y0, ny, lox);
-        if (A.stats && lane == 0) stat += 8 + w_probe_bytes(dx) + w_probe_bytes(ny);
-        if (k0 >= ny) continue;
-        const bool agg = mx <= K23_WARP_CAP && ny <= 65535;
-        stat += k23_walk_b<1>(A, A.hE, agg ? wc : nullptr, rowx, A.T + y0, k0, ny, mx, 0, lane);
-        if (agg) {
-            __syncwarp();
-            stat += k23_flush<32>(A, A.hE, wc, rowx, mx, lane);
-            __syncwarp();
-        }
-    }
-    w_flush_stat(A.stats, stat, lane);
-}
-
-// The heavy root's sums over its touched vertices, then the counters back
-// to zero; the last block to finish resets the item counters for the next
-// root.
-__global__ void __launch_bounds__(K23_THREADS) k23_heavy_reduce_kernel(WheelArgs A) {
-    __shared__ bool s_last;
-    const int tid = threadIdx.x, lane = tid & 31;
-    unsigned int *H = A.hctl;
-    const unsigned int nt = *(volatile unsigned int *)(H + 2);
-    u128 k23 = 0, k23e = 0;
-    uint64_t stat = 0;
-    for (unsigned int q = blockIdx.x * K23_THREADS + tid; q < nt; q += gridDim.x * K23_THREADS) {
-        const int32_t b = A.htouched[q];
-        if (!PM_DCHECK(A.ctl, b >= 0 && b < A.g.n)) continue;
-        const uint32_t w = A.hW[b];
-        const unsigned long long e = A.hE[b];
-        k23 += w_c3(w);
-        if (e) {
-            if (w < 2) atomicExch(&A.ctl->fault, 1);
-            else k23e += u128(e) * (w - 2);
-            A.hE[b] = 0;
-        }
-        A.hW[b] = 0;
-        if (A.stats) stat += 4 + 4 + 8 + 4 + (e ? 8 : 0);
-    }
-    w_flush(A.basis, DB_K23, k23, lane);
-    w_flush(A.basis, DB_K23E, k23e, lane);
-    w_flush_stat(A.stats, stat, lane);
-    __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        s_last = atomicAdd(H + 3, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (s_last && tid < 4) H[tid] = 0;
 }
 
 size_t k23_smem_bytes() { return sizeof(uint32_t) * K23_SMEM_WORDS; }
@@ -983,11 +873,6 @@ int launch_wheel(const WheelArgs &A, int passes, void *stream) {
     tlist_kernel<<<device_sm_count(device) * per_sm, TL_WARPS * 32, 0, s>>>(A);
     if (passes & DP_K23E) {
         mpos_kernel<<<device_sm_count(device) * per_sm, TL_WARPS * 32, 0, s>>>(A);
-        cudaFuncSetAttribute(k23_heavy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(k23_smem_bytes()));
-        for (int64_t r = 0; r < A.k23_light_begin; r++) {
-            k23_heavy_kernel<<<A.k23_blocks, K23_THREADS, k23_smem_bytes(), s>>>(A, int32_t(A.g.n - 1 - r));
-            k23_heavy_reduce_kernel<<<A.k23_blocks, K23_THREADS, 0, s>>>(A);
-        }
         cudaMemsetAsync(&A.ctl->work3, 0, sizeof(unsigned long long), s);
         cudaFuncSetAttribute(k23_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(k23_smem_bytes()));
         k23_kernel<<<A.k23_blocks, K23_THREADS, k23_smem_bytes(), s>>>(A);
@@ -1015,8 +900,7 @@ int launch_wheel(const WheelArgs &A, int passes, void *stream) {
 // Kernels launched by launch_wheel for a pass set.
 int wheel_launches(const WheelArgs &A, int passes) {
     if (A.g.nnz == 0) return 0;
-    return 4 + int(A.g.hub && A.hub_rank && A.n_hubs > 0) +
-           ((passes & DP_K23E) ? 2 + 2 * int(A.k23_light_begin) : 0) +
+    return 4 + int(A.g.hub && A.hub_rank && A.n_hubs > 0) + 2 * int((passes & DP_K23E) != 0) +
            int((passes & DP_W4) != 0) + int((passes & DP_K5E) != 0);
 }
 

@@ -160,11 +160,8 @@ def test_decomposition_on_scale20_matches_free_plans():
 
 def test_decomposition_with_hub_bitmaps_everywhere(monkeypatch):
     """Adjacency bitmaps for every vertex of degree >= 3: the common-neighbour
-    lists and mirror positions then come from the popcount rank index; and
-    every root of degree >= 3 goes through the whole-grid heavy-root path of
-    the K2,3 pass."""
+    lists and mirror positions then come from the popcount rank index."""
     monkeypatch.setenv("PM_HUB_MIN_DEGREE", "3")
-    monkeypatch.setenv("PM_K23_HEAVY_DEGREE", "3")
     n, s, d = hub_graph()
     og = oracle.prepare_graph(n, s, d)
     g = pm.Graph(n, s, d)
