@@ -1187,7 +1187,18 @@ pm_status prepare_active(pm_query_plan *p, cudaStream_t s) {
 // Cost of matching one pattern on a graph, for cost-based morph selection:
 // the autotuner's sampled time of its faster plan family (cached per graph);
 // a pattern whose sampled runs both hit the deadline costs 1e9 ms.
-double pattern_cost(const pm_graph *g, const Pat &q) {
+// Cost of a pattern not yet timed once the morph selection's sampling time
+// is spent: no sampling, an estimate that only orders patterns by what
+// drives matching cost on skewed graphs (size, and anti-edges for
+// vertex-induced patterns, whose set differences do not shrink on hubs).
+double estimated_cost(const Pat &q) {
+    double ms = 1.0;
+    for (int i = 3; i < q.k; i++) ms *= 10.0;
+    return q.vi && !q.is_clique() ? 20.0 * ms : ms;
+}
+
+double pattern_cost(const pm_graph *g, const Pat &q, std::chrono::steady_clock::time_point deadline) {
+    const bool spent = std::chrono::steady_clock::now() > deadline;
     const int f = decomp_formula(q);
     if (f >= 0) {
         // the decomposition passes this pattern needs, timed once per graph
@@ -1197,6 +1208,7 @@ double pattern_cost(const pm_graph *g, const Pat &q) {
             auto it = g->decomp_ms.find(passes);
             if (it != g->decomp_ms.end()) return it->second;
         }
+        if (spent) return 1.0;      // decomposition passes: tens to hundreds of ms at scale 20
         pm_pattern r{};
         r.k = q.k;
         r.edge_mask = q.mask();
@@ -1222,6 +1234,7 @@ double pattern_cost(const pm_graph *g, const Pat &q) {
         auto it = g->tuned_ms.find(key);
         if (it != g->tuned_ms.end()) return std::isfinite(it->second) ? it->second : 1e9;
     }
+    if (spent) return estimated_cost(q);
     pm_pattern r{};
     r.k = q.k;
     r.edge_mask = q.mask();
@@ -1550,7 +1563,15 @@ pm_status pm_plan(const pm_graph *g, const pm_pattern *queries, int32_t nq, pm_o
     p->op = op;
     std::string why;
     std::function<double(const Pat &)> cost;
-    if (mode == PM_MORPH_COST && g) cost = [g](const Pat &q) { return pattern_cost(g, q); };
+    if (mode == PM_MORPH_COST && g) {
+        // sampling time of the whole selection: environment PM_COST_BUDGET_S
+        // (default 30 s); patterns met after it get estimated costs
+        double budget_s = 30.0;
+        if (const char *env = std::getenv("PM_COST_BUDGET_S")) budget_s = std::atof(env);
+        const auto deadline = std::chrono::steady_clock::now() +
+                              std::chrono::microseconds(int64_t(std::max(0.0, budget_s) * 1e6));
+        cost = [g, deadline](const Pat &q) { return pattern_cost(g, q, deadline); };
+    }
     pm_status st = morph_select(pats, op, mode, p->morph, &why, g ? &cost : nullptr);
     if (st != PM_OK) {
         set_error("pm_plan: " + why);
