@@ -48,6 +48,9 @@ def parse():
                          "measurement line of the other workloads; pattern / motifs: one pattern "
                          "or one k-motif count (profiling targets)")
     ap.add_argument("--motif-k", type=int, default=5, help="motif size of the motifs workload")
+    ap.add_argument("--motif-mode", choices=["naive", "direct", "cost"], default="naive",
+                    help="morph selection of the motifs workload")
+    ap.add_argument("--motif-deadline", type=float, default=0.0, help="deadline of each motifs count (0: none)")
     ap.add_argument("--mc5-direct-deadline", type=float, default=60.0,
                     help="deadline of the whole-graph direct 5-motif count")
     ap.add_argument("--no-mc5", action="store_true", help="leave the 5-motif measurements out of the mc line")
@@ -558,23 +561,32 @@ def run_mc5(args):
 
 def run_motifs(args):
     """k-motif counting (all connected vertex-induced k-vertex patterns,
-    naive morph) on R-MAT (scale, ef 16, seed): one count that allocates
-    the plan's scratch, then one timed count (profiling target)."""
+    naive morph, direct or cost-based selection) on R-MAT (scale, ef 16,
+    seed): one count that allocates the plan's scratch, then one timed count
+    (a deadline, if given, applies to both)."""
     import torch
     import paper_2012_04553_b300 as pm
     src, dst = cached_rmat(args.scale, 16, args.seed)
     g = pm.Graph(1 << args.scale, src, dst)
+    mode = {"naive": pm.MORPH_NAIVE, "direct": pm.MORPH_NONE, "cost": pm.MORPH_COST}[args.motif_mode]
     plan = pm.Plan(g, [pm.make_pattern(args.motif_k, m, pm.VERTEX_INDUCED) for m in connected_classes(args.motif_k)],
-                   mode=pm.MORPH_NAIVE)
+                   mode=mode)
     plan.autotune()
-    plan.count()
+    try:
+        plan.count(timeout_s=args.motif_deadline)
+    except pm.PMTimeout:
+        pass
     torch.cuda.synchronize()
     t0 = time.time()
-    counts = plan.count()
+    try:
+        counts = plan.count(timeout_s=args.motif_deadline)
+        res = {"value": time.time() - t0, "counts": [str(c) for c in counts]}
+    except pm.PMTimeout:
+        res = {"value": None, "timed_out_after_s": round(time.time() - t0, 3), "deadline_s": args.motif_deadline}
     torch.cuda.synchronize()
-    print(json.dumps({"metric": f"{args.motif_k}-motif count (morphed), wall time", "value": time.time() - t0,
-                      "unit": "s", "counts": [str(c) for c in counts], "launches": plan.last_launches(),
-                      "scale": args.scale, "seed": args.seed}), flush=True)
+    print(json.dumps({"metric": f"{args.motif_k}-motif count ({args.motif_mode}), wall time", "unit": "s",
+                      **res, "launches": plan.last_launches(), "scale": args.scale, "seed": args.seed}),
+          flush=True)
 
 
 def run_pattern(args):
