@@ -906,6 +906,7 @@ pm_status launch_table(pm_query_plan *p, const PlanTable &t, const DevTasks &tas
         D.wheel.w4_blocks = p->wh.w4_blocks;
         D.wheel.kW = p->wh.kW;
         D.wheel.kE = p->wh.kE;
+        D.wheel.k23_narrow = g->max_degree < 65536 ? 1 : 0;
         D.wheel.ktouched = p->wh.ktouched;
         D.wheel.k23_blocks = p->wh.k23_blocks;
         D.wheel.k5g = p->wh.k5g;

@@ -207,6 +207,7 @@ struct WheelArgs {
     unsigned long long *kE;   // per block n diamond counters (zero on entry and exit)
     int32_t *ktouched;        // per block n touched vertices
     int k23_blocks;
+    int k23_narrow;           // largest degree < 65536: 16-bit 2-path and 32-bit diamond counters
     uint32_t *k5g;            // DP_K5E: per warp 32-bit counters above 2048 positions, or nullptr
     int64_t k5g_words;
     int k5e_blocks;

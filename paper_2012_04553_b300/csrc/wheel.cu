@@ -43,6 +43,7 @@
 // y.  The counters cover x's positions above y only (fewer than x's
 // neighbours ranked above x, a few hundred on R-MAT graphs).
 #include <algorithm>
+#include <type_traits>
 
 #include "devgraph.cuh"
 #include "internal.hpp"
@@ -537,8 +538,8 @@ __device__ __forceinline__ u128 w_c3(uint64_t x) { return x >= 3 ? u128(x) * (x 
 // CNT != nullptr the counts go to 16-bit counters over x's positions
 // (packed two to a word; a count never exceeds |T_(x,a)| <= 65535 here) and
 // are added to E once per position afterwards; otherwise straight to E.
-template <int STRIDE>
-__device__ __forceinline__ uint64_t k23_walk_b(const WheelArgs &A, unsigned long long *E, uint32_t *cnt,
+template <int STRIDE, class ET>
+__device__ __forceinline__ uint64_t k23_walk_b(const WheelArgs &A, ET *E, uint32_t *cnt,
                                                int64_t rowx, const int32_t *Y, int32_t k0, int32_t ny,
                                                int32_t mx, int first, int lane) {
     uint64_t stat = 0;
@@ -554,7 +555,7 @@ __device__ __forceinline__ uint64_t k23_walk_b(const WheelArgs &A, unsigned long
                 if (PM_DCHECK(A.ctl, (pb >> 1) < K23_SMEM_WORDS)) atomicAdd(cnt + (pb >> 1), (pb & 1) ? 65536u : 1u);
             } else {
                 const int32_t b = __ldg(A.g.col + rowx + pb);
-                if (PM_DCHECK(A.ctl, b >= 0 && b < A.g.n)) atomicAdd(E + b, 1ull);
+                if (PM_DCHECK(A.ctl, b >= 0 && b < A.g.n)) atomicAdd(E + b, ET(1));
             }
         }
         if (A.stats && lane == 0) stat += 4 + 16;
@@ -564,15 +565,15 @@ __device__ __forceinline__ uint64_t k23_walk_b(const WheelArgs &A, unsigned long
 
 // Adds the packed 16-bit counts of positions [0, mx) of x's row to E and
 // clears them (threads `first`, `first` + STRIDE, ...).
-template <int STRIDE>
-__device__ __forceinline__ uint64_t k23_flush(const WheelArgs &A, unsigned long long *E, uint32_t *cnt,
+template <int STRIDE, class ET>
+__device__ __forceinline__ uint64_t k23_flush(const WheelArgs &A, ET *E, uint32_t *cnt,
                                               int64_t rowx, int32_t mx, int first) {
     uint64_t stat = 0;
     for (int32_t w = first; w < (mx + 1) / 2; w += STRIDE) {
         const uint32_t v = cnt[w];
         if (!v) continue;
-        if (v & 0xffffu) atomicAdd(E + __ldg(A.g.col + rowx + 2 * w), (unsigned long long)(v & 0xffffu));
-        if (v >> 16) atomicAdd(E + __ldg(A.g.col + rowx + 2 * w + 1), (unsigned long long)(v >> 16));
+        if (v & 0xffffu) atomicAdd(E + __ldg(A.g.col + rowx + 2 * w), ET(v & 0xffffu));
+        if (v >> 16) atomicAdd(E + __ldg(A.g.col + rowx + 2 * w + 1), ET(v >> 16));
         cnt[w] = 0;
         if (A.stats) stat += 4 * (((v & 0xffffu) != 0) + ((v >> 16) != 0)) + 8;
     }
@@ -586,7 +587,12 @@ __device__ __forceinline__ uint64_t k23_flush(const WheelArgs &A, unsigned long 
 // fits its own 2048 16-bit counters; the whole block then takes the others
 // one at a time with 65536 counters in shared memory (rows above that, or
 // lists longer than 65535, add to E directly).
+template <bool NARROW>
 __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
+    // NARROW (largest degree below 65536): 16-bit 2-path and 32-bit diamond
+    // counters (a root's c_ab <= 65535 and e_ab <= C(65535, 2) < 2^32), half
+    // the scattered counter bytes of the 32/64-bit layout
+    using ET = typename std::conditional<NARROW, unsigned int, unsigned long long>::type;
     extern __shared__ uint32_t sc[];
     __shared__ unsigned long long s_root;
     __shared__ int s_stop;
@@ -596,8 +602,9 @@ __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
     const DevGraph &g = A.g;
     Control *ctl = A.ctl;
     const uint64_t deadline = *(volatile unsigned long long *)&ctl->deadline;
-    uint32_t *W = A.kW + size_t(blockIdx.x) * size_t(g.n);
-    unsigned long long *E = A.kE + size_t(blockIdx.x) * size_t(g.n);
+    uint32_t *W = A.kW + size_t(blockIdx.x) * size_t(g.n);          // NARROW: 16-bit halves
+    uint16_t *W16 = reinterpret_cast<uint16_t *>(W);
+    ET *E = reinterpret_cast<ET *>(A.kE + size_t(blockIdx.x) * size_t(g.n));
     int32_t *touched = A.ktouched + size_t(blockIdx.x) * size_t(g.n);
     uint32_t *wc = sc + warp * (K23_WARP_CAP / 2);
     u128 k23 = 0, k23e = 0;
@@ -629,7 +636,13 @@ __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
             for (int32_t j = lane; j < m; j += 32) {
                 const int32_t b = __ldg(g.col + roww + j);
                 if (!PM_DCHECK(ctl, b >= 0 && b < g.n)) break;
-                const uint32_t old = atomicAdd(W + b, 1u);
+                uint32_t old;
+                if (NARROW) {
+                    const int sh = 16 * (b & 1);
+                    old = (atomicAdd(W + (b >> 1), 1u << sh) >> sh) & 0xffffu;
+                } else {
+                    old = atomicAdd(W + b, 1u);
+                }
                 if (old == 0) {
                     const int q = atomicAdd(&s_nt, 1);
                     if (PM_DCHECK(ctl, q < g.n)) touched[q] = b;
@@ -657,10 +670,10 @@ __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
             if (A.stats && lane == 0) stat += 8 + w_probe_bytes(dx) + w_probe_bytes(ny);
             if (k0 >= ny) continue;
             const bool agg = ny <= 65535;
-            stat += k23_walk_b<1>(A, E, agg ? wc : nullptr, rowx, A.T + y0, k0, ny, mx, 0, lane);
+            stat += k23_walk_b<1, ET>(A, E, agg ? wc : nullptr, rowx, A.T + y0, k0, ny, mx, 0, lane);
             if (agg) {
                 __syncwarp();
-                stat += k23_flush<32>(A, E, wc, rowx, mx, lane);
+                stat += k23_flush<32, ET>(A, E, wc, rowx, mx, lane);
                 __syncwarp();
             }
         }
@@ -680,11 +693,11 @@ __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
             if (k0 >= ny) continue;
             if (A.stats && tid == 0) stat += 4 + 4 + 16 + 16 + 8 + w_probe_bytes(dx) + w_probe_bytes(ny);
             const bool agg = ny <= 65535 && mx <= 2 * K23_SMEM_WORDS;
-            stat += k23_walk_b<K23_THREADS / 32>(A, E, agg ? sc : nullptr, rowx, A.T + y0, k0, ny, mx, warp,
-                                                 lane);
+            stat += k23_walk_b<K23_THREADS / 32, ET>(A, E, agg ? sc : nullptr, rowx, A.T + y0, k0, ny, mx,
+                                                     warp, lane);
             if (agg) {
                 __syncthreads();
-                stat += k23_flush<K23_THREADS>(A, E, sc, rowx, mx, tid);
+                stat += k23_flush<K23_THREADS, ET>(A, E, sc, rowx, mx, tid);
                 __syncthreads();
             }
         }
@@ -692,7 +705,7 @@ __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
         const int nt = s_nt;
         for (int q = tid; q < nt; q += K23_THREADS) {
             const int32_t b = touched[q];
-            const uint32_t w = W[b];
+            const uint32_t w = NARROW ? uint32_t(W16[b]) : W[b];
             const unsigned long long e = E[b];
             k23 += w_c3(w);
             if (e) {
@@ -700,7 +713,8 @@ __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
                 else k23e += u128(e) * (w - 2);
                 E[b] = 0;
             }
-            W[b] = 0;
+            if (NARROW) W16[b] = 0;
+            else W[b] = 0;
             if (A.stats) stat += 4 + 4 + 8 + 4 + (e ? 8 : 0);
         }
     }
@@ -712,9 +726,12 @@ __global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
 size_t k23_smem_bytes() { return sizeof(uint32_t) * K23_SMEM_WORDS; }
 
 int k23_blocks(int device) {
-    cudaFuncSetAttribute(k23_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(k23_smem_bytes()));
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k23_kernel, K23_THREADS, k23_smem_bytes());
+    cudaFuncSetAttribute(k23_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(k23_smem_bytes()));
+    cudaFuncSetAttribute(k23_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(k23_smem_bytes()));
+    int per_sm = 0, per_sm_n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k23_kernel<false>, K23_THREADS, k23_smem_bytes());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_n, k23_kernel<true>, K23_THREADS, k23_smem_bytes());
+    per_sm = std::min(per_sm, per_sm_n);
     if (per_sm < 1) per_sm = 1;
     return device_sm_count(device) * per_sm;
 }
@@ -874,8 +891,13 @@ int launch_wheel(const WheelArgs &A, int passes, void *stream) {
     if (passes & DP_K23E) {
         mpos_kernel<<<device_sm_count(device) * per_sm, TL_WARPS * 32, 0, s>>>(A);
         cudaMemsetAsync(&A.ctl->work3, 0, sizeof(unsigned long long), s);
-        cudaFuncSetAttribute(k23_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(k23_smem_bytes()));
-        k23_kernel<<<A.k23_blocks, K23_THREADS, k23_smem_bytes(), s>>>(A);
+        if (A.k23_narrow) {
+            cudaFuncSetAttribute(k23_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(k23_smem_bytes()));
+            k23_kernel<true><<<A.k23_blocks, K23_THREADS, k23_smem_bytes(), s>>>(A);
+        } else {
+            cudaFuncSetAttribute(k23_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(k23_smem_bytes()));
+            k23_kernel<false><<<A.k23_blocks, K23_THREADS, k23_smem_bytes(), s>>>(A);
+        }
     }
     if (passes & DP_K5E) {
         cudaMemsetAsync(&A.ctl->work3, 0, sizeof(unsigned long long), s);
