@@ -59,11 +59,11 @@ constexpr int W4_WARPS = W4_THREADS / 32;
 constexpr int W4_WARP_CAP = 2048;                  // counter positions of a warp task
 constexpr int W4_SMEM_WORDS = 32768;               // 128 KB: 65536 16-bit block counters
 constexpr int64_t W4_BLOCK_CAP = 2 * int64_t(W4_SMEM_WORDS);
-constexpr int K23_THREADS = 1024;
+constexpr int K23_THREADS = 512;                   // two blocks (roots) per SM
 constexpr int K5E_THREADS = 512;
 constexpr int K5E_WARP_WORDS = 1024;               // 2048 16-bit counters per warp (64 KB per block)
 constexpr int K23_WARP_CAP = 2048;                 // walk-B window of a warp item (positions)
-constexpr int K23_SMEM_WORDS = 32768;              // 128 KB: 32 warps x 1024 words, or one block window
+constexpr int K23_SMEM_WORDS = 16384;              // 64 KB: 16 warps x 1024 words, or one block window
 
 __device__ __forceinline__ u128 w_c2(uint64_t x) { return x >= 2 ? u128(x) * (x - 1) / 2 : 0; }
 
@@ -585,10 +585,11 @@ __device__ __forceinline__ uint64_t k23_flush(const WheelArgs &A, ET *E, uint32_
 // Walk A: warps take neighbours w of the root from a shared counter.  Walk
 // B: a warp takes each neighbour x whose window (a's position in x's row)
 // fits its own 2048 16-bit counters; the whole block then takes the others
-// one at a time with 65536 counters in shared memory (rows above that, or
-// lists longer than 65535, add to E directly).
+// one at a time with 32768 counters in shared memory (rows above that, or
+// lists longer than 65535, add to E directly).  Two blocks share an SM, so
+// 2 x SMs roots are in flight (most roots have few neighbours).
 template <bool NARROW>
-__global__ void __launch_bounds__(K23_THREADS, 1) k23_kernel(WheelArgs A) {
+__global__ void __launch_bounds__(K23_THREADS, 2) k23_kernel(WheelArgs A) {
     // NARROW (largest degree below 65536): 16-bit 2-path and 32-bit diamond
     // counters (a root's c_ab <= 65535 and e_ab <= C(65535, 2) < 2^32), half
     // the scattered counter bytes of the 32/64-bit layout
