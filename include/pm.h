@@ -74,7 +74,10 @@ typedef enum { PM_OP_COUNT = 0, PM_OP_SUPPORT = 1 } pm_op;
  * a sum over vertex-induced superpatterns (Theorem 3.1) — where the cost of
  * a pattern is the autotuner's sampled GPU time on the plan's graph (counting
  * kernels, also for MNI) and patterns already selected for other queries
- * cost nothing.  PM_MORPH_COST needs a graph in pm_plan. */
+ * cost nothing.  PM_MORPH_COST needs a graph in pm_plan.  Its sampling is
+ * bounded (environment PM_COST_BUDGET_S, default 30 s per pm_plan): patterns
+ * met after that get an estimate instead (decomposed patterns cheap, else
+ * growing tenfold per vertex, and twentyfold for vertex-induced ones). */
 typedef enum { PM_MORPH_NONE = 0, PM_MORPH_NAIVE = 1, PM_MORPH_COST = 2 } pm_morph_mode;
 
 #define PM_MAX_K 8
@@ -212,9 +215,13 @@ pm_status pm_plan_set_launch(pm_query_plan *p, int32_t mode);
  * second-level candidates a task chunk keeps before the rest is deferred to
  * other warps, which sets how many warps share a hub root -- at a quarter
  * and at four times the compiled value, keeping one only if it is more than
- * 10% faster; decisions are cached on the graph.  families (nullable):
- * n_matched entries receiving PM_PLANS_ROOTED, PM_PLANS_FREE or (counting
- * plans, unless a set-operation family is forced) PM_PLANS_DECOMP. */
+ * 10% faster; decisions are cached on the graph.  Patterns are timed
+ * smallest first, at most 30 s of sampling per call (environment
+ * PM_AUTOTUNE_BUDGET_S); the rest take the quick rule (decomposition where
+ * it applies, the rooted family for the wedge kernels, else free) without
+ * being cached.  families (nullable): n_matched entries receiving
+ * PM_PLANS_ROOTED, PM_PLANS_FREE or (counting plans, unless a set-operation
+ * family is forced) PM_PLANS_DECOMP. */
 pm_status pm_plan_autotune(pm_query_plan *p, void *stream, int32_t *families);
 /* Copy the compiled plans of one family (PM_PLANS_ROOTED: n_kernels_plans
  * records; PM_PLANS_FREE: n_matched records) into out (cap bytes).  A record
