@@ -18,12 +18,11 @@ namespace pm {
 namespace {
 
 template <class F>
-void parallel_for(int64_t n, F f) {
+void parallel_for(int64_t n, F f, int64_t grain = 4096, int64_t min_parallel = 100000) {
     unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
-    if (n < 100000) nt = 1;
+    if (n < min_parallel) nt = 1;
     std::vector<std::thread> th;
     std::atomic<int64_t> next{0};
-    const int64_t grain = 4096;
     auto body = [&]() {
         for (;;) {
             int64_t b = next.fetch_add(grain);
@@ -35,6 +34,15 @@ void parallel_for(int64_t n, F f) {
     for (unsigned t = 1; t < nt; t++) th.emplace_back(body);
     body();
     for (auto &t : th) t.join();
+}
+
+// f(t) on threads t = 0 .. nt-1 (the calling thread runs t = 0).
+template <class F>
+void run_threads(unsigned nt, F f) {
+    std::vector<std::thread> th;
+    for (unsigned t = 1; t < nt; t++) th.emplace_back(f, t);
+    f(0u);
+    for (auto &x : th) x.join();
 }
 
 }  // namespace
@@ -57,23 +65,55 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
     g->n = n;
     g->labeled = labels != nullptr;
     try {
-        // 1. bucket both directions by source, dropping self-loops
-        std::vector<int64_t> rp(n + 1, 0);
+        // 1. bucket both directions by source, dropping self-loops: each
+        //    thread counts its slice of the edges per vertex, the counts are
+        //    scanned per vertex across threads, and each thread fills its own
+        //    part of every row (no shared cursors: hub rows would serialise
+        //    them); the order inside a row does not matter, rows are sorted next
+        unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        while (nt > 1 && (m_raw < int64_t(nt) * 65536 ||
+                          int64_t(nt) * n > std::min(m_raw, int64_t(1) << 25))) nt /= 2;   // counters <= edges
+        const int64_t slice = (m_raw + nt - 1) / nt;
+        std::vector<int64_t> tc(size_t(nt) * size_t(n), 0);   // thread t's counts, then cursors
+        std::vector<int64_t> tloops(nt, 0);
+        run_threads(nt, [&](unsigned t) {
+            int64_t *c = tc.data() + size_t(t) * size_t(n);
+            const int64_t b = int64_t(t) * slice, e = std::min(m_raw, b + slice);
+            for (int64_t i = b; i < e; i++) {
+                if (src[i] == dst[i]) { tloops[t]++; continue; }
+                c[src[i]]++;
+                c[dst[i]]++;
+            }
+        });
         int64_t loops = 0;
-        for (int64_t i = 0; i < m_raw; i++) {
-            if (src[i] == dst[i]) { loops++; continue; }
-            rp[src[i] + 1]++;
-            rp[dst[i] + 1]++;
+        for (unsigned t = 0; t < nt; t++) loops += tloops[t];
+        std::vector<int64_t> rp(n + 1, 0);
+        for (int64_t v = 0; v < n; v++) {
+            int64_t d = 0;
+            for (unsigned t = 0; t < nt; t++) d += tc[size_t(t) * size_t(n) + size_t(v)];
+            rp[v + 1] = rp[v] + d;
         }
-        for (int64_t v = 0; v < n; v++) rp[v + 1] += rp[v];
         std::vector<int32_t> adj(rp[n]);
         {
-            std::vector<int64_t> fill(rp.begin(), rp.end() - 1);
-            for (int64_t i = 0; i < m_raw; i++) {
-                if (src[i] == dst[i]) continue;
-                adj[fill[src[i]]++] = dst[i];
-                adj[fill[dst[i]]++] = src[i];
-            }
+            // per-thread write cursors relative to the row start
+            parallel_for(n, [&](int64_t v) {
+                int64_t run = 0;
+                for (unsigned t = 0; t < nt; t++) {
+                    int64_t &c = tc[size_t(t) * size_t(n) + size_t(v)];
+                    const int64_t k = c;
+                    c = run;
+                    run += k;
+                }
+            });
+            run_threads(nt, [&](unsigned t) {
+                int64_t *c = tc.data() + size_t(t) * size_t(n);
+                const int64_t b = int64_t(t) * slice, e = std::min(m_raw, b + slice);
+                for (int64_t i = b; i < e; i++) {
+                    if (src[i] == dst[i]) continue;
+                    adj[rp[src[i]] + c[src[i]]++] = dst[i];
+                    adj[rp[dst[i]] + c[dst[i]]++] = src[i];
+                }
+            });
         }
         // 2. sort and deduplicate each row
         std::vector<int64_t> deg(n);
@@ -81,7 +121,7 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
             int32_t *b = adj.data() + rp[v], *e = adj.data() + rp[v + 1];
             std::sort(b, e);
             deg[v] = std::unique(b, e) - b;
-        });
+        }, 256);
         int64_t nnz = 0, maxd = 0;
         for (int64_t v = 0; v < n; v++) { nnz += deg[v]; maxd = std::max(maxd, deg[v]); }
         g->m = nnz / 2;
@@ -104,14 +144,15 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
         for (int64_t r = 0; r < n; r++) rowptr[r + 1] = rowptr[r] + deg[old_of[r]];
         std::vector<int32_t> col(nnz);
         g->lowdeg.assign(n, 0);
-        parallel_for(n, [&](int64_t r) {
+        parallel_for(n, [&](int64_t i) {
+            const int64_t r = n - 1 - i;   // the longest rows (highest ranks) first, spread over threads
             const int64_t v = old_of[r];
             int32_t *o = col.data() + rowptr[r];
             const int64_t d = deg[v];
-            for (int64_t i = 0; i < d; i++) o[i] = g->new_id[adj[rp[v] + i]];
+            for (int64_t j = 0; j < d; j++) o[j] = g->new_id[adj[rp[v] + j]];
             std::sort(o, o + d);
             g->lowdeg[r] = int32_t(std::lower_bound(o, o + d, int32_t(r)) - o);
-        });
+        }, 64);
         if (labels) {
             g->labels.resize(n);
             for (int64_t r = 0; r < n; r++) g->labels[r] = labels[old_of[r]];
@@ -173,13 +214,13 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
             if (nh > 0) {
                 std::vector<int32_t> hub(n, -1);
                 std::vector<uint32_t> bits(size_t(nh) * size_t(words), 0u);
-                for (int64_t i = 0; i < nh; i++) {
+                parallel_for(nh, [&](int64_t i) {      // one hub's bitmap per task
                     const int64_t r = n - 1 - i;
                     hub[r] = int32_t(i);
                     uint32_t *w = bits.data() + size_t(i) * size_t(words);
                     for (int64_t e = rowptr[r]; e < rowptr[r + 1]; e++)
                         w[col[e] >> 5] |= 1u << (col[e] & 31);
-                }
+                }, 1, 2);
                 g->d_hub = (int32_t *)dev_alloc(sizeof(int32_t) * n, device);
                 g->d_bits = (uint32_t *)dev_alloc(sizeof(uint32_t) * bits.size(), device);
                 if (!g->d_hub || !g->d_bits) {
