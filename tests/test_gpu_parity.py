@@ -41,6 +41,26 @@ def test_rmat_s12_4motifs_golden():
                 gold["edge_induced"][str(k)]
 
 
+def test_threaded_graph_build_against_oracle():
+    """262144 raw edges (self-loops, duplicates and 15 vertices of degree
+    >= 1024 among them): enough that the host builder splits the edge list
+    over threads with per-thread row counts and cursors and builds the hub
+    bitmaps in parallel. The simple-graph edge count, the dropped loops and
+    duplicates, the maximum degree, the (degree, id) order and the
+    3-vertex counts equal the oracle's."""
+    n = 1 << 14
+    s, d = rmat_edges(14, 16, seed=131)
+    og = oracle.prepare_graph(n, s, d)
+    g = load(n, s, d)
+    info = g.info()
+    loops = int((np.asarray(s) == np.asarray(d)).sum())
+    assert (info["m"], info["self_loops"], info["max_degree"]) == (og.m, loops, int(np.max(og.degree)))
+    assert info["duplicates"] == len(s) - loops - og.m
+    assert np.array_equal(g.vertex_order(), og.rank)
+    want = [oracle.count(og, algebra.Pattern.from_mask(3, m)) for m in algebra.connected_classes(3)]
+    assert pm.Plan(g, motif_queries(3, vi=False), mode=pm.MORPH_NONE).count() == want
+
+
 @pytest.mark.parametrize("scale,ef,seed,kmax", [(7, 6, 100, 5), (8, 8, 101, 4), (9, 6, 102, 4),
                                                 (10, 4, 103, 4)])
 def test_motifs_small_rmat_against_oracle(scale, ef, seed, kmax):
