@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <thread>
 #include <vector>
 
@@ -34,6 +35,44 @@ void parallel_for(int64_t n, F f, int64_t grain = 4096, int64_t min_parallel = 1
     for (unsigned t = 1; t < nt; t++) th.emplace_back(body);
     body();
     for (auto &t : th) t.join();
+}
+
+// An array of k entries left uninitialised, for buffers whose every entry is
+// written by a parallel pass: the threads that fill it touch its pages first,
+// instead of one thread zeroing it beforehand.
+template <class T>
+std::unique_ptr<T[]> raw_array(size_t k) {
+    return std::unique_ptr<T[]>(new T[k]);
+}
+
+// Sorts a[0..d) of ids in [0, 2^bits) ascending: short rows by comparison,
+// long ones by least-significant-digit radix sort on 8-bit digits (one
+// stable counting pass per digit, alternating with a scratch row: on the
+// stack up to 4096 entries, on the heap above).
+void sort_ids(int32_t *a, int64_t d, int bits) {
+    if (d < 128) {
+        std::sort(a, a + d);
+        return;
+    }
+    int32_t local[4096];
+    std::unique_ptr<int32_t[]> heap;
+    if (d > 4096) heap = raw_array<int32_t>(size_t(d));
+    int32_t *from = a, *to = heap ? heap.get() : local;
+    for (int shift = 0; shift < bits; shift += 8) {
+        int64_t cnt[257] = {0};
+        for (int64_t i = 0; i < d; i++) cnt[((uint32_t(from[i]) >> shift) & 255u) + 1]++;
+        for (int b = 0; b < 256; b++) cnt[b + 1] += cnt[b];
+        for (int64_t i = 0; i < d; i++) to[cnt[(uint32_t(from[i]) >> shift) & 255u]++] = from[i];
+        std::swap(from, to);
+    }
+    if (from != a) std::copy(from, from + d, a);
+}
+
+// Bits needed for ids in [0, n).
+int id_bits(int64_t n) {
+    int b = 1;
+    while (b < 31 && (int64_t(1) << b) < n) b++;
+    return b;
 }
 
 // f(t) on threads t = 0 .. nt-1 (the calling thread runs t = 0).
@@ -74,10 +113,11 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
         while (nt > 1 && (m_raw < int64_t(nt) * 65536 ||
                           int64_t(nt) * n > std::min(m_raw, int64_t(1) << 25))) nt /= 2;   // counters <= edges
         const int64_t slice = (m_raw + nt - 1) / nt;
-        std::vector<int64_t> tc(size_t(nt) * size_t(n), 0);   // thread t's counts, then cursors
+        auto tc = raw_array<int64_t>(size_t(nt) * size_t(n));   // thread t's counts, then cursors
         std::vector<int64_t> tloops(nt, 0);
         run_threads(nt, [&](unsigned t) {
-            int64_t *c = tc.data() + size_t(t) * size_t(n);
+            int64_t *c = tc.get() + size_t(t) * size_t(n);
+            std::fill(c, c + n, int64_t(0));
             const int64_t b = int64_t(t) * slice, e = std::min(m_raw, b + slice);
             for (int64_t i = b; i < e; i++) {
                 if (src[i] == dst[i]) { tloops[t]++; continue; }
@@ -93,7 +133,7 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
             for (unsigned t = 0; t < nt; t++) d += tc[size_t(t) * size_t(n) + size_t(v)];
             rp[v + 1] = rp[v] + d;
         }
-        std::vector<int32_t> adj(rp[n]);
+        auto adj = raw_array<int32_t>(size_t(rp[n]));   // every entry written by the fill
         {
             // per-thread write cursors relative to the row start
             parallel_for(n, [&](int64_t v) {
@@ -106,7 +146,7 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
                 }
             });
             run_threads(nt, [&](unsigned t) {
-                int64_t *c = tc.data() + size_t(t) * size_t(n);
+                int64_t *c = tc.get() + size_t(t) * size_t(n);
                 const int64_t b = int64_t(t) * slice, e = std::min(m_raw, b + slice);
                 for (int64_t i = b; i < e; i++) {
                     if (src[i] == dst[i]) continue;
@@ -117,9 +157,10 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
         }
         // 2. sort and deduplicate each row
         std::vector<int64_t> deg(n);
+        const int bits = id_bits(n);
         parallel_for(n, [&](int64_t v) {
-            int32_t *b = adj.data() + rp[v], *e = adj.data() + rp[v + 1];
-            std::sort(b, e);
+            int32_t *b = adj.get() + rp[v], *e = adj.get() + rp[v + 1];
+            sort_ids(b, e - b, bits);
             deg[v] = std::unique(b, e) - b;
         }, 256);
         int64_t nnz = 0, maxd = 0;
@@ -142,15 +183,15 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
         // 4. CSR in internal ids, rows sorted
         std::vector<int64_t> rowptr(n + 1, 0);
         for (int64_t r = 0; r < n; r++) rowptr[r + 1] = rowptr[r] + deg[old_of[r]];
-        std::vector<int32_t> col(nnz);
+        auto col = raw_array<int32_t>(size_t(nnz));   // every row written below
         g->lowdeg.assign(n, 0);
         parallel_for(n, [&](int64_t i) {
             const int64_t r = n - 1 - i;   // the longest rows (highest ranks) first, spread over threads
             const int64_t v = old_of[r];
-            int32_t *o = col.data() + rowptr[r];
+            int32_t *o = col.get() + rowptr[r];
             const int64_t d = deg[v];
             for (int64_t j = 0; j < d; j++) o[j] = g->new_id[adj[rp[v] + j]];
-            std::sort(o, o + d);
+            sort_ids(o, d, bits);
             g->lowdeg[r] = int32_t(std::lower_bound(o, o + d, int32_t(r)) - o);
         }, 64);
         if (labels) {
@@ -213,16 +254,18 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
             }
             if (nh > 0) {
                 std::vector<int32_t> hub(n, -1);
-                std::vector<uint32_t> bits(size_t(nh) * size_t(words), 0u);
+                const size_t n_bits = size_t(nh) * size_t(words);
+                auto bits = raw_array<uint32_t>(n_bits);
                 parallel_for(nh, [&](int64_t i) {      // one hub's bitmap per task
                     const int64_t r = n - 1 - i;
                     hub[r] = int32_t(i);
-                    uint32_t *w = bits.data() + size_t(i) * size_t(words);
+                    uint32_t *w = bits.get() + size_t(i) * size_t(words);
+                    std::fill(w, w + words, 0u);
                     for (int64_t e = rowptr[r]; e < rowptr[r + 1]; e++)
                         w[col[e] >> 5] |= 1u << (col[e] & 31);
                 }, 1, 2);
                 g->d_hub = (int32_t *)dev_alloc(sizeof(int32_t) * n, device);
-                g->d_bits = (uint32_t *)dev_alloc(sizeof(uint32_t) * bits.size(), device);
+                g->d_bits = (uint32_t *)dev_alloc(sizeof(uint32_t) * n_bits, device);
                 if (!g->d_hub || !g->d_bits) {
                     set_error("pm_load_graph: device allocation failed (hub bitmaps)");
                     pm_free_graph(g);
@@ -231,10 +274,10 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
                 }
                 g->n_hubs = nh;
                 g->hub_words = words;
-                g->bytes += sizeof(int32_t) * n + sizeof(uint32_t) * bits.size();
+                g->bytes += sizeof(int32_t) * n + sizeof(uint32_t) * n_bits;
                 cudaError_t eh = cudaMemcpyAsync(g->d_hub, hub.data(), sizeof(int32_t) * n,
                                                  cudaMemcpyHostToDevice, s);
-                if (!eh) eh = cudaMemcpyAsync(g->d_bits, bits.data(), sizeof(uint32_t) * bits.size(),
+                if (!eh) eh = cudaMemcpyAsync(g->d_bits, bits.get(), sizeof(uint32_t) * n_bits,
                                               cudaMemcpyHostToDevice, s);
                 if (!eh) eh = cudaStreamSynchronize(s);   // host vectors die here
                 if (eh) {
@@ -246,7 +289,7 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
             }
         }
         cudaError_t e1 = cudaMemcpyAsync(g->d_rowptr, rowptr.data(), b_rp, cudaMemcpyHostToDevice, s);
-        cudaError_t e2 = nnz ? cudaMemcpyAsync(g->d_col, col.data(), sizeof(int32_t) * nnz,
+        cudaError_t e2 = nnz ? cudaMemcpyAsync(g->d_col, col.get(), sizeof(int32_t) * nnz,
                                                cudaMemcpyHostToDevice, s) : cudaSuccess;
         cudaError_t e3 = cudaSuccess;
         for (int sp = 0; sp < 3 && !e3; sp++)
