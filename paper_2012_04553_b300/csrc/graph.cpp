@@ -239,10 +239,20 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
             return PM_ENOMEM;
         }
         g->bytes = 4 * b_rp + b_col + (labels ? n : 0);
+        cudaError_t e1 = cudaMemcpyAsync(g->d_rowptr, rowptr.data(), b_rp, cudaMemcpyHostToDevice, s);
+        cudaError_t e2 = nnz ? cudaMemcpyAsync(g->d_col, col.get(), sizeof(int32_t) * nnz,
+                                               cudaMemcpyHostToDevice, s) : cudaSuccess;
+        cudaError_t e3 = cudaSuccess;
+        for (int sp = 0; sp < 3 && !e3; sp++)
+            e3 = cudaMemcpyAsync(g->d_off[sp], off[sp].data(), b_rp, cudaMemcpyHostToDevice, s);
+        cudaError_t e4 = labels ? cudaMemcpyAsync(g->d_labels, g->labels.data(), n,
+                                                  cudaMemcpyHostToDevice, s) : cudaSuccess;
         // 7. adjacency bitmaps for the highest-degree vertices: every vertex of
         //    degree >= PM_HUB_MIN_DEGREE (environment, default 1024), highest
-        //    first, within 256 MiB of bitmaps
-        {
+        //    first, within 256 MiB of bitmaps; built on the device from the
+        //    uploaded CSR, behind the copies on the same stream
+        cudaError_t e6 = cudaSuccess;
+        if (!(e1 || e2 || e3 || e4)) {
             int64_t min_degree = 1024;
             if (const char *env = std::getenv("PM_HUB_MIN_DEGREE")) min_degree = std::max(1L, std::atol(env));
             const int64_t words = (n + 31) / 32;
@@ -253,20 +263,11 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
                 nh++;
             }
             if (nh > 0) {
-                std::vector<int32_t> hub(n, -1);
                 const size_t n_bits = size_t(nh) * size_t(words);
-                auto bits = raw_array<uint32_t>(n_bits);
-                parallel_for(nh, [&](int64_t i) {      // one hub's bitmap per task
-                    const int64_t r = n - 1 - i;
-                    hub[r] = int32_t(i);
-                    uint32_t *w = bits.get() + size_t(i) * size_t(words);
-                    std::fill(w, w + words, 0u);
-                    for (int64_t e = rowptr[r]; e < rowptr[r + 1]; e++)
-                        w[col[e] >> 5] |= 1u << (col[e] & 31);
-                }, 1, 2);
                 g->d_hub = (int32_t *)dev_alloc(sizeof(int32_t) * n, device);
                 g->d_bits = (uint32_t *)dev_alloc(sizeof(uint32_t) * n_bits, device);
                 if (!g->d_hub || !g->d_bits) {
+                    cudaStreamSynchronize(s);   // the copies read host buffers of this frame
                     set_error("pm_load_graph: device allocation failed (hub bitmaps)");
                     pm_free_graph(g);
                     cudaSetDevice(prev);
@@ -275,32 +276,14 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
                 g->n_hubs = nh;
                 g->hub_words = words;
                 g->bytes += sizeof(int32_t) * n + sizeof(uint32_t) * n_bits;
-                cudaError_t eh = cudaMemcpyAsync(g->d_hub, hub.data(), sizeof(int32_t) * n,
-                                                 cudaMemcpyHostToDevice, s);
-                if (!eh) eh = cudaMemcpyAsync(g->d_bits, bits.get(), sizeof(uint32_t) * n_bits,
-                                              cudaMemcpyHostToDevice, s);
-                if (!eh) eh = cudaStreamSynchronize(s);   // host vectors die here
-                if (eh) {
-                    set_error(std::string("pm_load_graph: hub upload: ") + cudaGetErrorString(eh));
-                    pm_free_graph(g);
-                    cudaSetDevice(prev);
-                    return PM_ECUDA;
-                }
+                e6 = cudaError_t(launch_hub_bitmaps(g->d_rowptr, g->d_col, n, nh, words, g->d_hub, g->d_bits, s));
             }
         }
-        cudaError_t e1 = cudaMemcpyAsync(g->d_rowptr, rowptr.data(), b_rp, cudaMemcpyHostToDevice, s);
-        cudaError_t e2 = nnz ? cudaMemcpyAsync(g->d_col, col.get(), sizeof(int32_t) * nnz,
-                                               cudaMemcpyHostToDevice, s) : cudaSuccess;
-        cudaError_t e3 = cudaSuccess;
-        for (int sp = 0; sp < 3 && !e3; sp++)
-            e3 = cudaMemcpyAsync(g->d_off[sp], off[sp].data(), b_rp, cudaMemcpyHostToDevice, s);
-        cudaError_t e4 = labels ? cudaMemcpyAsync(g->d_labels, g->labels.data(), n,
-                                                  cudaMemcpyHostToDevice, s) : cudaSuccess;
         cudaError_t e5 = cudaStreamSynchronize(s);
         cudaSetDevice(prev);
-        if (e1 || e2 || e3 || e4 || e5) {
-            set_error(std::string("pm_load_graph: upload failed: ") +
-                      cudaGetErrorString(e5 ? e5 : (e1 ? e1 : (e2 ? e2 : (e3 ? e3 : e4)))));
+        if (e1 || e2 || e3 || e4 || e5 || e6) {
+            const cudaError_t first = e1 ? e1 : e2 ? e2 : e3 ? e3 : e4 ? e4 : e6 ? e6 : e5;
+            set_error(std::string("pm_load_graph: upload failed: ") + cudaGetErrorString(first));
             pm_free_graph(g);
             return PM_ECUDA;
         }

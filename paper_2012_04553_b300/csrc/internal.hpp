@@ -95,6 +95,14 @@ void dev_free(void *ptr, size_t bytes, int device);
 
 void set_error(const std::string &msg);
 
+// Graph preparation on the device (graph_dev.cu): zeroes d_bits and fills
+// the nh adjacency bitmaps (words 32-bit words each) of internal vertices
+// n-1, ..., n-nh from the device CSR, and d_hub[r] = n-1-r for those ranks,
+// -1 for the others; asynchronous on the stream.  Returns a cudaError_t
+// value (0 on success).
+int launch_hub_bitmaps(const int64_t *d_rowptr, const int32_t *d_col, int64_t n, int64_t nh,
+                       int64_t words, int32_t *d_hub, uint32_t *d_bits, void *stream);
+
 // Kernel launchers (match.cu).
 // Resets the control block and arms the deadline (budget_ns = 0: none).
 int launch_arm(Control *d_ctl, uint64_t budget_ns, void *stream);
