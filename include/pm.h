@@ -131,12 +131,29 @@ pm_status pm_set_allocator(pm_alloc_fn alloc, pm_free_fn release, void *ctx);
  * adjacency bitmap (highest degrees first, at most 256 MiB in total) that
  * turns membership tests in their lists into single bit reads.
  * Errors: PM_EINVAL (null pointer,
- * n < 1 or n > 2^31-1, an id outside [0, n)), PM_ENOMEM, PM_ECUDA. */
+ * n < 1 or n > 2^31-1, an id outside [0, n)), PM_ENOMEM, PM_ECUDA,
+ * PM_EUNSUPPORTED (2^32 or more adjacency entries). */
 pm_status pm_load_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_t *dst,
                         const uint8_t *labels, int device, void *stream, pm_graph **out);
 pm_status pm_graph_get_info(const pm_graph *g, pm_graph_info *out);
 /* new_id[v] = internal (degree-ordered) id of caller vertex v; n entries. */
 pm_status pm_graph_vertex_order(const pm_graph *g, int32_t *new_id);
+/* The host half of pm_load_graph alone (Section 2's data graph as the
+ * matching kernels read it), touching no device: self-loops and duplicate
+ * edges dropped, both directions stored, vertices renumbered by (degree,
+ * caller id) ascending, rows in internal ids sorted ascending.  All buffers
+ * are host memory owned by the caller.  rowptr: n + 1 int64 row offsets;
+ * col: room for 2 * m_raw int32 entries (an upper bound), of which rowptr[n]
+ * (twice the simple edge count) are written; new_id (NULL to skip): n int32,
+ * the internal id of each caller vertex; lowdeg (NULL to skip): n int64, per
+ * internal id the neighbours with smaller internal ids (where its row
+ * crosses its own id).  Labels are not taken: a caller permutes its own
+ * with new_id.
+ * Errors: PM_EINVAL (null rowptr or col, n < 1 or n > 2^31-1, null edge
+ * arrays with m_raw > 0, an id outside [0, n)), PM_ENOMEM, PM_EUNSUPPORTED
+ * (2^32 or more adjacency entries). */
+pm_status pm_prepare_csr(int64_t n, int64_t m_raw, const int32_t *src, const int32_t *dst,
+                         int64_t *rowptr, int32_t *col, int32_t *new_id, int64_t *lowdeg);
 void pm_free_graph(pm_graph *g);
 
 /* Plan a query set (Section 4.1 "external module", step a): canonicalise and

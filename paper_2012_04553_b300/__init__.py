@@ -84,6 +84,7 @@ def _load():
         "pm_load_graph": [i64, i64, vp, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)],
         "pm_graph_get_info": [vp, ctypes.POINTER(c_graph_info)],
         "pm_graph_vertex_order": [vp, vp],
+        "pm_prepare_csr": [i64, i64, vp, vp, vp, vp, vp, vp],
         "pm_plan": [vp, ctypes.POINTER(c_pattern), i32, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)],
         "pm_plan_get_info": [vp, ctypes.POINTER(c_plan_info)],
         "pm_plan_matched": [vp, ctypes.POINTER(c_pattern)],
@@ -146,6 +147,7 @@ ABI_SYMBOLS = [
     "pm_server_destroy", "pm_plan_set_launch", "pm_count_each", "pm_plan_query_columns",
     "pm_plan_pattern_ms", "pm_plan_last_launches", "pm_support_roots", "pm_domains_or",
     "pm_support_from_domains", "pm_enumerate", "pm_plan_capture_each", "pm_plan_pattern_bytes",
+    "pm_prepare_csr",
 ]
 
 
@@ -283,6 +285,24 @@ def make_pattern(k, edge_mask, induced=EDGE_INDUCED, labels=None):
 def _words_to_ints(words):
     w = np.asarray(words, dtype=np.uint64).reshape(-1, 2)
     return [int(lo) | (int(hi) << 64) for lo, hi in w]
+
+
+def prepare_csr(n, src, dst):
+    """pm_prepare_csr: the host half of graph loading alone, on no device.
+    Returns (rowptr int64[n+1], col int32[rowptr[n]], new_id int32[n],
+    lowdeg int64[n]): the degree-ordered CSR with sorted rows that
+    pm_load_graph uploads, the internal id of each caller vertex, and per
+    internal id its neighbours below it."""
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    n = int(n)
+    rowptr = np.zeros(max(n, 0) + 1, dtype=np.int64)
+    col = np.empty(max(1, 2 * len(src)), dtype=np.int32)
+    new_id = np.empty(max(n, 0), dtype=np.int32)
+    lowdeg = np.empty(max(n, 0), dtype=np.int64)
+    _check(_lib.pm_prepare_csr(n, len(src), _ptr(src), _ptr(dst), _ptr(rowptr), _ptr(col), _ptr(new_id),
+                               _ptr(lowdeg)), "pm_prepare_csr")
+    return rowptr, col[:rowptr[-1]].copy(), new_id, lowdeg
 
 
 class Graph:

@@ -21,6 +21,8 @@ namespace pm {
 
 pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_t *dst,
                       const uint8_t *labels, int device, void *stream, pm_graph **out);
+pm_status prepare_csr(int64_t n, int64_t m_raw, const int32_t *src, const int32_t *dst,
+                      int64_t *rowptr, int32_t *col, int32_t *new_id, int64_t *lowdeg);
 
 namespace {
 thread_local std::string g_last_error;
@@ -1496,6 +1498,11 @@ pm_status pm_load_graph(int64_t n, int64_t m_raw, const int32_t *src, const int3
         return PM_EINVAL;
     }
     return build_graph(n, m_raw, src, dst, labels, device, stream, out);
+}
+
+pm_status pm_prepare_csr(int64_t n, int64_t m_raw, const int32_t *src, const int32_t *dst,
+                         int64_t *rowptr, int32_t *col, int32_t *new_id, int64_t *lowdeg) {
+    return prepare_csr(n, m_raw, src, dst, rowptr, col, new_id, lowdeg);
 }
 
 pm_status pm_graph_get_info(const pm_graph *g, pm_graph_info *out) {

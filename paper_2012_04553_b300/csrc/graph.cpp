@@ -84,138 +84,178 @@ void run_threads(unsigned nt, F f) {
     for (auto &x : th) x.join();
 }
 
-}  // namespace
-
-pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_t *dst,
-                      const uint8_t *labels, int device, void *stream, pm_graph **out) {
-    if (!out || n < 1 || n > INT32_MAX || m_raw < 0 || (m_raw > 0 && (!src || !dst))) {
-        set_error("pm_load_graph: invalid argument");
+// Argument and edge checks shared by pm_load_graph and pm_prepare_csr.
+pm_status check_input(const char *who, int64_t n, int64_t m_raw, const int32_t *src, const int32_t *dst) {
+    if (n < 1 || n > INT32_MAX || m_raw < 0 || (m_raw > 0 && (!src || !dst))) {
+        set_error(std::string(who) + ": invalid argument");
         return PM_EINVAL;
     }
     for (int64_t i = 0; i < m_raw; i++) {
         if (src[i] < 0 || src[i] >= n || dst[i] < 0 || dst[i] >= n) {
-            set_error("pm_load_graph: edge " + std::to_string(i) + " has a vertex id outside [0, n)");
+            set_error(std::string(who) + ": edge " + std::to_string(i) + " has a vertex id outside [0, n)");
             return PM_EINVAL;
         }
     }
+    return PM_OK;
+}
+
+// The host CSR of a prepared graph: rows in internal ids, each sorted, and
+// the task offsets of the three task spaces.
+struct HostCsr {
+    std::vector<int64_t> rowptr;
+    std::unique_ptr<int32_t[]> col;
+    int64_t nnz = 0;
+    std::vector<int64_t> off[3];
+};
+
+// Steps 1-5 of graph preparation on checked input: fills the host fields of
+// g (counts, new_id, lowdeg, labels, task totals) and h.  May throw
+// std::bad_alloc.
+pm_status prepare_host(const char *who, int64_t n, int64_t m_raw, const int32_t *src, const int32_t *dst,
+                       const uint8_t *labels, pm_graph *g, HostCsr &h) {
+    g->n = n;
+    g->labeled = labels != nullptr;
+    // 1. bucket both directions by source, dropping self-loops: each
+    //    thread counts its slice of the edges per vertex, the counts are
+    //    scanned per vertex across threads, and each thread fills its own
+    //    part of every row (no shared cursors: hub rows would serialise
+    //    them); the order inside a row does not matter, rows are sorted next
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    while (nt > 1 && (m_raw < int64_t(nt) * 65536 ||
+                      int64_t(nt) * n > std::min(m_raw, int64_t(1) << 25))) nt /= 2;   // counters <= edges
+    const int64_t slice = (m_raw + nt - 1) / nt;
+    auto tc = raw_array<int64_t>(size_t(nt) * size_t(n));   // thread t's counts, then cursors
+    std::vector<int64_t> tloops(nt, 0);
+    run_threads(nt, [&](unsigned t) {
+        int64_t *c = tc.get() + size_t(t) * size_t(n);
+        std::fill(c, c + n, int64_t(0));
+        const int64_t b = int64_t(t) * slice, e = std::min(m_raw, b + slice);
+        for (int64_t i = b; i < e; i++) {
+            if (src[i] == dst[i]) { tloops[t]++; continue; }
+            c[src[i]]++;
+            c[dst[i]]++;
+        }
+    });
+    int64_t loops = 0;
+    for (unsigned t = 0; t < nt; t++) loops += tloops[t];
+    std::vector<int64_t> rp(n + 1, 0);
+    for (int64_t v = 0; v < n; v++) {
+        int64_t d = 0;
+        for (unsigned t = 0; t < nt; t++) d += tc[size_t(t) * size_t(n) + size_t(v)];
+        rp[v + 1] = rp[v] + d;
+    }
+    auto adj = raw_array<int32_t>(size_t(rp[n]));   // every entry written by the fill
+    {
+        // per-thread write cursors relative to the row start
+        parallel_for(n, [&](int64_t v) {
+            int64_t run = 0;
+            for (unsigned t = 0; t < nt; t++) {
+                int64_t &c = tc[size_t(t) * size_t(n) + size_t(v)];
+                const int64_t k = c;
+                c = run;
+                run += k;
+            }
+        });
+        run_threads(nt, [&](unsigned t) {
+            int64_t *c = tc.get() + size_t(t) * size_t(n);
+            const int64_t b = int64_t(t) * slice, e = std::min(m_raw, b + slice);
+            for (int64_t i = b; i < e; i++) {
+                if (src[i] == dst[i]) continue;
+                adj[rp[src[i]] + c[src[i]]++] = dst[i];
+                adj[rp[dst[i]] + c[dst[i]]++] = src[i];
+            }
+        });
+    }
+    // 2. sort and deduplicate each row
+    std::vector<int64_t> deg(n);
+    const int bits = id_bits(n);
+    parallel_for(n, [&](int64_t v) {
+        int32_t *b = adj.get() + rp[v], *e = adj.get() + rp[v + 1];
+        sort_ids(b, e - b, bits);
+        deg[v] = std::unique(b, e) - b;
+    }, 256);
+    int64_t nnz = 0, maxd = 0;
+    for (int64_t v = 0; v < n; v++) { nnz += deg[v]; maxd = std::max(maxd, deg[v]); }
+    g->m = nnz / 2;
+    g->self_loops = loops;
+    g->duplicates = (m_raw - loops) - g->m;
+    g->max_degree = maxd;
+    // 3. order by (degree, id): counting sort on degree, stable in id
+    std::vector<int64_t> cnt(maxd + 2, 0);
+    for (int64_t v = 0; v < n; v++) cnt[deg[v] + 1]++;
+    for (int64_t d = 0; d <= maxd; d++) cnt[d + 1] += cnt[d];
+    g->new_id.assign(n, 0);
+    std::vector<int32_t> old_of(n);
+    for (int64_t v = 0; v < n; v++) {
+        int64_t r = cnt[deg[v]]++;
+        g->new_id[v] = int32_t(r);
+        old_of[r] = int32_t(v);
+    }
+    // 4. CSR in internal ids, rows sorted
+    std::vector<int64_t> &rowptr = h.rowptr;
+    rowptr.assign(n + 1, 0);
+    for (int64_t r = 0; r < n; r++) rowptr[r + 1] = rowptr[r] + deg[old_of[r]];
+    h.col = raw_array<int32_t>(size_t(nnz));   // every row written below
+    int32_t *col = h.col.get();
+    g->lowdeg.assign(n, 0);
+    parallel_for(n, [&](int64_t i) {
+        const int64_t r = n - 1 - i;   // the longest rows (highest ranks) first, spread over threads
+        const int64_t v = old_of[r];
+        int32_t *o = col + rowptr[r];
+        const int64_t d = deg[v];
+        for (int64_t j = 0; j < d; j++) o[j] = g->new_id[adj[rp[v] + j]];
+        sort_ids(o, d, bits);
+        g->lowdeg[r] = int32_t(std::lower_bound(o, o + d, int32_t(r)) - o);
+    }, 64);
+    if (labels) {
+        g->labels.resize(n);
+        for (int64_t r = 0; r < n; r++) g->labels[r] = labels[old_of[r]];
+    }
+    // 5. task offsets for the implicit root list n-1, ..., 0, per task
+    //    space: lower neighbours, higher neighbours, all neighbours
+    std::vector<int64_t> *off = h.off;
+    for (int sp = 0; sp < 3; sp++) off[sp].assign(n + 1, 0);
+    for (int64_t i = 0; i < n; i++) {
+        const int64_t r = n - 1 - i;
+        const int64_t d = rowptr[r + 1] - rowptr[r];
+        off[0][i + 1] = off[0][i] + g->lowdeg[r];
+        off[1][i + 1] = off[1][i] + (d - g->lowdeg[r]);
+        off[2][i + 1] = off[2][i] + d;
+        g->max_updeg = std::max<int64_t>(g->max_updeg, d - g->lowdeg[r]);
+    }
+    for (int sp = 0; sp < 3; sp++) g->ntasks[sp] = off[sp][n];
+    if (nnz >= (int64_t(1) << 32)) {
+        set_error(std::string(who) + ": more than 2^32 - 1 adjacency entries");
+        return PM_EUNSUPPORTED;
+    }
+    h.nnz = nnz;
+    return PM_OK;
+}
+
+}  // namespace
+
+pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_t *dst,
+                      const uint8_t *labels, int device, void *stream, pm_graph **out) {
+    if (!out) {
+        set_error("pm_load_graph: invalid argument");
+        return PM_EINVAL;
+    }
+    pm_status st = check_input("pm_load_graph", n, m_raw, src, dst);
+    if (st != PM_OK) return st;
     auto *g = new (std::nothrow) pm_graph();
     if (!g) return PM_ENOMEM;
     g->device = device;
-    g->n = n;
-    g->labeled = labels != nullptr;
     try {
-        // 1. bucket both directions by source, dropping self-loops: each
-        //    thread counts its slice of the edges per vertex, the counts are
-        //    scanned per vertex across threads, and each thread fills its own
-        //    part of every row (no shared cursors: hub rows would serialise
-        //    them); the order inside a row does not matter, rows are sorted next
-        unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-        while (nt > 1 && (m_raw < int64_t(nt) * 65536 ||
-                          int64_t(nt) * n > std::min(m_raw, int64_t(1) << 25))) nt /= 2;   // counters <= edges
-        const int64_t slice = (m_raw + nt - 1) / nt;
-        auto tc = raw_array<int64_t>(size_t(nt) * size_t(n));   // thread t's counts, then cursors
-        std::vector<int64_t> tloops(nt, 0);
-        run_threads(nt, [&](unsigned t) {
-            int64_t *c = tc.get() + size_t(t) * size_t(n);
-            std::fill(c, c + n, int64_t(0));
-            const int64_t b = int64_t(t) * slice, e = std::min(m_raw, b + slice);
-            for (int64_t i = b; i < e; i++) {
-                if (src[i] == dst[i]) { tloops[t]++; continue; }
-                c[src[i]]++;
-                c[dst[i]]++;
-            }
-        });
-        int64_t loops = 0;
-        for (unsigned t = 0; t < nt; t++) loops += tloops[t];
-        std::vector<int64_t> rp(n + 1, 0);
-        for (int64_t v = 0; v < n; v++) {
-            int64_t d = 0;
-            for (unsigned t = 0; t < nt; t++) d += tc[size_t(t) * size_t(n) + size_t(v)];
-            rp[v + 1] = rp[v] + d;
-        }
-        auto adj = raw_array<int32_t>(size_t(rp[n]));   // every entry written by the fill
-        {
-            // per-thread write cursors relative to the row start
-            parallel_for(n, [&](int64_t v) {
-                int64_t run = 0;
-                for (unsigned t = 0; t < nt; t++) {
-                    int64_t &c = tc[size_t(t) * size_t(n) + size_t(v)];
-                    const int64_t k = c;
-                    c = run;
-                    run += k;
-                }
-            });
-            run_threads(nt, [&](unsigned t) {
-                int64_t *c = tc.get() + size_t(t) * size_t(n);
-                const int64_t b = int64_t(t) * slice, e = std::min(m_raw, b + slice);
-                for (int64_t i = b; i < e; i++) {
-                    if (src[i] == dst[i]) continue;
-                    adj[rp[src[i]] + c[src[i]]++] = dst[i];
-                    adj[rp[dst[i]] + c[dst[i]]++] = src[i];
-                }
-            });
-        }
-        // 2. sort and deduplicate each row
-        std::vector<int64_t> deg(n);
-        const int bits = id_bits(n);
-        parallel_for(n, [&](int64_t v) {
-            int32_t *b = adj.get() + rp[v], *e = adj.get() + rp[v + 1];
-            sort_ids(b, e - b, bits);
-            deg[v] = std::unique(b, e) - b;
-        }, 256);
-        int64_t nnz = 0, maxd = 0;
-        for (int64_t v = 0; v < n; v++) { nnz += deg[v]; maxd = std::max(maxd, deg[v]); }
-        g->m = nnz / 2;
-        g->self_loops = loops;
-        g->duplicates = (m_raw - loops) - g->m;
-        g->max_degree = maxd;
-        // 3. order by (degree, id): counting sort on degree, stable in id
-        std::vector<int64_t> cnt(maxd + 2, 0);
-        for (int64_t v = 0; v < n; v++) cnt[deg[v] + 1]++;
-        for (int64_t d = 0; d <= maxd; d++) cnt[d + 1] += cnt[d];
-        g->new_id.assign(n, 0);
-        std::vector<int32_t> old_of(n);
-        for (int64_t v = 0; v < n; v++) {
-            int64_t r = cnt[deg[v]]++;
-            g->new_id[v] = int32_t(r);
-            old_of[r] = int32_t(v);
-        }
-        // 4. CSR in internal ids, rows sorted
-        std::vector<int64_t> rowptr(n + 1, 0);
-        for (int64_t r = 0; r < n; r++) rowptr[r + 1] = rowptr[r] + deg[old_of[r]];
-        auto col = raw_array<int32_t>(size_t(nnz));   // every row written below
-        g->lowdeg.assign(n, 0);
-        parallel_for(n, [&](int64_t i) {
-            const int64_t r = n - 1 - i;   // the longest rows (highest ranks) first, spread over threads
-            const int64_t v = old_of[r];
-            int32_t *o = col.get() + rowptr[r];
-            const int64_t d = deg[v];
-            for (int64_t j = 0; j < d; j++) o[j] = g->new_id[adj[rp[v] + j]];
-            sort_ids(o, d, bits);
-            g->lowdeg[r] = int32_t(std::lower_bound(o, o + d, int32_t(r)) - o);
-        }, 64);
-        if (labels) {
-            g->labels.resize(n);
-            for (int64_t r = 0; r < n; r++) g->labels[r] = labels[old_of[r]];
-        }
-        // 5. task offsets for the implicit root list n-1, ..., 0, per task
-        //    space: lower neighbours, higher neighbours, all neighbours
-        std::vector<int64_t> off[3];
-        for (int sp = 0; sp < 3; sp++) off[sp].assign(n + 1, 0);
-        for (int64_t i = 0; i < n; i++) {
-            const int64_t r = n - 1 - i;
-            const int64_t d = rowptr[r + 1] - rowptr[r];
-            off[0][i + 1] = off[0][i] + g->lowdeg[r];
-            off[1][i + 1] = off[1][i] + (d - g->lowdeg[r]);
-            off[2][i + 1] = off[2][i] + d;
-            g->max_updeg = std::max<int64_t>(g->max_updeg, d - g->lowdeg[r]);
-        }
-        for (int sp = 0; sp < 3; sp++) g->ntasks[sp] = off[sp][n];
-        if (nnz >= (int64_t(1) << 32)) {
-            set_error("pm_load_graph: more than 2^32 - 1 adjacency entries");
+        HostCsr h;
+        st = prepare_host("pm_load_graph", n, m_raw, src, dst, labels, g, h);
+        if (st != PM_OK) {
             delete g;
-            return PM_EUNSUPPORTED;
+            return st;
         }
+        const std::vector<int64_t> &rowptr = h.rowptr;
+        const int32_t *col = h.col.get();
+        const int64_t nnz = h.nnz;
+        const std::vector<int64_t> *off = h.off;
 
         // 6. upload
         int prev = 0;
@@ -240,7 +280,7 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
         }
         g->bytes = 4 * b_rp + b_col + (labels ? n : 0);
         cudaError_t e1 = cudaMemcpyAsync(g->d_rowptr, rowptr.data(), b_rp, cudaMemcpyHostToDevice, s);
-        cudaError_t e2 = nnz ? cudaMemcpyAsync(g->d_col, col.get(), sizeof(int32_t) * nnz,
+        cudaError_t e2 = nnz ? cudaMemcpyAsync(g->d_col, col, sizeof(int32_t) * nnz,
                                                cudaMemcpyHostToDevice, s) : cudaSuccess;
         cudaError_t e3 = cudaSuccess;
         for (int sp = 0; sp < 3 && !e3; sp++)
@@ -293,6 +333,30 @@ pm_status build_graph(int64_t n, int64_t m_raw, const int32_t *src, const int32_
         return PM_ENOMEM;
     }
     *out = g;
+    return PM_OK;
+}
+
+pm_status prepare_csr(int64_t n, int64_t m_raw, const int32_t *src, const int32_t *dst,
+                      int64_t *rowptr, int32_t *col, int32_t *new_id, int64_t *lowdeg) {
+    if (!rowptr || !col) {
+        set_error("pm_prepare_csr: invalid argument");
+        return PM_EINVAL;
+    }
+    pm_status st = check_input("pm_prepare_csr", n, m_raw, src, dst);
+    if (st != PM_OK) return st;
+    try {
+        pm_graph g;   // host fields only: nothing on a device
+        HostCsr h;
+        st = prepare_host("pm_prepare_csr", n, m_raw, src, dst, nullptr, &g, h);
+        if (st != PM_OK) return st;
+        std::copy(h.rowptr.begin(), h.rowptr.end(), rowptr);
+        std::copy(h.col.get(), h.col.get() + h.nnz, col);
+        if (new_id) std::copy(g.new_id.begin(), g.new_id.end(), new_id);
+        if (lowdeg) std::copy(g.lowdeg.begin(), g.lowdeg.end(), lowdeg);
+    } catch (const std::bad_alloc &) {
+        set_error("pm_prepare_csr: host allocation failed");
+        return PM_ENOMEM;
+    }
     return PM_OK;
 }
 
