@@ -139,21 +139,23 @@ pm_status prepare_host(const char *who, int64_t n, int64_t m_raw, const int32_t 
     int64_t loops = 0;
     for (unsigned t = 0; t < nt; t++) loops += tloops[t];
     std::vector<int64_t> rp(n + 1, 0);
-    for (int64_t v = 0; v < n; v++) {
+    parallel_for(n, [&](int64_t v) {     // raw degree: the threads' counts summed
         int64_t d = 0;
         for (unsigned t = 0; t < nt; t++) d += tc[size_t(t) * size_t(n) + size_t(v)];
-        rp[v + 1] = rp[v] + d;
-    }
+        rp[v + 1] = d;
+    });
+    for (int64_t v = 0; v < n; v++) rp[v + 1] += rp[v];
     auto adj = raw_array<int32_t>(size_t(rp[n]));   // every entry written by the fill
     {
-        // per-thread write cursors relative to the row start
+        // per-thread write positions: thread t fills row v after the entries
+        // of threads 0 .. t-1, so each row keeps the input order of its edges
         parallel_for(n, [&](int64_t v) {
-            int64_t run = 0;
+            int64_t pos = rp[v];
             for (unsigned t = 0; t < nt; t++) {
                 int64_t &c = tc[size_t(t) * size_t(n) + size_t(v)];
                 const int64_t k = c;
-                c = run;
-                run += k;
+                c = pos;
+                pos += k;
             }
         });
         run_threads(nt, [&](unsigned t) {
@@ -161,8 +163,8 @@ pm_status prepare_host(const char *who, int64_t n, int64_t m_raw, const int32_t 
             const int64_t b = int64_t(t) * slice, e = std::min(m_raw, b + slice);
             for (int64_t i = b; i < e; i++) {
                 if (src[i] == dst[i]) continue;
-                adj[rp[src[i]] + c[src[i]]++] = dst[i];
-                adj[rp[dst[i]] + c[dst[i]]++] = src[i];
+                adj[c[src[i]]++] = dst[i];
+                adj[c[dst[i]]++] = src[i];
             }
         });
     }
