@@ -74,6 +74,16 @@ def test_star_one_long_row():
     assert new_id[0] == n - 1 and rowptr[-1] == 2 * (n - 1)
 
 
+@pytest.mark.parametrize("m_raw", [2 * 65536 - 1, 2 * 65536 + 1, 3 * 65536 + 7])
+def test_thread_split_boundaries(m_raw):
+    """Edge lists just below and above the two-thread threshold, and one
+    that does not divide evenly into the threads' slices."""
+    rng = np.random.default_rng(145 + m_raw)
+    s = rng.integers(0, 5000, m_raw).astype(np.int32)
+    d = rng.integers(0, 5000, m_raw).astype(np.int32)
+    check(5000, s, d)
+
+
 @pytest.mark.parametrize("n,p,seed", [(40, 0.3, 143), (300, 0.05, 144)])
 def test_small_random_graphs(n, p, seed):
     s, d = gnp_edges(n, p, seed)
